@@ -1,0 +1,145 @@
+/*
+ * esom.h -- C ABI of the GB300 EmbedSOM projection library (libesom.so).
+ *
+ * The library maps n high-dimensional points to 2-D with the EmbedSOM
+ * projection (paper: "Scalable semi-supervised dimensionality reduction with
+ * GPU-accelerated EmbedSOM", Section 3.1, steps 1-4; GPU form in Section 4:
+ * the k-NN step of Section 4.2 and the projection step of Section 4.3, run
+ * as in Section 4.4 but fused into one kernel).
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers (for example from torch's
+ *     data_ptr()) to contiguous, row-major float32 / int32 data, unless the
+ *     entry point says otherwise.  The caller owns every buffer it passes;
+ *     the library never frees caller memory.
+ *   - `stream` is a cudaStream_t (a CUstream_st*); NULL is the legacy
+ *     default stream.  Calls are asynchronous on that stream, make no host
+ *     synchronisation and allocate nothing after esom_create /
+ *     esom_set_landmarks (esom_project_host allocates its staging buffers on
+ *     its first call).
+ *   - A handle is bound to the device that was current at esom_create;
+ *     calls made while another device is current return ESOM_EINVAL.
+ *   - Every call checks its arguments first and launches nothing when they
+ *     are invalid; the message of the last failure on the calling host
+ *     thread is returned by esom_last_error().
+ *   - n == 0 returns ESOM_OK without launching.
+ *   - NaN or Inf inputs give unspecified output values, never a fault.
+ */
+#ifndef ESOM_H
+#define ESOM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct esom_ctx *esom_handle;
+typedef struct CUstream_st *esom_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+    ESOM_OK = 0,
+    ESOM_EINVAL = -1,        /* bad argument (size, range, null pointer, device) */
+    ESOM_ENOMEM = -2,        /* device or host allocation failed */
+    ESOM_EALIGN = -3,        /* pointer not 16-byte aligned, or d not a multiple of 4 */
+    ESOM_ENOLANDMARKS = -4,  /* esom_set_landmarks has not been called */
+    ESOM_ECUDA = -5,         /* a CUDA runtime call or launch failed */
+    ESOM_EUNSUPPORTED = -6,  /* (d, k) outside what this build instantiates */
+    ESOM_EDEVICE = -7        /* a kernel reported a device-side error (bounded wait ran out) */
+} esom_status;
+
+/* Limits of this build: d is a multiple of 4 in [4, ESOM_MAX_D];
+ * 2 <= k <= min(L, ESOM_MAX_K); 1 <= L <= ESOM_MAX_L. */
+#define ESOM_MAX_D 64
+#define ESOM_MAX_K 32
+#define ESOM_MAX_L (1 << 24)
+
+/* Creates a projection context for points of dimension d, L landmarks and k
+ * neighbours (Section 3.1 step 1 requires 3 <= k <= L; k = 2 is accepted as
+ * a degenerate case whose result is the nearest landmark's 2-D position).
+ * Allocates the device copies of the landmarks and a device status word on
+ * the current device.  On success *out receives the handle. */
+esom_status esom_create(int d, int L, int k, esom_handle *out);
+
+/* Copies the landmarks into the handle (Section 3.1: L is g x d, l is g x 2;
+ * the paper's g is L here).  hi: L x d float32, lo: L x 2 float32, host or
+ * device pointers (copied with cudaMemcpyDefault on `stream`).  The caller
+ * keeps ownership and may reuse the buffers once the copy has run on the
+ * stream.  Each call increments the landmark version.  Projections queued
+ * on other streams are not ordered against this copy by the library. */
+esom_status esom_set_landmarks(esom_handle h, const float *hi, const float *lo,
+                               esom_stream_t stream);
+
+/* Landmark version: 0 before the first esom_set_landmarks, then 1, 2, ... */
+uint64_t esom_landmark_version(esom_handle h);
+
+/* EmbedSOM projection (Section 3.1 steps 1-4; Section 4.3):
+ *   points: n x d float32, 16-byte aligned (ESOM_EALIGN otherwise);
+ *   out:    n x 2 float32, 8-byte aligned, receives x_i = (x, y);
+ *   boost > 0: sharpness of the distance-to-score map (step 2);
+ *   adjust >= 0: pair weight s_u s_v / |l_v - l_u|^(2 adjust); adjust = 1 is
+ *     exactly the objective printed in step 4.
+ * One fused kernel per call: k-NN in FP32, scores and pair terms in FP32,
+ * the 2x2 determinant and solve in FP64. */
+esom_status esom_project(esom_handle h, const float *points, int64_t n, float *out,
+                         float boost, float adjust, esom_stream_t stream);
+
+/* k-NN step alone (Section 3.1 step 1; Section 4.2):
+ *   points: n x d float32, 16-byte aligned;
+ *   idx:    n x k int32, landmark indices in ascending distance, ties to the
+ *           lower index;
+ *   dist2:  n x k float32, squared Euclidean distances (nullable). */
+esom_status esom_knn(esom_handle h, const float *points, int64_t n, int32_t *idx,
+                     float *dist2, esom_stream_t stream);
+
+/* esom_project for HOST buffers: points_host (n x d) and out_host (n x 2)
+ * are host pointers (pinned memory gives overlapped copies; pageable memory
+ * works but copies synchronously).  The points are streamed through device
+ * staging buffers owned by the handle in chunks, with host-to-device copies,
+ * projection and device-to-host copies of successive chunks overlapped on
+ * `stream` and two internal streams.  Returns after enqueueing; out_host is
+ * complete when `stream` reaches this point (synchronise it before reading).
+ * The staging buffers (2 x chunk x (d + 2) x 4 bytes) are allocated on the
+ * first call and kept until esom_destroy. */
+esom_status esom_project_host(esom_handle h, const float *points_host, int64_t n,
+                              float *out_host, float boost, float adjust,
+                              esom_stream_t stream);
+
+/* Waits for `stream`, then reports and clears any device-side error flag
+ * that a kernel of this handle raised (a bounded wait on an mbarrier that
+ * ran out): ESOM_EDEVICE if one was raised, ESOM_OK otherwise. */
+esom_status esom_device_status(esom_handle h, esom_stream_t stream);
+
+/* Forces the number of landmarks per shared-memory chunk (0 restores the
+ * automatic choice: all landmarks resident when L*d*4 <= 64 KiB, otherwise
+ * 32 KiB chunks streamed through two buffers).  Lets tests drive the
+ * chunked path with small L; also a tuning knob. */
+esom_status esom_set_landmark_chunk(esom_handle h, int chunk);
+
+/* Launch configuration chosen for this handle (for tests and tuning). */
+typedef struct {
+    int d, L, k, kc;            /* kc: compile-time capacity of the k-NN list */
+    int threads_per_block;      /* points per tile = threads per block */
+    int blocks_per_sm, num_sms;
+    int landmark_chunk;         /* landmarks per shared-memory chunk */
+    int landmark_chunks;        /* 1: all landmarks resident in shared memory */
+    int shared_bytes;           /* dynamic shared memory per block */
+} esom_config;
+
+esom_status esom_get_config(esom_handle h, esom_config *cfg);
+
+/* Releases the handle's device buffers.  Pending work on streams that use
+ * the handle must have completed. NULL is accepted. */
+esom_status esom_destroy(esom_handle h);
+
+/* Message of the last non-OK status returned on this host thread. */
+const char *esom_last_error(void);
+
+/* Constant name of a status code. */
+const char *esom_status_string(esom_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESOM_H */

@@ -1,0 +1,246 @@
+"""Python binding of libesom (ctypes).
+
+The functions named like the C ABI (``esom_create``, ``esom_project``, ...)
+only marshal arguments: pointers are passed as integers (for example
+``tensor.data_ptr()``) and each returns the C status code.  ``Projector`` is
+a convenience wrapper for torch CUDA tensors that checks shapes, dtypes and
+devices and raises ``EsomError`` on a non-OK status.  Every computation runs
+in the CUDA library; there is no CPU path, and loading fails loudly when the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+ESOM_OK = 0
+ESOM_EINVAL = -1
+ESOM_ENOMEM = -2
+ESOM_EALIGN = -3
+ESOM_ENOLANDMARKS = -4
+ESOM_ECUDA = -5
+ESOM_EUNSUPPORTED = -6
+ESOM_EDEVICE = -7
+
+HEADER = os.path.join(_build.INCLUDE, "esom.h")
+
+
+class EsomError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_string(status)}: {message}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in
+                ("d", "L", "k", "kc", "threads_per_block", "blocks_per_sm", "num_sms",
+                 "landmark_chunk", "landmark_chunks", "shared_bytes")]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libesom.so (building it first only if asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(
+                f"libesom.so is not built ({_build.LIB}); run "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P, I, I64, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float
+    sigs = {
+        "esom_create": ([I, I, I, ctypes.POINTER(P)], I),
+        "esom_set_landmarks": ([P, P, P, P], I),
+        "esom_landmark_version": ([P], ctypes.c_uint64),
+        "esom_project": ([P, P, I64, P, F, F, P], I),
+        "esom_knn": ([P, P, I64, P, P, P], I),
+        "esom_project_host": ([P, P, I64, P, F, F, P], I),
+        "esom_device_status": ([P, P], I),
+        "esom_set_landmark_chunk": ([P, I], I),
+        "esom_get_config": ([P, ctypes.POINTER(_Config)], I),
+        "esom_destroy": ([P], I),
+        "esom_last_error": ([], ctypes.c_char_p),
+        "esom_status_string": ([I], ctypes.c_char_p),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/esom.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(esom_[a-z_]+)\s*\(", text)))
+
+
+# --- the C ABI, one to one -------------------------------------------------
+
+def esom_create(d: int, L: int, k: int):
+    """Returns (status, handle)."""
+    h = ctypes.c_void_p()
+    st = load().esom_create(d, L, k, ctypes.byref(h))
+    return st, h.value
+
+
+def esom_set_landmarks(h, hi_ptr: int, lo_ptr: int, stream: int = 0) -> int:
+    return load().esom_set_landmarks(h, hi_ptr, lo_ptr, stream)
+
+
+def esom_landmark_version(h) -> int:
+    return int(load().esom_landmark_version(h))
+
+
+def esom_project(h, points_ptr: int, n: int, out_ptr: int, boost: float, adjust: float,
+                 stream: int = 0) -> int:
+    return load().esom_project(h, points_ptr, n, out_ptr, boost, adjust, stream)
+
+
+def esom_knn(h, points_ptr: int, n: int, idx_ptr: int, dist2_ptr: int | None,
+             stream: int = 0) -> int:
+    return load().esom_knn(h, points_ptr, n, idx_ptr, dist2_ptr, stream)
+
+
+def esom_project_host(h, points_ptr: int, n: int, out_ptr: int, boost: float, adjust: float,
+                      stream: int = 0) -> int:
+    return load().esom_project_host(h, points_ptr, n, out_ptr, boost, adjust, stream)
+
+
+def esom_device_status(h, stream: int = 0) -> int:
+    return load().esom_device_status(h, stream)
+
+
+def esom_set_landmark_chunk(h, chunk: int) -> int:
+    return load().esom_set_landmark_chunk(h, chunk)
+
+
+def esom_get_config(h):
+    """Returns (status, dict)."""
+    cfg = _Config()
+    st = load().esom_get_config(h, ctypes.byref(cfg))
+    return st, {name: getattr(cfg, name) for name, _ in _Config._fields_}
+
+
+def esom_destroy(h) -> int:
+    return load().esom_destroy(h)
+
+
+def esom_last_error() -> str:
+    return load().esom_last_error().decode()
+
+
+def status_string(status: int) -> str:
+    return load().esom_status_string(status).decode()
+
+
+def check(status: int) -> None:
+    if status != ESOM_OK:
+        raise EsomError(status, esom_last_error())
+
+
+# --- torch convenience wrapper ----------------------------------------------
+
+class Projector:
+    """A handle for (d, L, k) bound to the current CUDA device."""
+
+    def __init__(self, d: int, L: int, k: int):
+        st, h = esom_create(d, L, k)
+        check(st)
+        self.h, self.d, self.L, self.k = h, d, L, k
+
+    def close(self):
+        if self.h:
+            esom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _stream():
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+
+    def _points(self, X):
+        import torch
+        if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2
+                and X.shape[1] == self.d and X.is_contiguous()):
+            raise ValueError(f"points must be a contiguous CUDA float32 tensor n x {self.d}")
+        return X
+
+    def set_landmarks(self, hi, lo):
+        import torch
+        if hi.shape != (self.L, self.d) or lo.shape != (self.L, 2):
+            raise ValueError("landmark shapes must be L x d and L x 2")
+        if hi.dtype != torch.float32 or lo.dtype != torch.float32:
+            raise ValueError("landmarks must be float32")
+        hi, lo = hi.contiguous(), lo.contiguous()
+        check(esom_set_landmarks(self.h, hi.data_ptr(), lo.data_ptr(), self._stream()))
+        self._keep = (hi, lo)  # alive until the asynchronous copy has run
+
+    def project(self, X, boost: float = 1.0, adjust: float = 1.0, out=None):
+        import torch
+        X = self._points(X)
+        if out is None:
+            out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        check(esom_project(self.h, X.data_ptr(), X.shape[0], out.data_ptr(), boost, adjust,
+                           self._stream()))
+        return out
+
+    def knn(self, X, with_dist: bool = True):
+        import torch
+        X = self._points(X)
+        idx = torch.empty((X.shape[0], self.k), dtype=torch.int32, device=X.device)
+        d2 = (torch.empty((X.shape[0], self.k), dtype=torch.float32, device=X.device)
+              if with_dist else None)
+        check(esom_knn(self.h, X.data_ptr(), X.shape[0], idx.data_ptr(),
+                       d2.data_ptr() if d2 is not None else None, self._stream()))
+        return idx, d2
+
+    def project_host(self, X_host, boost: float = 1.0, adjust: float = 1.0, out_host=None):
+        """Host (CPU) tensors in and out; pinned memory overlaps the copies."""
+        import torch
+        if X_host.is_cuda or X_host.dtype != torch.float32 or not X_host.is_contiguous():
+            raise ValueError("points must be a contiguous CPU float32 tensor")
+        if out_host is None:
+            out_host = torch.empty((X_host.shape[0], 2), dtype=torch.float32,
+                                   pin_memory=X_host.is_pinned())
+        check(esom_project_host(self.h, X_host.data_ptr(), X_host.shape[0],
+                                out_host.data_ptr(), boost, adjust, self._stream()))
+        return out_host
+
+    def device_status(self) -> int:
+        return esom_device_status(self.h, self._stream())
+
+    def set_landmark_chunk(self, chunk: int):
+        check(esom_set_landmark_chunk(self.h, chunk))
+
+    def config(self) -> dict:
+        st, cfg = esom_get_config(self.h)
+        check(st)
+        return cfg

@@ -1,0 +1,387 @@
+// C ABI of libesom (declared in include/esom.h): handles, argument checks,
+// landmark staging, launch configuration and the host-buffer pipeline.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "esom.h"
+#include "esom_kernels.h"
+
+using esom::FusedArgs;
+using esom::KernelOps;
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+esom_status fail(esom_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+esom_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(ESOM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Shared-memory budget for landmarks kept resident in one block.
+constexpr size_t kResidentBytes = 64 * 1024;
+// Per-buffer budget when landmarks are streamed in chunks (two buffers).
+constexpr size_t kChunkBytes = 32 * 1024;
+// Points per chunk of the host-buffer pipeline.
+constexpr long long kHostChunk = 1 << 20;
+
+}  // namespace
+
+struct esom_ctx {
+    int d = 0, L = 0, k = 0, kc = 0, dev = 0;
+    float *hi = nullptr;   // L x d
+    float *lo = nullptr;   // L x 2
+    int *status = nullptr; // device status word
+    uint64_t version = 0;
+    const KernelOps *ops = nullptr;
+    int num_sms = 0;
+    int forced_chunk = 0;
+    // launch configuration (derived from L, d and the chunk choice)
+    int chunk = 0, nchunks = 0, blocks_per_sm = 0;
+    size_t smem = 0;
+    // host-buffer pipeline state (created on first use)
+    float *stage_x[2] = {nullptr, nullptr};
+    float *stage_out[2] = {nullptr, nullptr};
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
+                ev_free[2] = {nullptr, nullptr}, ev_start = nullptr;
+    std::mutex host_mu;
+};
+
+namespace {
+
+esom_status configure(esom_ctx *h) {
+    const size_t row_bytes = (size_t)h->d * sizeof(float);
+    int chunk;
+    if (h->forced_chunk > 0)
+        chunk = h->forced_chunk < h->L ? h->forced_chunk : h->L;
+    else if ((size_t)h->L * row_bytes <= kResidentBytes)
+        chunk = h->L;
+    else
+        chunk = (int)(kChunkBytes / row_bytes);
+    const int nchunks = (h->L + chunk - 1) / chunk;
+    const size_t smem = esom::fused_smem_bytes(h->d, chunk, nchunks);
+    // The attribute belongs to the kernel, shared by all handles: allow the
+    // device's opt-in maximum so no handle can shrink another's limit.
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(shared memory opt-in)");
+    if (smem > (size_t)optin)
+        return fail(ESOM_EUNSUPPORTED, "needs %zu bytes of shared memory per block, device has %d",
+                    smem, optin);
+    e = cudaFuncSetAttribute(h->ops->func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(shared memory)");
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, h->ops->func, esom::kThreads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (bps < 1)
+        return fail(ESOM_EUNSUPPORTED, "launch does not fit on an SM (shared %zu bytes)", smem);
+    h->chunk = chunk;
+    h->nchunks = nchunks;
+    h->smem = smem;
+    h->blocks_per_sm = bps;
+    return ESOM_OK;
+}
+
+esom_status check_device(const esom_ctx *h) {
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (cur != h->dev)
+        return fail(ESOM_EINVAL, "handle belongs to device %d but device %d is current", h->dev,
+                    cur);
+    return ESOM_OK;
+}
+
+esom_status launch(esom_ctx *h, const float *points, long long n, float *out, int *idx,
+                   float *dist2, float boost, float adjust, int mode, cudaStream_t stream) {
+    FusedArgs a;
+    memset(&a, 0, sizeof(a));
+    a.X = points;
+    a.n = n;
+    a.hi = h->hi;
+    a.lo = h->lo;
+    a.L = h->L;
+    a.k = h->k;
+    a.boost = boost;
+    a.adjust = adjust;
+    a.adjust_mode = adjust == 1.0f ? 1 : (adjust == 0.0f ? 2 : 0);
+    a.out = out;
+    a.idx = idx;
+    a.dist2 = dist2;
+    a.mode = mode;
+    a.chunk = h->chunk;
+    a.nchunks = h->nchunks;
+    a.ntiles = (n + esom::kThreads - 1) / esom::kThreads;
+    a.status = h->status;
+    long long grid = (long long)h->blocks_per_sm * h->num_sms;
+    if (grid > a.ntiles) grid = a.ntiles;
+    cudaError_t e = h->ops->launch(a, (int)grid, h->smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return ESOM_OK;
+}
+
+esom_status check_common(esom_ctx *h, const float *points, long long n) {
+    if (!h) return fail(ESOM_EINVAL, "null handle");
+    if (n < 0) return fail(ESOM_EINVAL, "n = %lld < 0", n);
+    if (h->version == 0) return fail(ESOM_ENOLANDMARKS, "esom_set_landmarks has not been called");
+    if (n > 0 && !points) return fail(ESOM_EINVAL, "null points");
+    if (((uintptr_t)points & 15u) != 0)
+        return fail(ESOM_EALIGN, "points must be 16-byte aligned");
+    return check_device(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+esom_status esom_create(int d, int L, int k, esom_handle *out) {
+    if (!out) return fail(ESOM_EINVAL, "null output handle pointer");
+    *out = nullptr;
+    if (d < 1 || d > ESOM_MAX_D) return fail(ESOM_EINVAL, "d = %d outside [1, %d]", d, ESOM_MAX_D);
+    if (d % 4 != 0) return fail(ESOM_EALIGN, "d = %d is not a multiple of 4", d);
+    if (L < 1 || L > ESOM_MAX_L) return fail(ESOM_EINVAL, "L = %d outside [1, %d]", L, ESOM_MAX_L);
+    if (k < 2 || k > L) return fail(ESOM_EINVAL, "k = %d outside [2, L = %d]", k, L);
+    if (k > ESOM_MAX_K) return fail(ESOM_EUNSUPPORTED, "k = %d above %d", k, ESOM_MAX_K);
+    int kc = ((k + 3) / 4) * 4;
+    if (kc < 8) kc = 8;
+    const KernelOps *ops = esom::kernel_ops(d, kc);
+    if (!ops) return fail(ESOM_EUNSUPPORTED, "no kernel for d = %d, k = %d", d, k);
+
+    esom_ctx *h = new (std::nothrow) esom_ctx;
+    if (!h) return fail(ESOM_ENOMEM, "host allocation of the handle failed");
+    h->d = d;
+    h->L = L;
+    h->k = k;
+    h->kc = kc;
+    h->ops = ops;
+    cudaError_t e = cudaGetDevice(&h->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "device query");
+    }
+    e = cudaMalloc(&h->hi, (size_t)L * d * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->lo, (size_t)L * 2 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->status, 256);
+    if (e == cudaSuccess) e = cudaMemset(h->status, 0, 256);
+    if (e != cudaSuccess) {
+        esom_destroy(h);
+        return fail(ESOM_ENOMEM, "device allocation: %s", cudaGetErrorString(e));
+    }
+    esom_status s = configure(h);
+    if (s != ESOM_OK) {
+        esom_destroy(h);
+        return s;
+    }
+    *out = h;
+    return ESOM_OK;
+}
+
+esom_status esom_set_landmarks(esom_handle h, const float *hi, const float *lo,
+                               esom_stream_t stream) {
+    if (!h) return fail(ESOM_EINVAL, "null handle");
+    if (!hi || !lo) return fail(ESOM_EINVAL, "null landmark pointer");
+    esom_status s = check_device(h);
+    if (s != ESOM_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(h->hi, hi, (size_t)h->L * h->d * sizeof(float),
+                                    cudaMemcpyDefault, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->lo, lo, (size_t)h->L * 2 * sizeof(float), cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(e, "landmark copy");
+    ++h->version;
+    return ESOM_OK;
+}
+
+uint64_t esom_landmark_version(esom_handle h) { return h ? h->version : 0; }
+
+esom_status esom_project(esom_handle h, const float *points, int64_t n, float *out, float boost,
+                         float adjust, esom_stream_t stream) {
+    esom_status s = check_common(h, points, n);
+    if (s != ESOM_OK) return s;
+    if (n > 0 && !out) return fail(ESOM_EINVAL, "null out");
+    if (((uintptr_t)out & 7u) != 0) return fail(ESOM_EALIGN, "out must be 8-byte aligned");
+    if (!(boost > 0.0f) || !(boost < INFINITY)) return fail(ESOM_EINVAL, "boost must be > 0");
+    if (!(adjust >= 0.0f) || !(adjust < INFINITY)) return fail(ESOM_EINVAL, "adjust must be >= 0");
+    if (n == 0) return ESOM_OK;
+    return launch(h, points, n, out, nullptr, nullptr, boost, adjust, esom::kProject,
+                  reinterpret_cast<cudaStream_t>(stream));
+}
+
+esom_status esom_knn(esom_handle h, const float *points, int64_t n, int32_t *idx, float *dist2,
+                     esom_stream_t stream) {
+    esom_status s = check_common(h, points, n);
+    if (s != ESOM_OK) return s;
+    if (n > 0 && !idx) return fail(ESOM_EINVAL, "null idx");
+    if (((uintptr_t)idx & 3u) != 0 || ((uintptr_t)dist2 & 3u) != 0)
+        return fail(ESOM_EALIGN, "idx and dist2 must be 4-byte aligned");
+    if (n == 0) return ESOM_OK;
+    return launch(h, points, n, nullptr, idx, dist2, 1.0f, 1.0f, esom::kKnn,
+                  reinterpret_cast<cudaStream_t>(stream));
+}
+
+esom_status esom_project_host(esom_handle h, const float *points_host, int64_t n,
+                              float *out_host, float boost, float adjust, esom_stream_t stream) {
+    if (!h) return fail(ESOM_EINVAL, "null handle");
+    if (n < 0) return fail(ESOM_EINVAL, "n = %lld < 0", (long long)n);
+    if (h->version == 0) return fail(ESOM_ENOLANDMARKS, "esom_set_landmarks has not been called");
+    if (n > 0 && (!points_host || !out_host)) return fail(ESOM_EINVAL, "null host buffer");
+    if (!(boost > 0.0f) || !(boost < INFINITY)) return fail(ESOM_EINVAL, "boost must be > 0");
+    if (!(adjust >= 0.0f) || !(adjust < INFINITY)) return fail(ESOM_EINVAL, "adjust must be >= 0");
+    esom_status s = check_device(h);
+    if (s != ESOM_OK) return s;
+    if (n == 0) return ESOM_OK;
+    std::lock_guard<std::mutex> lock(h->host_mu);
+    cudaError_t e = cudaSuccess;
+    const size_t xbytes = (size_t)kHostChunk * h->d * sizeof(float);
+    const size_t obytes = (size_t)kHostChunk * 2 * sizeof(float);
+    if (!h->stage_x[0]) {
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaMalloc(&h->stage_x[b], xbytes);
+            if (e == cudaSuccess) e = cudaMalloc(&h->stage_out[b], obytes);
+        }
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaEventCreateWithFlags(&h->ev_in[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_comp[b], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_free[b], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(ESOM_ENOMEM, "staging set-up: %s", cudaGetErrorString(e));
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // Order the pipeline after the caller's earlier work on `stream`.
+    e = cudaEventRecord(h->ev_start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_in, h->ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->ev_start, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline ordering");
+    bool used[2] = {false, false};
+    int c = 0;
+    for (long long p0 = 0; p0 < n; p0 += kHostChunk, ++c) {
+        const int b = c & 1;
+        const long long cnt = n - p0 < kHostChunk ? n - p0 : kHostChunk;
+        // input copy waits until the previous result in this buffer left the device
+        if (used[b]) e = cudaStreamWaitEvent(h->s_in, h->ev_free[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->stage_x[b], points_host + p0 * h->d,
+                                (size_t)cnt * h->d * sizeof(float), cudaMemcpyHostToDevice,
+                                h->s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[b], h->s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_in[b], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "host pipeline (input)");
+        s = launch(h, h->stage_x[b], cnt, h->stage_out[b], nullptr, nullptr, boost, adjust,
+                   esom::kProject, st);
+        if (s != ESOM_OK) return s;
+        e = cudaEventRecord(h->ev_comp[b], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->ev_comp[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out_host + p0 * 2, h->stage_out[b], (size_t)cnt * 2 * sizeof(float),
+                                cudaMemcpyDeviceToHost, h->s_out);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_free[b], h->s_out);
+        if (e != cudaSuccess) return cuda_fail(e, "host pipeline (output)");
+        used[b] = true;
+    }
+    // The caller's stream reaches this point only after every result copy.
+    for (int b = 0; b < 2; ++b)
+        if (used[b]) {
+            e = cudaStreamWaitEvent(st, h->ev_free[b], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "host pipeline (join)");
+        }
+    return ESOM_OK;
+}
+
+esom_status esom_device_status(esom_handle h, esom_stream_t stream) {
+    if (!h) return fail(ESOM_EINVAL, "null handle");
+    esom_status s = check_device(h);
+    if (s != ESOM_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int flag = 0;
+    e = cudaMemcpy(&flag, h->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (flag != 0) {
+        e = cudaMemset(h->status, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(e, "status clear");
+        return fail(ESOM_EDEVICE, "device error flags 0x%x (bounded wait ran out)", flag);
+    }
+    return ESOM_OK;
+}
+
+esom_status esom_set_landmark_chunk(esom_handle h, int chunk) {
+    if (!h) return fail(ESOM_EINVAL, "null handle");
+    if (chunk < 0) return fail(ESOM_EINVAL, "chunk = %d < 0", chunk);
+    const int old = h->forced_chunk;
+    h->forced_chunk = chunk;
+    esom_status s = configure(h);
+    if (s != ESOM_OK) {
+        h->forced_chunk = old;
+        configure(h);
+    }
+    return s;
+}
+
+esom_status esom_get_config(esom_handle h, esom_config *cfg) {
+    if (!h || !cfg) return fail(ESOM_EINVAL, "null argument");
+    cfg->d = h->d;
+    cfg->L = h->L;
+    cfg->k = h->k;
+    cfg->kc = h->kc;
+    cfg->threads_per_block = esom::kThreads;
+    cfg->blocks_per_sm = h->blocks_per_sm;
+    cfg->num_sms = h->num_sms;
+    cfg->landmark_chunk = h->chunk;
+    cfg->landmark_chunks = h->nchunks;
+    cfg->shared_bytes = (int)h->smem;
+    return ESOM_OK;
+}
+
+esom_status esom_destroy(esom_handle h) {
+    if (!h) return ESOM_OK;
+    cudaFree(h->hi);
+    cudaFree(h->lo);
+    cudaFree(h->status);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->stage_x[b]);
+        cudaFree(h->stage_out[b]);
+        if (h->ev_in[b]) cudaEventDestroy(h->ev_in[b]);
+        if (h->ev_comp[b]) cudaEventDestroy(h->ev_comp[b]);
+        if (h->ev_free[b]) cudaEventDestroy(h->ev_free[b]);
+    }
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
+    delete h;
+    return ESOM_OK;
+}
+
+const char *esom_last_error(void) { return g_last_error; }
+
+const char *esom_status_string(esom_status s) {
+    switch (s) {
+        case ESOM_OK: return "ESOM_OK";
+        case ESOM_EINVAL: return "ESOM_EINVAL";
+        case ESOM_ENOMEM: return "ESOM_ENOMEM";
+        case ESOM_EALIGN: return "ESOM_EALIGN";
+        case ESOM_ENOLANDMARKS: return "ESOM_ENOLANDMARKS";
+        case ESOM_ECUDA: return "ESOM_ECUDA";
+        case ESOM_EUNSUPPORTED: return "ESOM_EUNSUPPORTED";
+        case ESOM_EDEVICE: return "ESOM_EDEVICE";
+    }
+    return "ESOM_UNKNOWN";
+}
+
+}  // extern "C"

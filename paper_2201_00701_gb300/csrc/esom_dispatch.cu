@@ -1,0 +1,34 @@
+// Maps (D, list capacity) to the kernel instantiation compiled for it.
+#include "esom_kernels.h"
+
+namespace esom {
+
+#define ESOM_DECLARE_D(DV) const KernelOps *kernel_ops_d##DV(int kc);
+ESOM_DECLARE_D(4) ESOM_DECLARE_D(8) ESOM_DECLARE_D(12) ESOM_DECLARE_D(16)
+ESOM_DECLARE_D(20) ESOM_DECLARE_D(24) ESOM_DECLARE_D(28) ESOM_DECLARE_D(32)
+ESOM_DECLARE_D(36) ESOM_DECLARE_D(40) ESOM_DECLARE_D(44) ESOM_DECLARE_D(48)
+ESOM_DECLARE_D(52) ESOM_DECLARE_D(56) ESOM_DECLARE_D(60) ESOM_DECLARE_D(64)
+
+const KernelOps *kernel_ops(int D, int kc) {
+    switch (D) {
+        case 4: return kernel_ops_d4(kc);
+        case 8: return kernel_ops_d8(kc);
+        case 12: return kernel_ops_d12(kc);
+        case 16: return kernel_ops_d16(kc);
+        case 20: return kernel_ops_d20(kc);
+        case 24: return kernel_ops_d24(kc);
+        case 28: return kernel_ops_d28(kc);
+        case 32: return kernel_ops_d32(kc);
+        case 36: return kernel_ops_d36(kc);
+        case 40: return kernel_ops_d40(kc);
+        case 44: return kernel_ops_d44(kc);
+        case 48: return kernel_ops_d48(kc);
+        case 52: return kernel_ops_d52(kc);
+        case 56: return kernel_ops_d56(kc);
+        case 60: return kernel_ops_d60(kc);
+        case 64: return kernel_ops_d64(kc);
+        default: return nullptr;
+    }
+}
+
+}  // namespace esom

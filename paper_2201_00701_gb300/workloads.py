@@ -126,14 +126,18 @@ def mixture10_d8(seed: int = 0, n: int = 10_000) -> Workload:
     return Workload("mixture10_d8", X, hi, lo, k=10, boost=1.0, adjust=1.0)
 
 
-def mixture30_d16(seed: int = 0, n: int = 1_000_000) -> Workload:
+def mixture30_d16(seed: int = 0, n: int = 1_000_000, shard: int = 0) -> Workload:
+    """`shard` > 0 draws a different set of points (same mixture, landmarks
+    and layout), so ranks of a sharded run hold distinct points."""
     s = _streams(seed, 4)
     mix = Mixture(16, 30, s[0], kind="aniso")
     n_out = int(round(0.05 * n))
-    Xm = mix.sample(n - n_out, seed * 1000 + 1)
+    ps = seed * 1000 + 1 + 7919 * shard
+    Xm = mix.sample(n - n_out, ps)
     lo_box, hi_box = Xm.min(axis=0), Xm.max(axis=0)
-    Xo = s[2].uniform(lo_box, hi_box, (n_out, 16)).astype(np.float32)
-    X = np.concatenate([Xm, Xo])[s[3].permutation(n)]
+    t = _streams(ps, 2) if shard else s[2:4]
+    Xo = t[0].uniform(lo_box, hi_box, (n_out, 16)).astype(np.float32)
+    X = np.concatenate([Xm, Xo])[t[1].permutation(n)]
     hi = mix.sample(1024, seed * 1000 + 2)
     lo = grid_layout(1024, s[1])
     return Workload("mixture30_d16", np.ascontiguousarray(X), hi, lo,

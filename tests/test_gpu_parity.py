@@ -1,0 +1,119 @@
+"""CUDA path vs the FP64 oracle on the named workloads (GPU)."""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+from parity import coord_errors, knn_mismatches
+from paper_2201_00701_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def esom():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_00701_gb300 import binding
+    binding.load(build_if_missing=True)
+    return binding
+
+
+def run_gpu(esom, w, chunk=None, knn=True):
+    X = torch.from_numpy(w.X).cuda()
+    with esom.Projector(w.d, w.L, w.k) as P:
+        P.set_landmarks(torch.from_numpy(w.hi).cuda(), torch.from_numpy(w.lo).cuda())
+        if chunk is not None:
+            P.set_landmark_chunk(chunk)
+        out = P.project(X, w.boost, w.adjust)
+        idx = d2 = None
+        if knn:
+            idx, d2 = P.knn(X)
+        torch.cuda.synchronize()
+        assert P.device_status() == 0
+        cfg = P.config()
+    res = (out.cpu().numpy(), None if idx is None else idx.cpu().numpy(),
+           None if d2 is None else d2.cpu().numpy(), cfg)
+    return res
+
+
+def check(w, out, idx, d2, rows=None, label=""):
+    X = w.X if rows is None else w.X[rows]
+    o_out, ratio, _ = oracle.project(X, w.hi, w.lo, w.k, w.boost, w.adjust, diagnostics=True)
+    sel = slice(None) if rows is None else rows
+    stats = coord_errors(out[sel], o_out, ratio, w.extent)
+    if idx is not None:
+        o_idx, o_d2 = oracle.knn(X, w.hi, w.k)
+        nd, ties = knn_mismatches(X, w.hi, idx[sel], d2[sel], o_idx, o_d2)
+        stats.update(knn_rows_differing=nd, knn_tie_swaps=ties)
+    stats["label"] = label
+    print("PARITY", json.dumps(stats))
+    return stats
+
+
+def test_mixture10_d8_full(esom):
+    """n = 10,000, d = 8, L = 100, k = 10: every point (40 tiles, ragged tail)."""
+    w = workloads.mixture10_d8()
+    out, idx, d2, cfg = run_gpu(esom, w)
+    assert cfg["landmark_chunks"] == 1
+    check(w, out, idx, d2, label="mixture10_d8 full")
+
+
+@pytest.mark.parametrize("n", [1, 255, 256, 257, 20_000 + 77])
+def test_mixture30_d16_sizes(esom, n):
+    """d = 16, L = 1024, k = 20 at tile boundaries and a ragged tail."""
+    w = workloads.mixture30_d16(n=max(n, 2000))
+    w.X = np.ascontiguousarray(w.X[:n])
+    out, idx, d2, _ = run_gpu(esom, w)
+    check(w, out, idx, d2, label=f"mixture30_d16 n={n}")
+
+
+def test_mixture30_d16_full_size_sampled(esom):
+    """n = 1,000,000 in the benchmark's launch configuration; 3000 sampled
+    points against the oracle."""
+    w = workloads.mixture30_d16()
+    out, idx, d2, cfg = run_gpu(esom, w)
+    rows = np.sort(np.random.default_rng(7).choice(w.n, 3000, replace=False))
+    check(w, out, idx, d2, rows=rows, label="mixture30_d16 1e6 sampled")
+    assert np.isfinite(out).all()
+
+
+@pytest.mark.parametrize("chunk", [100, 333, 1000])
+def test_chunked_landmarks(esom, chunk):
+    """Landmarks streamed through shared memory in chunks (ragged last chunk)."""
+    w = workloads.mixture30_d16(n=6000)
+    out, idx, d2, cfg = run_gpu(esom, w, chunk=chunk)
+    assert cfg["landmark_chunks"] == -(-w.L // chunk)
+    check(w, out, idx, d2, label=f"chunk={chunk}")
+
+
+def test_uniform_paper_shapes(esom):
+    """The paper's uniform benchmark data (Section 4.1), d = 16 and 32."""
+    for d in (16, 32):
+        w = workloads.uniform(d, n=1 << 20)
+        out, idx, d2, _ = run_gpu(esom, w)
+        rows = np.sort(np.random.default_rng(d).choice(w.n, 2000, replace=False))
+        check(w, out, idx, d2, rows=rows, label=f"uniform d={d}")
+
+
+def test_batch_members(esom):
+    """Eight members of the 64-dataset batch: mixed d, L, k (chunked when the
+    landmarks exceed the resident budget)."""
+    params = workloads.batch64()[:8]
+    for p in params:
+        w = workloads.batch_member(p, n=min(p["n"], 8000))
+        out, idx, d2, cfg = run_gpu(esom, w)
+        check(w, out, idx, d2, label=f"batch {p['index']} d={w.d} L={w.L} k={w.k}")
+
+
+def test_student50_d32_full_size_sampled(esom):
+    """n = 10,000,000, d = 32, L = 4096 (chunked), k = 30; 1500 sampled points."""
+    w = workloads.student50_d32()
+    out, idx, d2, cfg = run_gpu(esom, w, knn=False)
+    assert cfg["landmark_chunks"] > 1
+    rows = np.sort(np.random.default_rng(3).choice(w.n, 1500, replace=False))
+    check(w, out, None, None, rows=rows, label="student50_d32 1e7 sampled")
+    assert np.isfinite(out).all()
