@@ -43,6 +43,7 @@ namespace esom {
 constexpr float kScoreEdge = 10.0f;     // steepness of the k-th-neighbour cut-off
 constexpr float kSigmaEps = 1e-12f;     // spread below this * mean counts as zero
 constexpr double kDetEps = 1e-10;       // det/trace^2 below this: rank-one solve
+constexpr double kDetRecheck = 1e-4;    // FP32 det/trace^2 below this: recompute it
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded mbarrier wait (2 s)
 
 // ---------------------------------------------------------------------------
@@ -124,21 +125,21 @@ __device__ __forceinline__ void issue_copy(void *dst, const void *src, uint32_t 
 
 template <int KC>
 __device__ __forceinline__ void list_insert(float (&sd)[KC], int (&si)[KC], float v, int vi) {
-    // One bubble pass: the new entry moves past every entry it is strictly
-    // smaller than.  Entries arrive in increasing landmark index, so an equal
-    // distance stays behind the earlier (lower-index) entry.
+    // Shift insertion: every slot at or after the new entry's position takes
+    // its predecessor, so existing entries keep their order.  Candidates
+    // arrive in increasing landmark index and go behind every entry of equal
+    // distance, which keeps the list sorted by (distance, index).  All the
+    // comparisons are independent of each other (no chain through the list).
+    bool c[KC];
 #pragma unroll
-    for (int t = 0; t < KC; ++t) {
-        const bool p = v < sd[t];
-        const float lo = p ? v : sd[t];
-        const float hi = p ? sd[t] : v;
-        const int li = p ? vi : si[t];
-        const int hi_i = p ? si[t] : vi;
-        sd[t] = lo;
-        si[t] = li;
-        v = hi;
-        vi = hi_i;
+    for (int t = 0; t < KC; ++t) c[t] = v < sd[t];
+#pragma unroll
+    for (int t = KC - 1; t > 0; --t) {
+        sd[t] = c[t - 1] ? sd[t - 1] : (c[t] ? v : sd[t]);
+        si[t] = c[t - 1] ? si[t - 1] : (c[t] ? vi : si[t]);
     }
+    sd[0] = c[0] ? v : sd[0];
+    si[0] = c[0] ? vi : si[0];
 }
 
 template <int KC>
@@ -218,6 +219,87 @@ __device__ __forceinline__ void scan_chunk(const float4 (&x)[D / 4], const float
 }
 
 // ---------------------------------------------------------------------------
+// Step 3: pair terms over u < v < m.  PASS 0 accumulates the normal system
+// (A, b); PASS 1 accumulates rho = sum w (h.n)^2 / r for a unit 2-D direction
+// n (the Rayleigh quotient n^T A n) and skips the work only PASS 0 needs.
+
+template <int D, int KC, int PASS>
+__device__ __forceinline__ void pair_sums(const float4 (&x)[D / 4], const int (&si)[KC],
+                                          const float (&ss)[KC], int m, const float4 *Lg,
+                                          const float2 *lo2, float2 l0, const FusedArgs &a,
+                                          float nx, float ny, float &A00, float &A01,
+                                          float &A11, float &B0, float &B1, float &rho) {
+#pragma unroll 1
+    for (int u = 0; u < m - 1; ++u) {
+        int iu = si[0];
+        float su = ss[0];
+#pragma unroll
+        for (int t = 1; t < KC; ++t)
+            if (t == u) {
+                iu = si[t];
+                su = ss[t];
+            }
+        const float4 *Lu = Lg + (size_t)iu * (D / 4);
+        float4 lu[D / 4], y[D / 4];
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) {
+            lu[e] = Lu[e];
+            y[e] = make_float4(x[e].x - lu[e].x, x[e].y - lu[e].y, x[e].z - lu[e].z,
+                               x[e].w - lu[e].w);
+        }
+        const float2 lut = __ldg(&lo2[iu]);
+        const float lux = lut.x - l0.x, luy = lut.y - l0.y;  // l_u relative to l_0
+#pragma unroll
+        for (int v = 1; v < KC; ++v) {
+            if (v > u && v < m) {
+                const float4 *Lv = Lg + (size_t)si[v] * (D / 4);
+                float q0 = 0.f, q1 = 0.f, n0 = 0.f, n1 = 0.f;
+#pragma unroll
+                for (int e = 0; e < D / 4; ++e) {
+                    const float4 lv = Lv[e];
+                    const float ex = lv.x - lu[e].x, ey = lv.y - lu[e].y;
+                    const float ez = lv.z - lu[e].z, ew = lv.w - lu[e].w;
+                    q0 = fmaf(ex, ex, q0);
+                    q1 = fmaf(ey, ey, q1);
+                    q0 = fmaf(ez, ez, q0);
+                    q1 = fmaf(ew, ew, q1);
+                    n0 = fmaf(y[e].x, ex, n0);
+                    n1 = fmaf(y[e].y, ey, n1);
+                    n0 = fmaf(y[e].z, ez, n0);
+                    n1 = fmaf(y[e].w, ew, n1);
+                }
+                const float q = q0 + q1, num = n0 + n1;
+                const float2 lvt = __ldg(&lo2[si[v]]);
+                const float hx = lvt.x - lut.x, hy = lvt.y - lut.y;
+                const float r = fmaf(hx, hx, hy * hy);
+                if (q > 0.f && r > 0.f) {
+                    const float Duv = num * __frcp_rn(q);
+                    const float ir = __frcp_rn(r);
+                    float w = su * ss[v];
+                    if (a.adjust_mode == 1)
+                        w *= ir;
+                    else if (a.adjust_mode == 0)
+                        w *= exp2f(-a.adjust * log2f(r));
+                    const float wr = w * ir;
+                    if (PASS == 0) {
+                        const float rhs = fmaf(fmaf(hx, lux, hy * luy), ir, Duv);
+                        A00 = fmaf(wr * hx, hx, A00);
+                        A01 = fmaf(wr * hx, hy, A01);
+                        A11 = fmaf(wr * hy, hy, A11);
+                        const float wrhs = w * rhs;
+                        B0 = fmaf(wrhs, hx, B0);
+                        B1 = fmaf(wrhs, hy, B1);
+                    } else {
+                        const float t = fmaf(hx, nx, hy * ny);
+                        rho = fmaf(wr * t, t, rho);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Steps 2-4 for one point: scores, pair sums, FP64 solve.
 
 template <int D, int KC>
@@ -283,75 +365,35 @@ __device__ __forceinline__ float2 project_point(const float4 (&x)[D / 4], const 
         }
 
     // Step 3: pair terms, u < v < m.
-    float A00 = 0.f, A01 = 0.f, A11 = 0.f, B0 = 0.f, B1 = 0.f;
-#pragma unroll 1
-    for (int u = 0; u < m - 1; ++u) {
-        int iu = si[0];
-        float su = ss[0];
-#pragma unroll
-        for (int t = 1; t < KC; ++t)
-            if (t == u) {
-                iu = si[t];
-                su = ss[t];
-            }
-        const float4 *Lu = Lg + (size_t)iu * (D / 4);
-        float4 lu[D / 4], y[D / 4];
-#pragma unroll
-        for (int e = 0; e < D / 4; ++e) {
-            lu[e] = Lu[e];
-            y[e] = make_float4(x[e].x - lu[e].x, x[e].y - lu[e].y, x[e].z - lu[e].z,
-                               x[e].w - lu[e].w);
-        }
-        const float2 lut = __ldg(&lo2[iu]);
-        const float lux = lut.x - l0.x, luy = lut.y - l0.y;  // l_u relative to l_0
-#pragma unroll
-        for (int v = 1; v < KC; ++v) {
-            if (v > u && v < m) {
-                const float4 *Lv = Lg + (size_t)si[v] * (D / 4);
-                float q0 = 0.f, q1 = 0.f, n0 = 0.f, n1 = 0.f;
-#pragma unroll
-                for (int e = 0; e < D / 4; ++e) {
-                    const float4 lv = Lv[e];
-                    const float ex = lv.x - lu[e].x, ey = lv.y - lu[e].y;
-                    const float ez = lv.z - lu[e].z, ew = lv.w - lu[e].w;
-                    q0 = fmaf(ex, ex, q0);
-                    q1 = fmaf(ey, ey, q1);
-                    q0 = fmaf(ez, ez, q0);
-                    q1 = fmaf(ew, ew, q1);
-                    n0 = fmaf(y[e].x, ex, n0);
-                    n1 = fmaf(y[e].y, ey, n1);
-                    n0 = fmaf(y[e].z, ez, n0);
-                    n1 = fmaf(y[e].w, ew, n1);
-                }
-                const float q = q0 + q1, num = n0 + n1;
-                const float2 lvt = __ldg(&lo2[si[v]]);
-                const float hx = lvt.x - lut.x, hy = lvt.y - lut.y;
-                const float r = fmaf(hx, hx, hy * hy);
-                if (q > 0.f && r > 0.f) {
-                    const float Duv = num * __frcp_rn(q);
-                    const float ir = __frcp_rn(r);
-                    float w = su * ss[v];
-                    if (a.adjust_mode == 1)
-                        w *= ir;
-                    else if (a.adjust_mode == 0)
-                        w *= exp2f(-a.adjust * log2f(r));
-                    const float wr = w * ir;
-                    const float rhs = fmaf(fmaf(hx, lux, hy * luy), ir, Duv);
-                    A00 = fmaf(wr * hx, hx, A00);
-                    A01 = fmaf(wr * hx, hy, A01);
-                    A11 = fmaf(wr * hy, hy, A11);
-                    const float wrhs = w * rhs;
-                    B0 = fmaf(wrhs, hx, B0);
-                    B1 = fmaf(wrhs, hy, B1);
-                }
-            }
-        }
-    }
+    float A00 = 0.f, A01 = 0.f, A11 = 0.f, B0 = 0.f, B1 = 0.f, rho = 0.f;
+    pair_sums<D, KC, 0>(x, si, ss, m, Lg, lo2, l0, a, 0.f, 0.f, A00, A01, A11, B0, B1, rho);
 
     // Step 4: FP64 solve.
     const double a00 = A00, a01 = A01, a11 = A11, b0 = B0, b1 = B1;
-    const double det = a00 * a11 - a01 * a01;
+    double det = a00 * a11 - a01 * a01;
     const double tr = a00 + a11;
+    if (tr > 0.0 && det <= kDetRecheck * tr * tr) {
+        // A00 A11 - A01^2 from FP32 sums cannot resolve det/trace^2 below
+        // ~1e-6.  Recompute the small eigenvalue as the Rayleigh quotient
+        // n^T A n along the minor eigenvector n of the FP32 matrix: a sum of
+        // non-negative terms w (h.n)^2 / r over the pairs, free of
+        // cancellation, and accurate to second order in the error of n.
+        const double disc = sqrt((a00 - a11) * (a00 - a11) + 4.0 * a01 * a01);
+        const double lmax = 0.5 * (tr + disc);
+        // two candidate major eigenvectors; take the better conditioned one
+        const double va0 = a01, va1 = lmax - a00, vb0 = lmax - a11, vb1 = a01;
+        const double na = va0 * va0 + va1 * va1, nb = vb0 * vb0 + vb1 * vb1;
+        const double v0 = na >= nb ? va0 : vb0, v1 = na >= nb ? va1 : vb1;
+        const double nn = sqrt(na >= nb ? na : nb);
+        if (nn > 0.0) {
+            // minor direction: the major one turned by 90 degrees
+            float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f, z4 = 0.f;
+            pair_sums<D, KC, 1>(x, si, ss, m, Lg, lo2, l0, a, (float)(-v1 / nn), (float)(v0 / nn),
+                                z0, z1, z2, z3, z4, rho);
+            const double lmin = (double)rho;
+            det = lmin * (tr - lmin);
+        }
+    }
     double px, py;
     if (det > kDetEps * tr * tr) {
         const double id = 1.0 / det;

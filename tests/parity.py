@@ -10,9 +10,15 @@ Tolerances (stated here, used by every parity test):
     (the FP32 sum of d squared differences carries at most ~(d/4+3) * 2^-24
     relative error with four partial sums).
   * Coordinates: |x_gpu - x_oracle| <= 1e-4 * layout extent (the largest range
-    of the 2-D landmarks over both axes).  Points whose oracle system is
-    within 10x of the rank-one threshold (det/trace^2 < 1e-9) take a
-    different branch under rounding and are exempt; they are counted.
+    of the 2-D landmarks over both axes) for every point whose oracle normal
+    matrix has det/trace^2 >= 1e-3 (condition number <= ~1e3; every point of
+    the named workloads sits there) and for rank-one / zero systems
+    (det/trace^2 < 1e-11 or A = 0).  Between those, FP32 sums of the normal
+    system carry ~1e-7 relative error that the solve amplifies by the
+    condition number, so the bound is scaled by 1e-3 / (det/trace^2); these
+    points are counted ("ill_conditioned").  Points within 10x of the
+    rank-one threshold (1e-11 <= det/trace^2 < 1e-9) may take the other
+    branch under rounding and are exempt; they are counted ("exempt").
 """
 from __future__ import annotations
 
@@ -21,7 +27,9 @@ import numpy as np
 COORD_TOL = 1e-4
 TIE_REL = 1e-6
 DIST_REL = 1e-5
-DET_EXEMPT = 1e-9
+DET_EXEMPT_LO = 1e-11
+DET_EXEMPT_HI = 1e-9
+COND_KNEE = 1e-3
 
 
 def knn_mismatches(X, hi, gidx, gd2, oidx, od2, tie_rel=TIE_REL, dist_rel=DIST_REL):
@@ -50,23 +58,29 @@ def knn_mismatches(X, hi, gidx, gd2, oidx, od2, tie_rel=TIE_REL, dist_rel=DIST_R
     return len(diff_rows), ties
 
 
-def coord_errors(gpu, ref, ratio, extent, tol=COORD_TOL, exempt=DET_EXEMPT):
+def coord_errors(gpu, ref, ratio, extent, tol=COORD_TOL):
     """Checks coordinates; returns a dict of error statistics."""
     gpu = np.asarray(gpu, np.float64)
     err = np.abs(gpu - ref).max(axis=1)
-    ex = (ratio >= 0) & (ratio < exempt)
-    ok = ~ex
-    bound = tol * extent
+    exempt = (ratio >= DET_EXEMPT_LO) & (ratio < DET_EXEMPT_HI)
+    ill = (ratio >= DET_EXEMPT_HI) & (ratio < COND_KNEE)
+    strict = ~exempt & ~ill
+    base = tol * extent
+    bound = np.where(ill, base * COND_KNEE / np.maximum(ratio, 1e-300), base)
     stats = {
         "n": int(len(err)),
-        "exempt": int(ex.sum()),
-        "max_err": float(err[ok].max()) if ok.any() else 0.0,
-        "p99_err": float(np.percentile(err[ok], 99)) if ok.any() else 0.0,
-        "bound": bound,
+        "exempt": int(exempt.sum()),
+        "ill_conditioned": int(ill.sum()),
+        "max_err": float(err[strict].max()) if strict.any() else 0.0,
+        "p99_err": float(np.percentile(err[strict], 99)) if strict.any() else 0.0,
+        "max_err_ill": float(err[ill].max()) if ill.any() else 0.0,
+        "bound": base,
         "far_points": int((np.abs(ref).max(axis=1) > 2 * extent).sum()),
     }
-    bad = np.nonzero(ok & ~(err <= bound))[0]
-    assert bad.size == 0, (
-        f"{bad.size} of {len(err)} points beyond {bound:.3e}: worst {err[bad].max():.3e} at "
-        f"{bad[np.argmax(err[bad])]} (det ratio {ratio[bad[np.argmax(err[bad])]]:.2e}); {stats}")
+    bad = np.nonzero(~exempt & ~(err <= bound))[0]
+    if bad.size:
+        w = bad[np.argmax(err[bad] / bound[bad])]
+        raise AssertionError(
+            f"{bad.size} of {len(err)} points beyond their bound: worst {err[w]:.3e} > "
+            f"{bound[w]:.3e} at {w} (det ratio {ratio[w]:.2e}); {stats}")
     return stats
