@@ -128,6 +128,36 @@ typedef struct {
 
 esom_status esom_get_config(esom_handle h, esom_config *cfg);
 
+/* Projection without any device allocation, for callers that cannot call
+ * cudaMalloc (for example an application whose device memory all belongs to
+ * its own pool allocator, or a frame loop that must not risk the device-wide
+ * synchronisation cudaMalloc/cudaFree can cause).  The paper has no
+ * counterpart: this is a deployment variant of esom_project.
+ *
+ * The caller passes everything esom_create / esom_set_landmarks /
+ * esom_project would take: points (n x d, 16-byte aligned device pointer),
+ * hi (L x d) and lo (L x 2) landmarks (host or device pointers), d, L, k,
+ * out (n x 2, 8-byte aligned device pointer), boost, adjust and the stream.
+ * The function allocates nothing.  Its scratch -- a staged copy of the
+ * landmarks and the kernel's status word -- lives in one fixed
+ * ESOM_NOALLOC_SCRATCH_BYTES array in device memory that every GPU that
+ * loads the library holds until the process exits.  Landmark sets with
+ * L * (d + 2) * 4 + 256 > ESOM_NOALLOC_SCRATCH_BYTES are rejected with
+ * ESOM_EINVAL before anything is queued.
+ *
+ * The first call on a device looks up that device's address of the scratch
+ * array (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture.  Every call shares the one array and leaves its
+ * landmarks there; the status word is cleared at the start of each call.
+ * Calls whose work overlaps on the GPU (on different streams, or from several
+ * host threads) race on the scratch and give undefined results: serialise
+ * them.  Device-side timeouts are recorded in the scratch status word but are
+ * not reported by this call. */
+#define ESOM_NOALLOC_SCRATCH_BYTES (4u << 20)
+esom_status esom_project_noalloc(const float *points, int64_t n, const float *hi,
+                                 const float *lo, int d, int L, int k, float *out,
+                                 float boost, float adjust, esom_stream_t stream);
+
 /* Releases the handle's device buffers.  Pending work on streams that use
  * the handle must have completed. NULL is accepted. */
 esom_status esom_destroy(esom_handle h);

@@ -70,6 +70,7 @@ def load(build_if_missing: bool = False):
         "esom_device_status": ([P, P], I),
         "esom_set_landmark_chunk": ([P, I], I),
         "esom_get_config": ([P, ctypes.POINTER(_Config)], I),
+        "esom_project_noalloc": ([P, I64, P, P, I, I, I, P, F, F, P], I),
         "esom_destroy": ([P], I),
         "esom_last_error": ([], ctypes.c_char_p),
         "esom_status_string": ([I], ctypes.c_char_p),
@@ -135,6 +136,14 @@ def esom_get_config(h):
     cfg = _Config()
     st = load().esom_get_config(h, ctypes.byref(cfg))
     return st, {name: getattr(cfg, name) for name, _ in _Config._fields_}
+
+
+def esom_project_noalloc(points_ptr: int, n: int, hi_ptr: int, lo_ptr: int, d: int, L: int,
+                         k: int, out_ptr: int, boost: float, adjust: float,
+                         stream: int = 0) -> int:
+    """Projection with no device allocation (scratch in a fixed device array)."""
+    return load().esom_project_noalloc(points_ptr, n, hi_ptr, lo_ptr, d, L, k, out_ptr, boost,
+                                       adjust, stream)
 
 
 def esom_destroy(h) -> int:

@@ -38,6 +38,13 @@ constexpr long long kHostChunk = 1 << 20;
 
 }  // namespace
 
+namespace esom {
+int set_error(int s, const char *msg) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+    return s;
+}
+}  // namespace esom
+
 struct esom_ctx {
     int d = 0, L = 0, k = 0, kc = 0, dev = 0;
     float *hi = nullptr;   // L x d

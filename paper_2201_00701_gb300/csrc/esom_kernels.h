@@ -44,6 +44,9 @@ struct KernelOps {
 // Returns the instantiation for dimension D and list capacity kc, or nullptr.
 const KernelOps *kernel_ops(int D, int kc);
 
+// Records `msg` as this host thread's last error message; returns s.
+int set_error(int s, const char *msg);
+
 inline size_t fused_smem_bytes(int D, int chunk, int nchunks) {
     size_t s = kBarrierBytes;
     s += (size_t)kThreads * D * sizeof(float);                    // point tile
