@@ -52,21 +52,24 @@ typedef enum {
  * 2 <= k <= min(L, ESOM_MAX_K); 1 <= L <= ESOM_MAX_L. */
 #define ESOM_MAX_D 64
 #define ESOM_MAX_K 32
-#define ESOM_MAX_L (1 << 24)
+#define ESOM_MAX_L 65536
 
 /* Creates a projection context for points of dimension d, L landmarks and k
  * neighbours (Section 3.1 step 1 requires 3 <= k <= L; k = 2 is accepted as
  * a degenerate case whose result is the nearest landmark's 2-D position).
- * Allocates the device copies of the landmarks and a device status word on
- * the current device.  On success *out receives the handle. */
+ * Allocates the device copies of the landmarks, their squared norms and a
+ * device status word on the current device.  On success *out receives the
+ * handle. */
 esom_status esom_create(int d, int L, int k, esom_handle *out);
 
 /* Copies the landmarks into the handle (Section 3.1: L is g x d, l is g x 2;
  * the paper's g is L here).  hi: L x d float32, lo: L x 2 float32, host or
  * device pointers (copied with cudaMemcpyDefault on `stream`).  The caller
  * keeps ownership and may reuse the buffers once the copy has run on the
- * stream.  Each call increments the landmark version.  Projections queued
- * on other streams are not ordered against this copy by the library. */
+ * stream.  A small kernel on the same stream then computes the landmarks'
+ * squared norms for the screening scan.  Each call increments the landmark
+ * version.  Projections queued on other streams are not ordered against this
+ * copy by the library. */
 esom_status esom_set_landmarks(esom_handle h, const float *hi, const float *lo,
                                esom_stream_t stream);
 
@@ -79,8 +82,11 @@ uint64_t esom_landmark_version(esom_handle h);
  *   boost > 0: sharpness of the distance-to-score map (step 2);
  *   adjust >= 0: pair weight s_u s_v / |l_v - l_u|^(2 adjust); adjust = 1 is
  *     exactly the objective printed in step 4.
- * One fused kernel per call: k-NN in FP32, scores and pair terms in FP32,
- * the 2x2 determinant and solve in FP64. */
+ * One fused kernel per call: k-NN by an FP32 screening scan whose
+ * candidates are re-ranked exactly in FP32 (the k nearest are those of the
+ * FP32 difference-form distance, certified by an error bound), scores and
+ * pair terms in FP32, the 2x2 determinant and solve in FP64.  Inputs whose
+ * squared distances overflow FP32 give unspecified output. */
 esom_status esom_project(esom_handle h, const float *points, int64_t n, float *out,
                          float boost, float adjust, esom_stream_t stream);
 
@@ -109,6 +115,17 @@ esom_status esom_project_host(esom_handle h, const float *points_host, int64_t n
  * that a kernel of this handle raised (a bounded wait on an mbarrier that
  * ran out): ESOM_EDEVICE if one was raised, ESOM_OK otherwise. */
 esom_status esom_device_status(esom_handle h, esom_stream_t stream);
+
+/* Counters kept by a handle's kernels. */
+typedef struct {
+    uint64_t points;    /* points projected or searched */
+    uint64_t rescans;   /* points whose screening certificate failed, so their k
+                           nearest were found by an exact rescan (slower path) */
+} esom_stats;
+
+/* Waits for `stream`, then returns the handle's counters accumulated since
+ * esom_create or the last reset; reset != 0 zeroes them afterwards. */
+esom_status esom_get_stats(esom_handle h, esom_stream_t stream, esom_stats *out, int reset);
 
 /* Forces the number of landmarks per shared-memory chunk (0 restores the
  * automatic choice: all landmarks resident when L*d*4 <= 64 KiB, otherwise
@@ -139,11 +156,12 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg);
  * hi (L x d) and lo (L x 2) landmarks (host or device pointers), d, L, k,
  * out (n x 2, 8-byte aligned device pointer), boost, adjust and the stream.
  * The function allocates nothing.  Its scratch -- a staged copy of the
- * landmarks and the kernel's status word -- lives in one fixed
- * ESOM_NOALLOC_SCRATCH_BYTES array in device memory that every GPU that
- * loads the library holds until the process exits.  Landmark sets with
- * L * (d + 2) * 4 + 256 > ESOM_NOALLOC_SCRATCH_BYTES are rejected with
- * ESOM_EINVAL before anything is queued.
+ * landmarks, their squared norms and the kernel's status word -- lives in
+ * one fixed ESOM_NOALLOC_SCRATCH_BYTES array in device memory that every GPU
+ * that loads the library holds until the process exits.  Landmark sets with
+ * (L * (d + 2) + L rounded up to a multiple of 4) * 4 + 256 bytes above
+ * ESOM_NOALLOC_SCRATCH_BYTES are rejected with ESOM_EINVAL before anything is
+ * queued.
  *
  * The first call on a device looks up that device's address of the scratch
  * array (cudaGetSymbolAddress, with the device current); make that first call

@@ -34,6 +34,10 @@ class EsomError(RuntimeError):
         self.status = status
 
 
+class _Stats(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_uint64), ("rescans", ctypes.c_uint64)]
+
+
 class _Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("d", "L", "k", "kc", "threads_per_block", "blocks_per_sm", "num_sms",
@@ -71,6 +75,7 @@ def load(build_if_missing: bool = False):
         "esom_set_landmark_chunk": ([P, I], I),
         "esom_get_config": ([P, ctypes.POINTER(_Config)], I),
         "esom_project_noalloc": ([P, I64, P, P, I, I, I, P, F, F, P], I),
+        "esom_get_stats": ([P, P, ctypes.POINTER(_Stats), I], I),
         "esom_destroy": ([P], I),
         "esom_last_error": ([], ctypes.c_char_p),
         "esom_status_string": ([I], ctypes.c_char_p),
@@ -136,6 +141,13 @@ def esom_get_config(h):
     cfg = _Config()
     st = load().esom_get_config(h, ctypes.byref(cfg))
     return st, {name: getattr(cfg, name) for name, _ in _Config._fields_}
+
+
+def esom_get_stats(h, stream: int = 0, reset: bool = False):
+    """Returns (status, {"points": ..., "rescans": ...})."""
+    st_ = _Stats()
+    st = load().esom_get_stats(h, stream, ctypes.byref(st_), int(reset))
+    return st, {"points": int(st_.points), "rescans": int(st_.rescans)}
 
 
 def esom_project_noalloc(points_ptr: int, n: int, hi_ptr: int, lo_ptr: int, d: int, L: int,
@@ -245,6 +257,11 @@ class Projector:
 
     def device_status(self) -> int:
         return esom_device_status(self.h, self._stream())
+
+    def stats(self, reset: bool = False) -> dict:
+        st, out = esom_get_stats(self.h, self._stream(), reset)
+        check(st)
+        return out
 
     def set_landmark_chunk(self, chunk: int):
         check(esom_set_landmark_chunk(self.h, chunk))

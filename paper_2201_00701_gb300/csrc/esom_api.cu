@@ -29,10 +29,6 @@ esom_status cuda_fail(cudaError_t e, const char *what) {
     return fail(ESOM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// Shared-memory budget for landmarks kept resident in one block.
-constexpr size_t kResidentBytes = 64 * 1024;
-// Per-buffer budget when landmarks are streamed in chunks (two buffers).
-constexpr size_t kChunkBytes = 32 * 1024;
 // Points per chunk of the host-buffer pipeline.
 constexpr long long kHostChunk = 1 << 20;
 
@@ -43,17 +39,43 @@ int set_error(int s, const char *msg) {
     snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
     return s;
 }
+
+// One thread per landmark: squared norm (FMA chain) and the running maximum
+// of the norms (non-negative floats order like their bit patterns).
+__global__ void landmark_prep_kernel(const float *__restrict__ hi, int L, int D,
+                                     float *__restrict__ norms, float *__restrict__ lmax) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int padded = (L + 3) & ~3;
+    if (j >= padded) return;
+    if (j >= L) {
+        norms[j] = 0.f;
+        return;
+    }
+    float s = 0.f;
+    for (int t = 0; t < D; ++t) s = fmaf(hi[(size_t)j * D + t], hi[(size_t)j * D + t], s);
+    norms[j] = s;
+    atomicMax(reinterpret_cast<int *>(lmax), __float_as_int(sqrtf(s)));
+}
+
+cudaError_t launch_landmark_prep(const float *hi, int L, int D, float *norms, float *lmax,
+                                 cudaStream_t stream) {
+    const int padded = (L + 3) & ~3;
+    landmark_prep_kernel<<<(padded + 255) / 256, 256, 0, stream>>>(hi, L, D, norms, lmax);
+    return cudaGetLastError();
+}
 }  // namespace esom
 
 struct esom_ctx {
     int d = 0, L = 0, k = 0, kc = 0, dev = 0;
     float *hi = nullptr;   // L x d
     float *lo = nullptr;   // L x 2
-    int *status = nullptr; // device status word
+    float *norms = nullptr; // squared landmark norms, padded to a multiple of 4
+    int *status = nullptr; // device status word; the float after it: largest norm
     uint64_t version = 0;
     const KernelOps *ops = nullptr;
     int num_sms = 0;
     int forced_chunk = 0;
+    uint64_t points = 0;   // points handed to the kernels since the last stats reset
     // launch configuration (derived from L, d and the chunk choice)
     int chunk = 0, nchunks = 0, blocks_per_sm = 0;
     size_t smem = 0;
@@ -69,14 +91,7 @@ struct esom_ctx {
 namespace {
 
 esom_status configure(esom_ctx *h) {
-    const size_t row_bytes = (size_t)h->d * sizeof(float);
-    int chunk;
-    if (h->forced_chunk > 0)
-        chunk = h->forced_chunk < h->L ? h->forced_chunk : h->L;
-    else if ((size_t)h->L * row_bytes <= kResidentBytes)
-        chunk = h->L;
-    else
-        chunk = (int)(kChunkBytes / row_bytes);
+    const int chunk = esom::landmark_chunk(h->L, h->d, h->forced_chunk);
     const int nchunks = (h->L + chunk - 1) / chunk;
     const size_t smem = esom::fused_smem_bytes(h->d, chunk, nchunks);
     // The attribute belongs to the kernel, shared by all handles: allow the
@@ -119,6 +134,9 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
     a.n = n;
     a.hi = h->hi;
     a.lo = h->lo;
+    a.norms = h->norms;
+    a.lmax = reinterpret_cast<const float *>(h->status + 1);
+    esom::key_layout(h->L, &a.key_mask, &a.key_quant);
     a.L = h->L;
     a.k = h->k;
     a.boost = boost;
@@ -136,6 +154,7 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
     if (grid > a.ntiles) grid = a.ntiles;
     cudaError_t e = h->ops->launch(a, (int)grid, h->smem, stream);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    h->points += (uint64_t)n;
     return ESOM_OK;
 }
 
@@ -161,8 +180,7 @@ esom_status esom_create(int d, int L, int k, esom_handle *out) {
     if (L < 1 || L > ESOM_MAX_L) return fail(ESOM_EINVAL, "L = %d outside [1, %d]", L, ESOM_MAX_L);
     if (k < 2 || k > L) return fail(ESOM_EINVAL, "k = %d outside [2, L = %d]", k, L);
     if (k > ESOM_MAX_K) return fail(ESOM_EUNSUPPORTED, "k = %d above %d", k, ESOM_MAX_K);
-    int kc = ((k + 3) / 4) * 4;
-    if (kc < 8) kc = 8;
+    const int kc = esom::list_capacity(k);
     const KernelOps *ops = esom::kernel_ops(d, kc);
     if (!ops) return fail(ESOM_EUNSUPPORTED, "no kernel for d = %d, k = %d", d, k);
 
@@ -181,6 +199,7 @@ esom_status esom_create(int d, int L, int k, esom_handle *out) {
     }
     e = cudaMalloc(&h->hi, (size_t)L * d * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->lo, (size_t)L * 2 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->norms, (size_t)((L + 3) & ~3) * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->status, 256);
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, 256);
     if (e != cudaSuccess) {
@@ -207,6 +226,9 @@ esom_status esom_set_landmarks(esom_handle h, const float *hi, const float *lo,
                                     cudaMemcpyDefault, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->lo, lo, (size_t)h->L * 2 * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status + 1, 0, sizeof(float), st);
+    if (e == cudaSuccess) e = esom::launch_landmark_prep(h->hi, h->L, h->d, h->norms,
+                                                         reinterpret_cast<float *>(h->status + 1), st);
     if (e != cudaSuccess) return cuda_fail(e, "landmark copy");
     ++h->version;
     return ESOM_OK;
@@ -328,6 +350,24 @@ esom_status esom_device_status(esom_handle h, esom_stream_t stream) {
     return ESOM_OK;
 }
 
+esom_status esom_get_stats(esom_handle h, esom_stream_t stream, esom_stats *out, int reset) {
+    if (!h || !out) return fail(ESOM_EINVAL, "null argument");
+    esom_status s = check_device(h);
+    if (s != ESOM_OK) return s;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    unsigned words[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(words, h->status, sizeof(words), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "stats read");
+    out->points = h->points;
+    out->rescans = words[2];
+    if (reset) {
+        e = cudaMemset(h->status + 2, 0, sizeof(unsigned));
+        if (e != cudaSuccess) return cuda_fail(e, "stats reset");
+        h->points = 0;
+    }
+    return ESOM_OK;
+}
+
 esom_status esom_set_landmark_chunk(esom_handle h, int chunk) {
     if (!h) return fail(ESOM_EINVAL, "null handle");
     if (chunk < 0) return fail(ESOM_EINVAL, "chunk = %d < 0", chunk);
@@ -360,6 +400,7 @@ esom_status esom_destroy(esom_handle h) {
     if (!h) return ESOM_OK;
     cudaFree(h->hi);
     cudaFree(h->lo);
+    cudaFree(h->norms);
     cudaFree(h->status);
     for (int b = 0; b < 2; ++b) {
         cudaFree(h->stage_x[b]);

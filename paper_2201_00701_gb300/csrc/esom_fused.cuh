@@ -1,7 +1,7 @@
 // Fused EmbedSOM projection kernel for sm_103a (one launch per call).
 //
 // Per point (paper, Section 3.1 steps 1-4; Section 4.2 and 4.3):
-//   1. k-NN over all L landmarks (squared Euclidean, FP32, ties to the lower
+//   1. k-NN over all L landmarks (squared Euclidean, ties to the lower
 //      index).  The paper's GPU k-NN keeps the distances inside one fused
 //      kernel instead of materialising a distance matrix (Section 4.2); so
 //      does this one, and it also fuses the projection step, which the
@@ -18,18 +18,24 @@
 //     over tiles;
 //   * the tile of points is copied global -> shared by one bulk TMA copy
 //     (cp.async.bulk + mbarrier), prefetched one tile ahead;
-//   * the landmarks are copied by bulk TMA into shared memory once per block
-//     when they fit (L*D*4 <= chunk budget), otherwise streamed in chunks
-//     through two shared buffers; every thread reads the same landmark at
-//     the same time, so each shared load is a broadcast;
-//   * the k-NN list lives in registers, sorted, with compile-time capacity
-//     KC >= k; new distances below the current k-th are appended to a small
-//     per-thread queue in shared memory and merged into the list in
-//     warp-uniform flushes, so the insertion network runs in lock-step;
-//   * scores and the pair sums run in FP32 registers, with the 2-D landmark
-//     coordinates taken relative to the nearest neighbour's (the fit is
-//     shift-equivariant) to keep the FP32 sums small; only the determinant
-//     and the solve are FP64.
+//   * the landmarks (rows and squared norms) are copied by bulk TMA into
+//     shared memory once per block when they fit, otherwise streamed in
+//     chunks through two shared buffers; every thread reads the same
+//     landmark at the same time, so each shared load is a broadcast;
+//   * screening scan: |x|^2 + |l|^2 - 2 x.l in FP32 (one FMA per element),
+//     packed with the landmark index into one 32-bit key (index in the low
+//     mantissa bits), kept in a sorted register list of KC = k + spare
+//     entries; keys below the current threshold go to a per-thread queue in
+//     shared memory and are merged in warp-uniform flushes with a min/max
+//     insertion (two instructions a slot, no chain through the list);
+//   * exact re-rank: the listed candidates get their squared distance in the
+//     FP32 difference form, are ordered by (distance, index), and a bound on
+//     the screening error certifies that no landmark outside the list can
+//     enter the k nearest; a point that fails the certificate is rescanned
+//     exactly on its own;
+//   * scores and the pair sums in FP32 registers (D_uv from the law of
+//     cosines on the exact squared distances), 2-D coordinates relative to
+//     the nearest neighbour's; only the determinant and the solve in FP64.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,6 +51,7 @@ constexpr float kSigmaEps = 1e-12f;     // spread below this * mean counts as ze
 constexpr double kDetEps = 1e-10;       // det/trace^2 below this: rank-one solve
 constexpr double kDetRecheck = 1e-4;    // FP32 det/trace^2 below this: recompute it
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded mbarrier wait (2 s)
+constexpr float kU = 5.9604645e-8f;     // 2^-24, unit roundoff of FP32
 
 // ---------------------------------------------------------------------------
 // mbarrier and bulk-copy helpers (inline PTX).
@@ -108,11 +115,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
-// Issues the bulk copy of `bytes` into `dst` and arms `bar` for it; large
-// copies are split into pieces below the mbarrier transaction limit.
-__device__ __forceinline__ void issue_copy(void *dst, const void *src, uint32_t bytes,
-                                           uint64_t *bar) {
-    mbar_expect_tx(bar, bytes);
+// Bulk copy of `bytes` into `dst`, split below the mbarrier transaction
+// limit; the caller has armed `bar` for the total.
+__device__ __forceinline__ void copy_pieces(void *dst, const void *src, uint32_t bytes,
+                                            uint64_t *bar) {
     const uint32_t piece = 1u << 16;
     for (uint32_t off = 0; off < bytes; off += piece) {
         const uint32_t b = bytes - off < piece ? bytes - off : piece;
@@ -121,55 +127,80 @@ __device__ __forceinline__ void issue_copy(void *dst, const void *src, uint32_t 
 }
 
 // ---------------------------------------------------------------------------
-// Register-resident sorted k-NN list.
+// Screening keys: a 32-bit pattern whose high bits are the FP32 screening
+// value and whose low `b` bits are the landmark index.  Read back as a float
+// it is the value with its low mantissa bits replaced, so keys of different
+// landmarks never tie and float min/max order them by value up to a
+// relative perturbation below 2^(b-23).
 
-template <int KC>
-__device__ __forceinline__ void list_insert(float (&sd)[KC], int (&si)[KC], float v, int vi) {
-    // Shift insertion: every slot at or after the new entry's position takes
-    // its predecessor, so existing entries keep their order.  Candidates
-    // arrive in increasing landmark index and go behind every entry of equal
-    // distance, which keeps the list sorted by (distance, index).  All the
-    // comparisons are independent of each other (no chain through the list).
-    bool c[KC];
-#pragma unroll
-    for (int t = 0; t < KC; ++t) c[t] = v < sd[t];
-#pragma unroll
-    for (int t = KC - 1; t > 0; --t) {
-        sd[t] = c[t - 1] ? sd[t - 1] : (c[t] ? v : sd[t]);
-        si[t] = c[t - 1] ? si[t - 1] : (c[t] ? vi : si[t]);
-    }
-    sd[0] = c[0] ? v : sd[0];
-    si[0] = c[0] ? vi : si[0];
+__device__ __forceinline__ float make_key(float value, uint32_t j, uint32_t mask) {
+    return __uint_as_float((__float_as_uint(value) & ~mask) | j);
 }
 
+// Sorted key list: inserting v gives slot t the value
+// max(list[t-1], min(v, list[t])) -- shift when v is smaller than list[t-1],
+// v at its place, unchanged after.  Every slot uses only old values.
 template <int KC>
-__device__ __forceinline__ float list_at(const float (&a)[KC], int pos) {
+__device__ __forceinline__ void key_insert(float (&keys)[KC], float v) {
+    float prev = keys[0];
+    keys[0] = fminf(v, keys[0]);
+#pragma unroll
+    for (int t = 1; t < KC; ++t) {
+        const float cur = keys[t];
+        keys[t] = fmaxf(prev, fminf(v, cur));
+        prev = cur;
+    }
+}
+
+// Batcher's odd-even merge sort network for any N, as a compile-time list of
+// compare-exchange pairs, so that the unrolled loop indexes registers only.
+template <int N>
+struct SortNetwork {
+    int lo[320], hi[320], count;
+    constexpr SortNetwork() : lo(), hi(), count(0) {
+        for (int p = 1; p < N; p += p)
+            for (int k = p; k > 0; k /= 2)
+                for (int j = k % p; j + k < N; j += k + k)
+                    for (int i = 0; i < k; ++i)
+                        if (i + j + k < N && (i + j) / (p + p) == (i + j + k) / (p + p)) {
+                            lo[count] = i + j;
+                            hi[count] = i + j + k;
+                            ++count;
+                        }
+    }
+};
+
+template <int N>
+__device__ __forceinline__ void key_sort(float (&a)[N]) {
+    constexpr SortNetwork<N> net{};
+    static_assert(net.count <= 320, "sorting network table too small");
+#pragma unroll
+    for (int c = 0; c < net.count; ++c) {
+        const float x = a[net.lo[c]], y = a[net.hi[c]];
+        a[net.lo[c]] = fminf(x, y);
+        a[net.hi[c]] = fmaxf(x, y);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ float at(const float (&a)[N], int pos) {
     float r = a[0];
 #pragma unroll
-    for (int t = 1; t < KC; ++t)
+    for (int t = 1; t < N; ++t)
         if (t == pos) r = a[t];
     return r;
 }
 
-// Merges this thread's queued candidates into its list; the warp runs as
-// many insertion rounds as its fullest queue needs.
-template <int KC>
-__device__ __forceinline__ void queue_flush(float (&sd)[KC], int (&si)[KC], int &qn, float &thr,
-                                            const float *qd, const int *qi, int tid, int k) {
-    const int mx = __reduce_max_sync(0xffffffffu, qn);
-    for (int i = 0; i < mx; ++i) {
-        float v = INFINITY;
-        int vi = 0;
-        if (i < qn) {
-            v = qd[i * kThreads + tid];
-            vi = qi[i * kThreads + tid];
-        }
-        list_insert<KC>(sd, si, v, vi);
-    }
-    qn = 0;
-    thr = list_at<KC>(sd, k - 1);
+// Threshold for queueing: a key at or above it cannot belong to the k
+// nearest.  g is the k-th key's value widened by its quantisation; the
+// screening/exact distance gap M is allowed on both sides.
+__device__ __forceinline__ float push_threshold(float kth, float M, float q) {
+    const float g = kth + 2.f * q * fabsf(kth);
+    return g + 2.f * M + 4.f * q * (fabsf(g) + 2.f * M) + 1e-30f;
 }
 
+// Squared distance in the FP32 difference form with four partial sums (the
+// exact distance that is reported and ranked).
 template <int D>
 __device__ __forceinline__ float dist2_row(const float4 (&x)[D / 4], const float4 *l) {
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -186,74 +217,200 @@ __device__ __forceinline__ float dist2_row(const float4 (&x)[D / 4], const float
     return (a0 + a1) + (a2 + a3);
 }
 
-// Scans `cnt` landmarks of one shared-memory chunk (global indices base..).
+// Screening value |x|^2 + |l|^2 - 2 x.l, accumulated as
+// -2 (-(|x|^2 + |l|^2)/2 + x.l) in one FMA chain (hxx = -|x|^2/2; the
+// scalings by -1/2 and -2 are exact).
+template <int D>
+__device__ __forceinline__ float screen_row(const float4 (&x)[D / 4], float hxx, float ll,
+                                            const float4 *l) {
+    float a = fmaf(-0.5f, ll, hxx);
+#pragma unroll
+    for (int e = 0; e < D / 4; ++e) {
+        const float4 q = l[e];
+        a = fmaf(x[e].x, q.x, a);
+        a = fmaf(x[e].y, q.y, a);
+        a = fmaf(x[e].z, q.z, a);
+        a = fmaf(x[e].w, q.w, a);
+    }
+    return -2.f * a;
+}
+
+struct ScanState {
+    int qn;        // queued keys of this thread
+    float thr;     // push threshold
+};
+
+template <int KC>
+__device__ __forceinline__ void queue_flush(float (&keys)[KC], ScanState &st, const uint32_t *qk,
+                                            int tid, int k, float M, float q) {
+    const int mx = __reduce_max_sync(0xffffffffu, st.qn);
+    for (int i = 0; i < mx; ++i) {
+        const float v = i < st.qn ? __uint_as_float(qk[i * kThreads + tid]) : INFINITY;
+        key_insert<KC>(keys, v);
+    }
+    st.qn = 0;
+    st.thr = push_threshold(at<KC>(keys, k - 1), M, q);
+}
+
+// Screens landmarks j_begin..cnt-1 of one shared-memory chunk (global
+// indices base + j).
 template <int D, int KC>
-__device__ __forceinline__ void scan_chunk(const float4 (&x)[D / 4], const float *Lc, int cnt,
-                                           int base, float (&sd)[KC], int (&si)[KC], int &qn,
-                                           float &thr, float *qd, int *qi, int tid, int k) {
+__device__ __forceinline__ void scan_chunk(const float4 (&x)[D / 4], float hxx, const float *Lc,
+                                           const float *Nc, int j_begin, int cnt, int base,
+                                           uint32_t mask, float (&keys)[KC], ScanState &st,
+                                           uint32_t *qk, int tid, int k, float M, float q) {
     const float4 *L4 = reinterpret_cast<const float4 *>(Lc);
-    for (int j0 = 0; j0 < cnt; j0 += kCheck) {
+    for (int j0 = j_begin; j0 < cnt; j0 += kCheck) {
         if (j0 + kCheck <= cnt) {
 #pragma unroll
             for (int jj = 0; jj < kCheck; ++jj) {
-                const float d2 = dist2_row<D>(x, L4 + (size_t)(j0 + jj) * (D / 4));
-                if (d2 < thr) {
-                    qd[qn * kThreads + tid] = d2;
-                    qi[qn * kThreads + tid] = base + j0 + jj;
-                    ++qn;
+                const int j = j0 + jj;
+                const float v = screen_row<D>(x, hxx, Nc[j], L4 + (size_t)j * (D / 4));
+                const float key = make_key(v, (uint32_t)(base + j), mask);
+                if (key < st.thr) {
+                    qk[st.qn * kThreads + tid] = __float_as_uint(key);
+                    ++st.qn;
                 }
             }
         } else {
             for (int j = j0; j < cnt; ++j) {
-                const float d2 = dist2_row<D>(x, L4 + (size_t)j * (D / 4));
-                if (d2 < thr) {
-                    qd[qn * kThreads + tid] = d2;
-                    qi[qn * kThreads + tid] = base + j;
-                    ++qn;
+                const float v = screen_row<D>(x, hxx, Nc[j], L4 + (size_t)j * (D / 4));
+                const float key = make_key(v, (uint32_t)(base + j), mask);
+                if (key < st.thr) {
+                    qk[st.qn * kThreads + tid] = __float_as_uint(key);
+                    ++st.qn;
                 }
             }
         }
-        if (__any_sync(0xffffffffu, qn > kQueue - kCheck))
-            queue_flush<KC>(sd, si, qn, thr, qd, qi, tid, k);
+        if (__any_sync(0xffffffffu, st.qn > kQueue - kCheck))
+            queue_flush<KC>(keys, st, qk, tid, k, M, q);
     }
+}
+
+// Exact k-NN of one point by a plain scan (the rare path when the screening
+// certificate fails): difference-form distances, stable shift insertion.
+template <int D, int KK>
+__device__ __forceinline__ void exact_rescan(const float4 (&x)[D / 4], const float4 *Lg, int L,
+                                          float (&ed)[KK], int (&ei)[KK]) {
+#pragma unroll
+    for (int t = 0; t < KK; ++t) {
+        ed[t] = INFINITY;
+        ei[t] = 0;
+    }
+    for (int j = 0; j < L; ++j) {
+        const float d2 = dist2_row<D>(x, Lg + (size_t)j * (D / 4));
+        if (d2 < ed[KK - 1]) {
+            bool c[KK];
+#pragma unroll
+            for (int t = 0; t < KK; ++t) c[t] = d2 < ed[t];
+#pragma unroll
+            for (int t = KK - 1; t > 0; --t) {
+                ed[t] = c[t - 1] ? ed[t - 1] : (c[t] ? d2 : ed[t]);
+                ei[t] = c[t - 1] ? ei[t - 1] : (c[t] ? j : ei[t]);
+            }
+            if (c[0]) {
+                ed[0] = d2;
+                ei[0] = j;
+            }
+        }
+    }
+}
+
+// Exact re-rank of the screened list.  On return ed/ei hold the KK nearest
+// listed candidates by (FP32 difference-form distance, index); returns false
+// if the screening certificate fails (then the caller rescans).
+template <int D, int KC, int KK>
+__device__ __forceinline__ bool rerank(const float4 (&x)[D / 4], const float (&keys)[KC],
+                                       const float4 *Lg, uint32_t mask, int L, int k, float M,
+                                       float q, float (&ed)[KK], int (&ei)[KK]) {
+    float cd[KC];
+    int ci[KC];
+#pragma unroll
+    for (int t = 0; t < KC; ++t) {
+        const bool valid = keys[t] < INFINITY;
+        // (the min() only guards the row read; listed keys carry indices < L)
+        ci[t] = valid ? min((int)(__float_as_uint(keys[t]) & mask), L - 1) : 0;
+        cd[t] = valid ? dist2_row<D>(x, Lg + (size_t)ci[t] * (D / 4)) : INFINITY;
+    }
+    // The screened order is the exact order except near ties; repair with
+    // odd-even transposition passes on (distance, index) until sorted.
+    bool sorted = true;
+#pragma unroll
+    for (int t = 0; t + 1 < KC; ++t)
+        sorted = sorted && !(cd[t + 1] < cd[t] || (cd[t + 1] == cd[t] && ci[t + 1] < ci[t]));
+    for (int pass = 0; pass < KC && __any_sync(0xffffffffu, !sorted); ++pass) {
+#pragma unroll
+        for (int t = 0; t + 1 < KC; ++t) {
+            if ((t & 1) != (pass & 1)) continue;
+            const bool sw = cd[t + 1] < cd[t] || (cd[t + 1] == cd[t] && ci[t + 1] < ci[t]);
+            const float d0 = cd[t], d1 = cd[t + 1];
+            const int i0 = ci[t], i1 = ci[t + 1];
+            cd[t] = sw ? d1 : d0;
+            cd[t + 1] = sw ? d0 : d1;
+            ci[t] = sw ? i1 : i0;
+            ci[t + 1] = sw ? i0 : i1;
+        }
+        sorted = true;
+#pragma unroll
+        for (int t = 0; t + 1 < KC; ++t)
+            sorted = sorted && !(cd[t + 1] < cd[t] || (cd[t + 1] == cd[t] && ci[t + 1] < ci[t]));
+    }
+#pragma unroll
+    for (int t = 0; t < KK; ++t) {
+        ed[t] = cd[t];
+        ei[t] = ci[t];
+    }
+    // Every landmark left out has a key >= the last key in the list (or was
+    // never queued, which push_threshold covers), so its exact distance is at
+    // least last - 2q|last| - M.
+    const float last = keys[KC - 1];
+    if (!(last < INFINITY)) return true;
+    const float exact_k = at<KC>(cd, k - 1);
+    return last - 2.f * q * fabsf(last) - M > exact_k;
+}
+
+// Neighbour indices parked in this thread's own column of the queue buffer
+// (32-bit words col[i * kThreads]; word i holds ranks 2i and 2i+1 as 16-bit
+// halves), so no other thread's words are touched.
+__device__ __forceinline__ int nb_at(const uint32_t *col, int t) {
+    return (int)((col[(t >> 1) * kThreads] >> ((t & 1) * 16)) & 0xFFFFu);
 }
 
 // ---------------------------------------------------------------------------
 // Step 3: pair terms over u < v < m.  PASS 0 accumulates the normal system
 // (A, b); PASS 1 accumulates rho = sum w (h.n)^2 / r for a unit 2-D direction
 // n (the Rayleigh quotient n^T A n) and skips the work only PASS 0 needs.
+// D_uv uses the law of cosines on the exact squared distances:
+// <X - L_u, L_v - L_u> = (|X - L_u|^2 + |L_v - L_u|^2 - |X - L_v|^2) / 2.
 
-template <int D, int KC, int PASS>
-__device__ __forceinline__ void pair_sums(const float4 (&x)[D / 4], const int (&si)[KC],
-                                          const float (&ss)[KC], int m, const float4 *Lg,
+template <int D, int KK, int PASS>
+__device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t *nb,
+                                          const float (&ss)[KK], int m, const float4 *Lg,
                                           const float2 *lo2, float2 l0, const FusedArgs &a,
                                           float nx, float ny, float &A00, float &A01,
                                           float &A11, float &B0, float &B1, float &rho) {
 #pragma unroll 1
     for (int u = 0; u < m - 1; ++u) {
-        int iu = si[0];
-        float su = ss[0];
+        const int iu = nb_at(nb, u);
+        float su = ss[0], du = sd[0];
 #pragma unroll
-        for (int t = 1; t < KC; ++t)
+        for (int t = 1; t < KK; ++t)
             if (t == u) {
-                iu = si[t];
                 su = ss[t];
+                du = sd[t];
             }
         const float4 *Lu = Lg + (size_t)iu * (D / 4);
-        float4 lu[D / 4], y[D / 4];
+        float4 lu[D / 4];
 #pragma unroll
-        for (int e = 0; e < D / 4; ++e) {
-            lu[e] = Lu[e];
-            y[e] = make_float4(x[e].x - lu[e].x, x[e].y - lu[e].y, x[e].z - lu[e].z,
-                               x[e].w - lu[e].w);
-        }
+        for (int e = 0; e < D / 4; ++e) lu[e] = Lu[e];
         const float2 lut = __ldg(&lo2[iu]);
         const float lux = lut.x - l0.x, luy = lut.y - l0.y;  // l_u relative to l_0
 #pragma unroll
-        for (int v = 1; v < KC; ++v) {
+        for (int v = 1; v < KK; ++v) {
             if (v > u && v < m) {
-                const float4 *Lv = Lg + (size_t)si[v] * (D / 4);
-                float q0 = 0.f, q1 = 0.f, n0 = 0.f, n1 = 0.f;
+                const int iv = nb_at(nb, v);
+                const float4 *Lv = Lg + (size_t)iv * (D / 4);
+                float q0 = 0.f, q1 = 0.f;
 #pragma unroll
                 for (int e = 0; e < D / 4; ++e) {
                     const float4 lv = Lv[e];
@@ -263,17 +420,12 @@ __device__ __forceinline__ void pair_sums(const float4 (&x)[D / 4], const int (&
                     q1 = fmaf(ey, ey, q1);
                     q0 = fmaf(ez, ez, q0);
                     q1 = fmaf(ew, ew, q1);
-                    n0 = fmaf(y[e].x, ex, n0);
-                    n1 = fmaf(y[e].y, ey, n1);
-                    n0 = fmaf(y[e].z, ez, n0);
-                    n1 = fmaf(y[e].w, ew, n1);
                 }
-                const float q = q0 + q1, num = n0 + n1;
-                const float2 lvt = __ldg(&lo2[si[v]]);
+                const float qq = q0 + q1;
+                const float2 lvt = __ldg(&lo2[iv]);
                 const float hx = lvt.x - lut.x, hy = lvt.y - lut.y;
                 const float r = fmaf(hx, hx, hy * hy);
-                if (q > 0.f && r > 0.f) {
-                    const float Duv = num * __frcp_rn(q);
+                if (qq > 0.f && r > 0.f) {
                     const float ir = __frcp_rn(r);
                     float w = su * ss[v];
                     if (a.adjust_mode == 1)
@@ -282,6 +434,7 @@ __device__ __forceinline__ void pair_sums(const float4 (&x)[D / 4], const int (&
                         w *= exp2f(-a.adjust * log2f(r));
                     const float wr = w * ir;
                     if (PASS == 0) {
+                        const float Duv = 0.5f * (du - sd[v] + qq) * __frcp_rn(qq);
                         const float rhs = fmaf(fmaf(hx, lux, hy * luy), ir, Duv);
                         A00 = fmaf(wr * hx, hx, A00);
                         A01 = fmaf(wr * hx, hy, A01);
@@ -299,25 +452,37 @@ __device__ __forceinline__ void pair_sums(const float4 (&x)[D / 4], const int (&
     }
 }
 
-// ---------------------------------------------------------------------------
-// Steps 2-4 for one point: scores, pair sums, FP64 solve.
+template <int D, int KK>
+__device__ __forceinline__ float minor_rayleigh(const float (&sd)[KK], const uint32_t *nb,
+                                             const float (&ss)[KK], int m, const float4 *Lg,
+                                             const float2 *lo2, float2 l0, const FusedArgs &a,
+                                             float nx, float ny) {
+    float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f, z4 = 0.f, rho = 0.f;
+    pair_sums<D, KK, 1>(sd, nb, ss, m, Lg, lo2, l0, a, nx, ny, z0, z1, z2, z3, z4, rho);
+    return rho;
+}
 
-template <int D, int KC>
-__device__ __forceinline__ float2 project_point(const float4 (&x)[D / 4], const float (&sd)[KC],
-                                                const int (&si)[KC], const float4 *Lg,
-                                                const float2 *lo2, const FusedArgs &a) {
+// ---------------------------------------------------------------------------
+// Steps 2-4 for one point: scores, pair sums, FP64 solve.  sd holds the
+// exact squared distances of the k nearest; their landmark indices are in
+// this thread's column of shared memory (nb_at(nb, t) for rank t).
+
+template <int D, int KK>
+__device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uint32_t *nb,
+                                                const float4 *Lg, const float2 *lo2,
+                                                const FusedArgs &a) {
     const int k = a.k, m = k - 1;
 
     // Step 2: scores.  Distances are Euclidean; the weights of the mean and
     // spread are 1/i over the m scored neighbours.  exp(boost (d_1 - d_i) /
     // sigma) differs from exp(boost (mean - d_i) / sigma) by one common
     // factor, which cancels in the solve, and it cannot overflow.
-    float del[KC];
+    float del[KK];
 #pragma unroll
-    for (int t = 0; t < KC; ++t) del[t] = sqrtf(sd[t]);
+    for (int t = 0; t < KK; ++t) del[t] = sqrtf(sd[t]);
     float wsum = 0.f, mean = 0.f;
 #pragma unroll
-    for (int t = 0; t < KC; ++t)
+    for (int t = 0; t < KK; ++t)
         if (t < m) {
             const float w = 1.0f / (float)(t + 1);
             wsum += w;
@@ -326,20 +491,20 @@ __device__ __forceinline__ float2 project_point(const float4 (&x)[D / 4], const 
     mean /= wsum;
     float var = 0.f;
 #pragma unroll
-    for (int t = 0; t < KC; ++t)
+    for (int t = 0; t < KK; ++t)
         if (t < m) {
             const float w = 1.0f / (float)(t + 1);
             const float dd = del[t] - mean;
             var = fmaf(w * dd, dd, var);
         }
     const float sigma = sqrtf(var / wsum);
-    const float dk = list_at<KC>(del, k - 1);
+    const float dk = at<KK>(del, k - 1);
     const bool flat = sigma <= kSigmaEps * fmaxf(mean, 1e-30f);
     const float inv_sigma = flat ? 0.f : a.boost / sigma;
     const float inv_dk = dk > 0.f ? 1.0f / dk : 0.f;
-    float ss[KC];
+    float ss[KK];
 #pragma unroll
-    for (int t = 0; t < KC; ++t) {
+    for (int t = 0; t < KK; ++t) {
         float s = 0.f;
         if (t < m) {
             const float f1 = flat ? 1.f : expf((del[0] - del[t]) * inv_sigma);
@@ -350,12 +515,12 @@ __device__ __forceinline__ float2 project_point(const float4 (&x)[D / 4], const 
     }
 
     // 2-D coordinates relative to the nearest neighbour's.
-    const float2 l0 = __ldg(&lo2[si[0]]);
+    const float2 l0 = __ldg(&lo2[nb_at(nb, 0)]);
     float C0 = 0.f, C1 = 0.f, Ssum = 0.f, M0 = 0.f, M1 = 0.f;
 #pragma unroll
-    for (int t = 0; t < KC; ++t)
+    for (int t = 0; t < KK; ++t)
         if (t < m) {
-            const float2 lt = __ldg(&lo2[si[t]]);
+            const float2 lt = __ldg(&lo2[nb_at(nb, t)]);
             const float px = lt.x - l0.x, py = lt.y - l0.y;
             C0 = fmaf(ss[t], px, C0);
             C1 = fmaf(ss[t], py, C1);
@@ -366,7 +531,7 @@ __device__ __forceinline__ float2 project_point(const float4 (&x)[D / 4], const 
 
     // Step 3: pair terms, u < v < m.
     float A00 = 0.f, A01 = 0.f, A11 = 0.f, B0 = 0.f, B1 = 0.f, rho = 0.f;
-    pair_sums<D, KC, 0>(x, si, ss, m, Lg, lo2, l0, a, 0.f, 0.f, A00, A01, A11, B0, B1, rho);
+    pair_sums<D, KK, 0>(sd, nb, ss, m, Lg, lo2, l0, a, 0.f, 0.f, A00, A01, A11, B0, B1, rho);
 
     // Step 4: FP64 solve.
     const double a00 = A00, a01 = A01, a11 = A11, b0 = B0, b1 = B1;
@@ -382,15 +547,13 @@ __device__ __forceinline__ float2 project_point(const float4 (&x)[D / 4], const 
         const double lmax = 0.5 * (tr + disc);
         // two candidate major eigenvectors; take the better conditioned one
         const double va0 = a01, va1 = lmax - a00, vb0 = lmax - a11, vb1 = a01;
-        const double na = va0 * va0 + va1 * va1, nb = vb0 * vb0 + vb1 * vb1;
-        const double v0 = na >= nb ? va0 : vb0, v1 = na >= nb ? va1 : vb1;
-        const double nn = sqrt(na >= nb ? na : nb);
+        const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
+        const double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
+        const double nn = sqrt(ga >= gb ? ga : gb);
         if (nn > 0.0) {
             // minor direction: the major one turned by 90 degrees
-            float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f, z4 = 0.f;
-            pair_sums<D, KC, 1>(x, si, ss, m, Lg, lo2, l0, a, (float)(-v1 / nn), (float)(v0 / nn),
-                                z0, z1, z2, z3, z4, rho);
-            const double lmin = (double)rho;
+            const double lmin = (double)minor_rayleigh<D, KK>(
+                sd, nb, ss, m, Lg, lo2, l0, a, (float)(-v1 / nn), (float)(v0 / nn));
             det = lmin * (tr - lmin);
         }
     }
@@ -417,9 +580,9 @@ __device__ __forceinline__ float2 project_point(const float4 (&x)[D / 4], const 
             const double disc = sqrt((a00 - a11) * (a00 - a11) + 4.0 * a01 * a01);
             const double lam = 0.5 * (tr + disc);
             double va0 = a01, va1 = lam - a00, vb0 = lam - a11, vb1 = a01;
-            const double na = va0 * va0 + va1 * va1, nb = vb0 * vb0 + vb1 * vb1;
-            double v0 = na >= nb ? va0 : vb0, v1 = na >= nb ? va1 : vb1;
-            double nn = na >= nb ? na : nb;
+            const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
+            double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
+            double nn = ga >= gb ? ga : gb;
             if (nn == 0.0) {
                 v0 = 1.0;
                 v1 = 0.0;
@@ -443,15 +606,18 @@ __device__ __forceinline__ float2 project_point(const float4 (&x)[D / 4], const 
 template <int D, int KC, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a) {
     static_assert(D % 4 == 0 && D >= 4 && D <= 64, "D must be a multiple of 4 in [4, 64]");
-    static_assert(KC >= 2 && KC <= 32, "list capacity out of range");
+    static_assert(KC >= 8 && KC <= 36 && KC % 4 == 0, "list capacity out of range");
+    static_assert((KC - 4) / 2 <= kQueue, "neighbour indices must fit in the thread's queue column");
+    constexpr int KK = KC - 4;  // largest k this capacity serves (>= 4 spare entries)
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // [0] points, [1],[2] landmarks
-    float *sX = reinterpret_cast<float *>(smem + kBarrierBytes);
-    float *sL = sX + kThreads * D;
-    const int nbufL = a.nchunks == 1 ? 1 : 2;
-    float *qd = sL + (size_t)nbufL * a.chunk * D;
-    int *qi = reinterpret_cast<int *>(qd + kQueue * kThreads);
     volatile int &s_abort = *reinterpret_cast<int *>(smem + 64);
+    float *sX = reinterpret_cast<float *>(smem + kBarrierBytes);
+    const int nbufL = a.nchunks == 1 ? 1 : 2;
+    const int chunk4 = (a.chunk + 3) & ~3;
+    float *sL = sX + kThreads * D;                       // nbufL x chunk x D
+    float *sN = sL + (size_t)nbufL * a.chunk * D;        // nbufL x chunk4 norms
+    uint32_t *qk = reinterpret_cast<uint32_t *>(sN + (size_t)nbufL * chunk4);
 
     const int tid = threadIdx.x;
     const long long first = blockIdx.x;
@@ -476,12 +642,17 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
     auto issue_tile = [&](long long tile) {
         const long long r0 = tile * kThreads;
         const long long rows = a.n - r0 < kThreads ? a.n - r0 : kThreads;
-        issue_copy(sX, a.X + r0 * D, (uint32_t)(rows * D * sizeof(float)), &bars[0]);
+        const uint32_t bytes = (uint32_t)(rows * D * sizeof(float));
+        mbar_expect_tx(&bars[0], bytes);
+        copy_pieces(sX, a.X + r0 * D, bytes, &bars[0]);
     };
     auto issue_chunk = [&](int c, int buf) {
         const int cnt = a.L - c * a.chunk < a.chunk ? a.L - c * a.chunk : a.chunk;
-        issue_copy(sL + buf * chunk_floats, a.hi + (size_t)c * chunk_floats,
-                   (uint32_t)((size_t)cnt * D * sizeof(float)), &bars[1 + buf]);
+        const uint32_t rb = (uint32_t)((size_t)cnt * D * sizeof(float));
+        const uint32_t nb = (uint32_t)(((cnt + 3) & ~3) * sizeof(float));
+        mbar_expect_tx(&bars[1 + buf], rb + nb);
+        copy_pieces(sL + buf * chunk_floats, a.hi + (size_t)c * chunk_floats, rb, &bars[1 + buf]);
+        copy_pieces(sN + buf * chunk4, a.norms + (size_t)c * a.chunk, nb, &bars[1 + buf]);
     };
     if (tid == 0) {
         issue_tile(first);
@@ -504,6 +675,14 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
     const float4 *Lg = a.nchunks == 1 ? reinterpret_cast<const float4 *>(sL)
                                       : reinterpret_cast<const float4 *>(a.hi);
     const float2 *lo2 = reinterpret_cast<const float2 *>(a.lo);
+    const float lmax = *a.lmax;
+    const uint32_t mask = a.key_mask;
+    const float q = a.key_quant;
+    // |screening value - exact distance| <= kGamma (|x| + max |l|)^2: the
+    // screening sum carries at most D + 2 roundings of partial sums bounded
+    // by that square, plus the D-term norms |x|^2 and |l|^2 (2D), the
+    // four-way difference form (D/4 + 5); 25% margin.
+    constexpr float kGamma = (2.25f * D + 10.f) * kU * 1.25f;
 
     auto abort_block = [&]() {
         // Drain this block's own copies in flight (bounded), then leave.
@@ -540,28 +719,51 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
             }
         }
 
-        // Step 1: k-NN.
-        float sd[KC];
-        int si[KC];
+        // Step 1a: screening scan.
+        float xx = 0.f;
 #pragma unroll
-        for (int s = 0; s < KC; ++s) {
-            sd[s] = INFINITY;
-            si[s] = 0;
+        for (int e = 0; e < D / 4; ++e) {
+            xx = fmaf(xr[e].x, xr[e].x, xx);
+            xx = fmaf(xr[e].y, xr[e].y, xx);
+            xx = fmaf(xr[e].z, xr[e].z, xx);
+            xx = fmaf(xr[e].w, xr[e].w, xx);
         }
-        float thr = INFINITY;
-        int qn = 0;
+        const float sx = sqrtf(xx) + lmax;
+        const float M = kGamma * sx * sx;  // |screening value - exact distance| bound
+        float keys[KC];
+        ScanState st;
+        st.qn = 0;
+        st.thr = INFINITY;
         for (int c = 0; c < a.nchunks; ++c) {
             const int base = c * a.chunk;
             const int cnt = a.L - base < a.chunk ? a.L - base : a.chunk;
-            const float *Lc = sL;
+            const float *Lc = sL, *Nc = sN;
             int buf = 0;
             if (a.nchunks > 1) {
                 buf = (int)(step & 1);
                 const uint32_t par = (uint32_t)((step >> 1) & 1);
                 if (!mbar_wait(&bars[1 + buf], par)) s_abort = 1;
                 Lc = sL + buf * chunk_floats;
+                Nc = sN + buf * chunk4;
             }
-            scan_chunk<D, KC>(xr, Lc, cnt, base, sd, si, qn, thr, qd, qi, tid, a.k);
+            int j_begin = 0;
+            if (c == 0) {
+                // The first KC landmarks go straight into the list, then one
+                // sorting network (a chunk always holds at least KC
+                // landmarks, or all of them).
+                const float4 *L4 = reinterpret_cast<const float4 *>(Lc);
+#pragma unroll
+                for (int t2 = 0; t2 < KC; ++t2)
+                    keys[t2] = t2 < cnt ? make_key(screen_row<D>(xr, -0.5f * xx, Nc[t2],
+                                                                 L4 + (size_t)t2 * (D / 4)),
+                                                   (uint32_t)t2, mask)
+                                        : INFINITY;
+                key_sort<KC>(keys);
+                st.thr = push_threshold(at<KC>(keys, a.k - 1), M, q);
+                j_begin = KC < cnt ? KC : cnt;
+            }
+            scan_chunk<D, KC>(xr, -0.5f * xx, Lc, Nc, j_begin, cnt, base, mask, keys, st, qk, tid, a.k,
+                              M, q);
             if (a.nchunks > 1) {
                 __syncthreads();  // chunk buffer consumed; abort flag visible
                 if (tid == 0) {
@@ -587,13 +789,22 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
                 ++step;
             }
         }
-        queue_flush<KC>(sd, si, qn, thr, qd, qi, tid, a.k);
+        queue_flush<KC>(keys, st, qk, tid, a.k, M, q);
+
+        // Step 1b: exact re-rank of the list and its certificate.
+        float sd[KK];
+        int si[KK];
+        const bool cert = rerank<D, KC, KK>(xr, keys, Lg, mask, a.L, a.k, M, q, sd, si);
+        if (!cert) {
+            if (active) atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
+            exact_rescan<D, KK>(xr, Lg, a.L, sd, si);
+        }
 
         if (a.mode == kKnn) {
             if (active) {
                 const long long row = row0 + tid;
 #pragma unroll
-                for (int s = 0; s < KC; ++s)
+                for (int s = 0; s < KK; ++s)
                     if (s < a.k) {
                         a.idx[row * a.k + s] = si[s];
                         if (a.dist2) a.dist2[row * a.k + s] = sd[s];
@@ -601,7 +812,14 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
             }
             continue;
         }
-        const float2 p = project_point<D, KC>(xr, sd, si, Lg, lo2, a);
+        // The queue is empty now: park the neighbour indices in this thread's
+        // own column of it (two 16-bit indices a word) to free registers for
+        // the pair loop.
+        uint32_t *nb = qk + tid;
+#pragma unroll
+        for (int s = 0; s < KK; s += 2)
+            nb[(s >> 1) * kThreads] = (uint32_t)si[s] | ((uint32_t)si[s + 1] << 16);
+        const float2 p = project_point<D, KK>(sd, nb, Lg, lo2, a);
         if (active) reinterpret_cast<float2 *>(a.out)[row0 + tid] = p;
     }
 }
@@ -616,7 +834,7 @@ template <int D, int KC>
 struct Instance {
     // Two resident blocks per SM (<= 128 registers a thread) where the list
     // and the point rows fit without spilling; one otherwise.
-    static constexpr int kMinBlocks = (D <= 16 && KC <= 20) || (D <= 8 && KC <= 24) ? 2 : 1;
+    static constexpr int kMinBlocks = (D <= 16 && KC <= 24) ? 2 : 1;
     static const KernelOps ops;
 };
 
@@ -636,6 +854,7 @@ const KernelOps Instance<D, KC>::ops = {
             case 24: return &Instance<DV, 24>::ops;                  \
             case 28: return &Instance<DV, 28>::ops;                  \
             case 32: return &Instance<DV, 32>::ops;                  \
+            case 36: return &Instance<DV, 36>::ops;                  \
             default: return nullptr;                                 \
         }                                                            \
     }

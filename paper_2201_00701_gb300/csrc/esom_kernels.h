@@ -3,12 +3,13 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace esom {
 
 constexpr int kThreads = 256;      // threads per block = points per tile
-constexpr int kQueue = 16;         // per-thread candidate queue capacity
+constexpr int kQueue = 24;         // per-thread candidate queue capacity (keys)
 constexpr int kCheck = 8;          // landmarks scanned between queue checks
 constexpr int kBarrierBytes = 128; // mbarrier area at the start of shared memory
 
@@ -22,6 +23,8 @@ struct FusedArgs {
     long long n;
     const float *hi;      // L x D landmarks (library-owned, 256-byte aligned)
     const float *lo;      // L x 2 landmarks (library-owned)
+    const float *norms;   // squared norms of the L landmarks, padded to a multiple of 4
+    const float *lmax;    // largest landmark norm (one float)
     int L, k;
     float boost, adjust;
     int adjust_mode;      // 0 general, 1 adjust == 1, 2 adjust == 0
@@ -32,7 +35,9 @@ struct FusedArgs {
     int chunk;            // landmarks per shared-memory chunk
     int nchunks;          // ceil(L / chunk); 1 = resident
     long long ntiles;     // ceil(n / kThreads)
-    int *status;          // device status word (error bits)
+    unsigned key_mask;    // low bits of a screening key that hold the landmark index
+    float key_quant;      // 2^(bits - 23): relative perturbation of a key
+    int *status;          // device status words: [0] error bits, [2] rescan count
 };
 
 struct KernelOps {
@@ -47,12 +52,48 @@ const KernelOps *kernel_ops(int D, int kc);
 // Records `msg` as this host thread's last error message; returns s.
 int set_error(int s, const char *msg);
 
+// Squared landmark norms (norms[j], j < L; zero padding up to a multiple of
+// 4) and the largest norm (*lmax, which must hold 0 on entry).
+cudaError_t launch_landmark_prep(const float *hi, int L, int D, float *norms, float *lmax,
+                                 cudaStream_t stream);
+
+// List capacity for k neighbours: k plus at least four spare entries, a
+// multiple of 4, at least 8.
+inline int list_capacity(int k) {
+    int kc = ((k + 4 + 3) / 4) * 4;
+    return kc < 8 ? 8 : kc;
+}
+
+// Screening-key layout for L landmarks.
+inline void key_layout(int L, unsigned *mask, float *quant) {
+    int b = 1;
+    while ((1 << b) < L) ++b;
+    *mask = (1u << b) - 1u;
+    *quant = ldexpf(1.0f, b - 23);
+}
+
 inline size_t fused_smem_bytes(int D, int chunk, int nchunks) {
+    const size_t nbuf = nchunks == 1 ? 1 : 2;
     size_t s = kBarrierBytes;
-    s += (size_t)kThreads * D * sizeof(float);                    // point tile
-    s += (size_t)(nchunks == 1 ? 1 : 2) * chunk * D * sizeof(float); // landmark chunk(s)
-    s += (size_t)2 * kQueue * kThreads * sizeof(float);           // candidate queue
+    s += (size_t)kThreads * D * sizeof(float);                // point tile
+    s += nbuf * chunk * D * sizeof(float);                    // landmark rows
+    s += nbuf * (size_t)((chunk + 3) & ~3) * sizeof(float);   // landmark norms
+    s += (size_t)kQueue * kThreads * sizeof(unsigned);        // candidate queue
     return s;
+}
+
+// Landmarks per shared-memory chunk: all of them when rows and norms fit in
+// 72 KiB (resident), otherwise a multiple of 4 filling 32 KiB per buffer;
+// `forced` > 0 overrides (rounded up to a multiple of 4).
+inline int landmark_chunk(int L, int D, int forced) {
+    const size_t per = (size_t)D * sizeof(float) + sizeof(float);
+    if (forced > 0) {
+        int c = (forced + 3) & ~3;
+        return c >= L ? L : c;
+    }
+    if ((size_t)L * per <= 72 * 1024) return L;
+    int c = (int)((32 * 1024) / per) & ~3;
+    return c < 8 ? 8 : c;
 }
 
 }  // namespace esom

@@ -61,10 +61,12 @@ extern "C" esom_status esom_project_noalloc(const float *points, int64_t n, cons
         return noalloc_fail(ESOM_EINVAL, "d must be a multiple of 4 in [4, 64]");
     if (L < 2 || k < 2 || k > L || k > ESOM_MAX_K)
         return noalloc_fail(ESOM_EINVAL, "need 2 <= k <= min(L, 32)");
-    if ((size_t)L * (size_t)(d + 2) + kStatusFloats > kScratchFloats)
+    if (L > ESOM_MAX_L ||
+        (size_t)L * (size_t)d + (size_t)((2 * L + 3) & ~3) + (size_t)((L + 3) & ~3) +
+                kStatusFloats > kScratchFloats)
         return noalloc_fail(ESOM_EINVAL,
-                            "landmarks exceed the no-alloc scratch: need L*(d+2)*4 + 256 bytes "
-                            "<= ESOM_NOALLOC_SCRATCH_BYTES");
+                            "landmarks exceed the no-alloc scratch: need (L*(d+2) + L rounded up "
+                            "to 4)*4 + 256 bytes <= ESOM_NOALLOC_SCRATCH_BYTES");
     if (n < 0) return noalloc_fail(ESOM_EINVAL, "n < 0");
     if (!hi || !lo) return noalloc_fail(ESOM_EINVAL, "null landmark pointer");
     if (n > 0 && (!points || !out)) return noalloc_fail(ESOM_EINVAL, "null points or out");
@@ -75,9 +77,7 @@ extern "C" esom_status esom_project_noalloc(const float *points, int64_t n, cons
         return noalloc_fail(ESOM_EINVAL, "adjust must be >= 0");
     if (n == 0) return ESOM_OK;
 
-    int kc = ((k + 3) / 4) * 4;
-    if (kc < 8) kc = 8;
-    const esom::KernelOps *ops = esom::kernel_ops(d, kc);
+    const esom::KernelOps *ops = esom::kernel_ops(d, esom::list_capacity(k));
     if (!ops) return noalloc_fail(ESOM_EUNSUPPORTED, "no kernel for this (d, k)");
 
     int dev = 0, sms = 0, optin = 0, bps = 0;
@@ -88,10 +88,8 @@ extern "C" esom_status esom_project_noalloc(const float *points, int64_t n, cons
     e = scratch_address(dev, &scratch);
     if (e != cudaSuccess) return noalloc_fail(ESOM_ECUDA, cudaGetErrorString(e));
 
-    // Launch shape as for a handle: resident landmarks up to 64 KiB, else
-    // 32 KiB chunks through two shared buffers.
-    const size_t row_bytes = (size_t)d * sizeof(float);
-    const int chunk = (size_t)L * row_bytes <= 64 * 1024 ? L : (int)((32 * 1024) / row_bytes);
+    // Launch shape as for a handle.
+    const int chunk = esom::landmark_chunk(L, d, 0);
     const int nchunks = (L + chunk - 1) / chunk;
     const size_t smem = esom::fused_smem_bytes(d, chunk, nchunks);
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -104,16 +102,21 @@ extern "C" esom_status esom_project_noalloc(const float *points, int64_t n, cons
     if (e != cudaSuccess) return noalloc_fail(ESOM_ECUDA, cudaGetErrorString(e));
     if (bps < 1) return noalloc_fail(ESOM_EUNSUPPORTED, "launch does not fit on an SM");
 
-    // Scratch layout: [status word | landmarks L x d | 2-D landmarks L x 2].
+    // Scratch layout (every part 16-byte aligned): [status word, largest
+    // norm | landmarks L x d | 2-D landmarks L x 2 | squared norms, L rounded
+    // up to 4].
     int *status = reinterpret_cast<int *>(scratch);
+    float *s_lmax = scratch + 1;
     float *s_hi = scratch + kStatusFloats;
     float *s_lo = s_hi + (size_t)L * d;
+    float *s_norms = s_lo + (size_t)((2 * L + 3) & ~3);  // 16-byte aligned for the bulk copy
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    e = cudaMemsetAsync(status, 0, sizeof(int), st);  // must start at zero
+    e = cudaMemsetAsync(status, 0, 2 * sizeof(int), st);  // status and max norm start at zero
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s_hi, hi, (size_t)L * d * sizeof(float), cudaMemcpyDefault, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s_lo, lo, (size_t)L * 2 * sizeof(float), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = esom::launch_landmark_prep(s_hi, L, d, s_norms, s_lmax, st);
     if (e != cudaSuccess) return noalloc_fail(ESOM_ECUDA, cudaGetErrorString(e));
 
     esom::FusedArgs a;
@@ -122,6 +125,9 @@ extern "C" esom_status esom_project_noalloc(const float *points, int64_t n, cons
     a.n = n;
     a.hi = s_hi;
     a.lo = s_lo;
+    a.norms = s_norms;
+    a.lmax = s_lmax;
+    esom::key_layout(L, &a.key_mask, &a.key_quant);
     a.L = L;
     a.k = k;
     a.boost = boost;

@@ -35,12 +35,21 @@ def run_gpu(esom, w, chunk=None, knn=True):
         torch.cuda.synchronize()
         assert P.device_status() == 0
         cfg = P.config()
+        cfg["stats"] = P.stats()
     res = (out.cpu().numpy(), None if idx is None else idx.cpu().numpy(),
            None if d2 is None else d2.cpu().numpy(), cfg)
     return res
 
 
-def check(w, out, idx, d2, rows=None, label=""):
+def rescan_fraction(cfg):
+    st = cfg["stats"]
+    return st["rescans"] / max(st["points"], 1)
+
+
+def check(w, out, idx, d2, rows=None, label="", cfg=None, max_rescans=0.01):
+    """Coordinates and k-NN against the oracle.  The screening certificate
+    must fail (forcing an exact rescan) for at most `max_rescans` of the
+    points on these continuous-valued workloads."""
     X = w.X if rows is None else w.X[rows]
     o_out, ratio, _ = oracle.project(X, w.hi, w.lo, w.k, w.boost, w.adjust, diagnostics=True)
     sel = slice(None) if rows is None else rows
@@ -50,7 +59,11 @@ def check(w, out, idx, d2, rows=None, label=""):
         nd, ties = knn_mismatches(X, w.hi, idx[sel], d2[sel], o_idx, o_d2)
         stats.update(knn_rows_differing=nd, knn_tie_swaps=ties)
     stats["label"] = label
+    if cfg is not None:
+        stats["rescan_fraction"] = rescan_fraction(cfg)
     print("PARITY", json.dumps(stats))
+    if cfg is not None:
+        assert stats["rescan_fraction"] <= max_rescans, stats
     return stats
 
 
@@ -59,7 +72,7 @@ def test_mixture10_d8_full(esom):
     w = workloads.mixture10_d8()
     out, idx, d2, cfg = run_gpu(esom, w)
     assert cfg["landmark_chunks"] == 1
-    check(w, out, idx, d2, label="mixture10_d8 full")
+    check(w, out, idx, d2, label="mixture10_d8 full", cfg=cfg)
 
 
 @pytest.mark.parametrize("n", [1, 255, 256, 257, 20_000 + 77])
@@ -67,8 +80,8 @@ def test_mixture30_d16_sizes(esom, n):
     """d = 16, L = 1024, k = 20 at tile boundaries and a ragged tail."""
     w = workloads.mixture30_d16(n=max(n, 2000))
     w.X = np.ascontiguousarray(w.X[:n])
-    out, idx, d2, _ = run_gpu(esom, w)
-    check(w, out, idx, d2, label=f"mixture30_d16 n={n}")
+    out, idx, d2, cfg = run_gpu(esom, w)
+    check(w, out, idx, d2, label=f"mixture30_d16 n={n}", cfg=cfg if n > 255 else None)
 
 
 def test_mixture30_d16_full_size_sampled(esom):
@@ -77,7 +90,7 @@ def test_mixture30_d16_full_size_sampled(esom):
     w = workloads.mixture30_d16()
     out, idx, d2, cfg = run_gpu(esom, w)
     rows = np.sort(np.random.default_rng(7).choice(w.n, 3000, replace=False))
-    check(w, out, idx, d2, rows=rows, label="mixture30_d16 1e6 sampled")
+    check(w, out, idx, d2, rows=rows, label="mixture30_d16 1e6 sampled", cfg=cfg)
     assert np.isfinite(out).all()
 
 
@@ -87,16 +100,16 @@ def test_chunked_landmarks(esom, chunk):
     w = workloads.mixture30_d16(n=6000)
     out, idx, d2, cfg = run_gpu(esom, w, chunk=chunk)
     assert cfg["landmark_chunks"] == -(-w.L // chunk)
-    check(w, out, idx, d2, label=f"chunk={chunk}")
+    check(w, out, idx, d2, label=f"chunk={chunk}", cfg=cfg)
 
 
 def test_uniform_paper_shapes(esom):
     """The paper's uniform benchmark data (Section 4.1), d = 16 and 32."""
     for d in (16, 32):
         w = workloads.uniform(d, n=1 << 20)
-        out, idx, d2, _ = run_gpu(esom, w)
+        out, idx, d2, cfg = run_gpu(esom, w)
         rows = np.sort(np.random.default_rng(d).choice(w.n, 2000, replace=False))
-        check(w, out, idx, d2, rows=rows, label=f"uniform d={d}")
+        check(w, out, idx, d2, rows=rows, label=f"uniform d={d}", cfg=cfg)
 
 
 def test_batch_members(esom):
@@ -106,7 +119,7 @@ def test_batch_members(esom):
     for p in params:
         w = workloads.batch_member(p, n=min(p["n"], 8000))
         out, idx, d2, cfg = run_gpu(esom, w)
-        check(w, out, idx, d2, label=f"batch {p['index']} d={w.d} L={w.L} k={w.k}")
+        check(w, out, idx, d2, label=f"batch {p['index']} d={w.d} L={w.L} k={w.k}", cfg=cfg)
 
 
 def test_student50_d32_full_size_sampled(esom):
@@ -115,5 +128,5 @@ def test_student50_d32_full_size_sampled(esom):
     out, idx, d2, cfg = run_gpu(esom, w, knn=False)
     assert cfg["landmark_chunks"] > 1
     rows = np.sort(np.random.default_rng(3).choice(w.n, 1500, replace=False))
-    check(w, out, None, None, rows=rows, label="student50_d32 1e7 sampled")
+    check(w, out, None, None, rows=rows, label="student50_d32 1e7 sampled", cfg=cfg)
     assert np.isfinite(out).all()
