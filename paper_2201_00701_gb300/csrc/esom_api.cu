@@ -40,9 +40,10 @@ int set_error(int s, const char *msg) {
     return s;
 }
 
-// One thread per landmark: squared norm (FMA chain) and the running maximum
-// of the norms (non-negative floats order like their bit patterns).
-__global__ void landmark_prep_kernel(const float *__restrict__ hi, int L, int D,
+// One thread per landmark: squared norm (FMA chain, logical order), the
+// running maximum of the norms (non-negative floats order like their bit
+// patterns), and the row rewritten in place with its chunks swizzled.
+__global__ void landmark_prep_kernel(float *__restrict__ hi, int L, int D,
                                      float *__restrict__ norms, float *__restrict__ lmax) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int padded = (L + 3) & ~3;
@@ -51,13 +52,24 @@ __global__ void landmark_prep_kernel(const float *__restrict__ hi, int L, int D,
         norms[j] = 0.f;
         return;
     }
+    float4 *row = reinterpret_cast<float4 *>(hi + (size_t)j * D);
+    float4 buf[16];
+    const int c = D / 4;
     float s = 0.f;
-    for (int t = 0; t < D; ++t) s = fmaf(hi[(size_t)j * D + t], hi[(size_t)j * D + t], s);
+    for (int e = 0; e < c; ++e) {
+        buf[e] = row[e];
+        s = fmaf(buf[e].x, buf[e].x, s);
+        s = fmaf(buf[e].y, buf[e].y, s);
+        s = fmaf(buf[e].z, buf[e].z, s);
+        s = fmaf(buf[e].w, buf[e].w, s);
+    }
+    const int f = swz(D, j);
+    for (int e = 0; e < c; ++e) row[e ^ f] = buf[e];
     norms[j] = s;
     atomicMax(reinterpret_cast<int *>(lmax), __float_as_int(sqrtf(s)));
 }
 
-cudaError_t launch_landmark_prep(const float *hi, int L, int D, float *norms, float *lmax,
+cudaError_t launch_landmark_prep(float *hi, int L, int D, float *norms, float *lmax,
                                  cudaStream_t stream) {
     const int padded = (L + 3) & ~3;
     landmark_prep_kernel<<<(padded + 255) / 256, 256, 0, stream>>>(hi, L, D, norms, lmax);

@@ -199,14 +199,17 @@ __device__ __forceinline__ float push_threshold(float kth, float M, float q) {
     return g + 2.f * M + 4.f * q * (fabsf(g) + 2.f * M) + 1e-30f;
 }
 
-// Squared distance in the FP32 difference form with four partial sums (the
-// exact distance that is reported and ranked).
+// Squared distance to landmark j (rows of L4, chunk-swizzled) in the FP32
+// difference form with four partial sums (the exact distance that is
+// reported and ranked).
 template <int D>
-__device__ __forceinline__ float dist2_row(const float4 (&x)[D / 4], const float4 *l) {
+__device__ __forceinline__ float dist2_row(const float4 (&x)[D / 4], const float4 *L4, int j) {
+    const float4 *l = L4 + (size_t)j * (D / 4);
+    const int f = swz(D, j);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
     for (int e = 0; e < D / 4; ++e) {
-        const float4 q = l[e];
+        const float4 q = l[e ^ f];
         const float dx = x[e].x - q.x, dy = x[e].y - q.y;
         const float dz = x[e].z - q.z, dw = x[e].w - q.w;
         a0 = fmaf(dx, dx, a0);
@@ -222,11 +225,13 @@ __device__ __forceinline__ float dist2_row(const float4 (&x)[D / 4], const float
 // scalings by -1/2 and -2 are exact).
 template <int D>
 __device__ __forceinline__ float screen_row(const float4 (&x)[D / 4], float hxx, float ll,
-                                            const float4 *l) {
+                                            const float4 *L4, int j) {
+    const float4 *l = L4 + (size_t)j * (D / 4);
+    const int f = swz(D, j);
     float a = fmaf(-0.5f, ll, hxx);
 #pragma unroll
     for (int e = 0; e < D / 4; ++e) {
-        const float4 q = l[e];
+        const float4 q = l[e ^ f];
         a = fmaf(x[e].x, q.x, a);
         a = fmaf(x[e].y, q.y, a);
         a = fmaf(x[e].z, q.z, a);
@@ -252,39 +257,66 @@ __device__ __forceinline__ void queue_flush(float (&keys)[KC], ScanState &st, co
     st.thr = push_threshold(at<KC>(keys, k - 1), M, q);
 }
 
+// Screening values of NB consecutive landmarks j0.. of a chunk, with the NB
+// FMA chains interleaved chunk by chunk (hxx = -|x|^2 / 2).  j0 is a
+// multiple of 8, so the chunk swizzle of every row is known at compile time.
+template <int D, int NB>
+__device__ __forceinline__ void screen_block(const float4 (&x)[D / 4], float hxx,
+                                             const float4 *L4, const float *Nc, int j0,
+                                             float (&v)[NB]) {
+#pragma unroll
+    for (int jj = 0; jj < NB; ++jj) v[jj] = fmaf(-0.5f, Nc[j0 + jj], hxx);
+#pragma unroll
+    for (int e = 0; e < D / 4; ++e)
+#pragma unroll
+        for (int jj = 0; jj < NB; ++jj) {
+            const float4 q = L4[(size_t)(j0 + jj) * (D / 4) + (e ^ swz(D, jj))];
+            v[jj] = fmaf(x[e].x, q.x, v[jj]);
+            v[jj] = fmaf(x[e].y, q.y, v[jj]);
+            v[jj] = fmaf(x[e].z, q.z, v[jj]);
+            v[jj] = fmaf(x[e].w, q.w, v[jj]);
+        }
+#pragma unroll
+    for (int jj = 0; jj < NB; ++jj) v[jj] *= -2.f;
+}
+
 // Screens landmarks j_begin..cnt-1 of one shared-memory chunk (global
-// indices base + j).
+// indices base + j; base is a multiple of 8).  Single landmarks up to the
+// next multiple of 8, then blocks of 8, then the tail; the queue is checked
+// after every block and after each single-step run (at most 7 pushes).
+template <int D, int KC>
+__device__ __forceinline__ void push_key(float v, int jg, uint32_t mask, ScanState &st,
+                                         uint32_t *qk, int tid) {
+    const float key = make_key(v, (uint32_t)jg, mask);
+    if (key < st.thr) {
+        qk[st.qn * kThreads + tid] = __float_as_uint(key);
+        ++st.qn;
+    }
+}
+
 template <int D, int KC>
 __device__ __forceinline__ void scan_chunk(const float4 (&x)[D / 4], float hxx, const float *Lc,
                                            const float *Nc, int j_begin, int cnt, int base,
                                            uint32_t mask, float (&keys)[KC], ScanState &st,
                                            uint32_t *qk, int tid, int k, float M, float q) {
     const float4 *L4 = reinterpret_cast<const float4 *>(Lc);
-    for (int j0 = j_begin; j0 < cnt; j0 += kCheck) {
-        if (j0 + kCheck <= cnt) {
+    int j = j_begin;
+    for (; j < cnt && (j & 7) != 0; ++j)
+        push_key<D, KC>(screen_row<D>(x, hxx, Nc[j], L4, j), base + j, mask, st, qk, tid);
+    if (__any_sync(0xffffffffu, st.qn > kQueue - kCheck))
+        queue_flush<KC>(keys, st, qk, tid, k, M, q);
+    for (; j + kCheck <= cnt; j += kCheck) {
+        float v[kCheck];
+        screen_block<D, kCheck>(x, hxx, L4, Nc, j, v);
 #pragma unroll
-            for (int jj = 0; jj < kCheck; ++jj) {
-                const int j = j0 + jj;
-                const float v = screen_row<D>(x, hxx, Nc[j], L4 + (size_t)j * (D / 4));
-                const float key = make_key(v, (uint32_t)(base + j), mask);
-                if (key < st.thr) {
-                    qk[st.qn * kThreads + tid] = __float_as_uint(key);
-                    ++st.qn;
-                }
-            }
-        } else {
-            for (int j = j0; j < cnt; ++j) {
-                const float v = screen_row<D>(x, hxx, Nc[j], L4 + (size_t)j * (D / 4));
-                const float key = make_key(v, (uint32_t)(base + j), mask);
-                if (key < st.thr) {
-                    qk[st.qn * kThreads + tid] = __float_as_uint(key);
-                    ++st.qn;
-                }
-            }
-        }
+        for (int jj = 0; jj < kCheck; ++jj) push_key<D, KC>(v[jj], base + j + jj, mask, st, qk, tid);
         if (__any_sync(0xffffffffu, st.qn > kQueue - kCheck))
             queue_flush<KC>(keys, st, qk, tid, k, M, q);
     }
+    for (; j < cnt; ++j)
+        push_key<D, KC>(screen_row<D>(x, hxx, Nc[j], L4, j), base + j, mask, st, qk, tid);
+    if (__any_sync(0xffffffffu, st.qn > kQueue - kCheck))
+        queue_flush<KC>(keys, st, qk, tid, k, M, q);
 }
 
 // Exact k-NN of one point by a plain scan (the rare path when the screening
@@ -298,7 +330,7 @@ __device__ __forceinline__ void exact_rescan(const float4 (&x)[D / 4], const flo
         ei[t] = 0;
     }
     for (int j = 0; j < L; ++j) {
-        const float d2 = dist2_row<D>(x, Lg + (size_t)j * (D / 4));
+        const float d2 = dist2_row<D>(x, Lg, j);
         if (d2 < ed[KK - 1]) {
             bool c[KK];
 #pragma unroll
@@ -330,7 +362,7 @@ __device__ __forceinline__ bool rerank(const float4 (&x)[D / 4], const float (&k
         const bool valid = keys[t] < INFINITY;
         // (the min() only guards the row read; listed keys carry indices < L)
         ci[t] = valid ? min((int)(__float_as_uint(keys[t]) & mask), L - 1) : 0;
-        cd[t] = valid ? dist2_row<D>(x, Lg + (size_t)ci[t] * (D / 4)) : INFINITY;
+        cd[t] = valid ? dist2_row<D>(x, Lg, ci[t]) : INFINITY;
     }
     // The screened order is the exact order except near ties; repair with
     // odd-even transposition passes on (distance, index) until sorted.
@@ -400,9 +432,10 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
                 du = sd[t];
             }
         const float4 *Lu = Lg + (size_t)iu * (D / 4);
+        const int fu = swz(D, iu);
         float4 lu[D / 4];
 #pragma unroll
-        for (int e = 0; e < D / 4; ++e) lu[e] = Lu[e];
+        for (int e = 0; e < D / 4; ++e) lu[e] = Lu[e ^ fu];
         const float2 lut = __ldg(&lo2[iu]);
         const float lux = lut.x - l0.x, luy = lut.y - l0.y;  // l_u relative to l_0
 #pragma unroll
@@ -410,10 +443,11 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
             if (v > u && v < m) {
                 const int iv = nb_at(nb, v);
                 const float4 *Lv = Lg + (size_t)iv * (D / 4);
+                const int fv = swz(D, iv);
                 float q0 = 0.f, q1 = 0.f;
 #pragma unroll
                 for (int e = 0; e < D / 4; ++e) {
-                    const float4 lv = Lv[e];
+                    const float4 lv = Lv[e ^ fv];
                     const float ex = lv.x - lu[e].x, ey = lv.y - lu[e].y;
                     const float ez = lv.z - lu[e].z, ew = lv.w - lu[e].w;
                     q0 = fmaf(ex, ex, q0);
@@ -751,16 +785,32 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
                 // The first KC landmarks go straight into the list, then one
                 // sorting network (a chunk always holds at least KC
                 // landmarks, or all of them).
+                // KF = KC rounded up to 8 landmarks are screened as one
+                // block and sorted; the KF - KC largest keys are dropped,
+                // which the certificate covers like any key pushed out of
+                // the list (they are >= its last key).
+                constexpr int KF = (KC + 7) & ~7;
                 const float4 *L4 = reinterpret_cast<const float4 *>(Lc);
+                if (cnt >= KF) {
+                    float v[KF];
+                    screen_block<D, KF>(xr, -0.5f * xx, L4, Nc, 0, v);
 #pragma unroll
-                for (int t2 = 0; t2 < KC; ++t2)
-                    keys[t2] = t2 < cnt ? make_key(screen_row<D>(xr, -0.5f * xx, Nc[t2],
-                                                                 L4 + (size_t)t2 * (D / 4)),
-                                                   (uint32_t)t2, mask)
-                                        : INFINITY;
-                key_sort<KC>(keys);
+                    for (int t2 = 0; t2 < KF; ++t2) v[t2] = make_key(v[t2], (uint32_t)t2, mask);
+                    key_sort<KF>(v);
+#pragma unroll
+                    for (int t2 = 0; t2 < KC; ++t2) keys[t2] = v[t2];
+                    j_begin = KF;
+                } else {
+#pragma unroll
+                    for (int t2 = 0; t2 < KC; ++t2)
+                        keys[t2] = t2 < cnt ? make_key(screen_row<D>(xr, -0.5f * xx, Nc[t2], L4,
+                                                                     t2),
+                                                       (uint32_t)t2, mask)
+                                            : INFINITY;
+                    key_sort<KC>(keys);
+                    j_begin = KC < cnt ? KC : cnt;
+                }
                 st.thr = push_threshold(at<KC>(keys, a.k - 1), M, q);
-                j_begin = KC < cnt ? KC : cnt;
             }
             scan_chunk<D, KC>(xr, -0.5f * xx, Lc, Nc, j_begin, cnt, base, mask, keys, st, qk, tid, a.k,
                               M, q);

@@ -53,9 +53,26 @@ const KernelOps *kernel_ops(int D, int kc);
 int set_error(int s, const char *msg);
 
 // Squared landmark norms (norms[j], j < L; zero padding up to a multiple of
-// 4) and the largest norm (*lmax, which must hold 0 on entry).
-cudaError_t launch_landmark_prep(const float *hi, int L, int D, float *norms, float *lmax,
+// 4), the largest norm (*lmax, which must hold 0 on entry), and the rows of
+// hi swizzled in place (see swz).
+cudaError_t launch_landmark_prep(float *hi, int L, int D, float *norms, float *lmax,
                                  cudaStream_t stream);
+
+// Landmark rows are stored with their 16-byte chunks permuted: logical chunk
+// e of row j sits at physical chunk e ^ swz(j), with g = gcd(d/4, 8) and
+// swz(j) = (j / (8/g)) mod g.  Rows are d*4 bytes apart, so without the
+// permutation the same chunk of different rows falls on few of the eight
+// 16-byte bank groups; with it, any eight consecutive rows use all eight,
+// and the random-row gathers of the re-rank and the pair loop see ~2.6-way
+// instead of up to 8-way conflicts.  swz depends only on j mod 8.
+__host__ __device__ inline int swz_groups(int D) {
+    const int c = D / 4;
+    return (c % 8 == 0) ? 8 : (c % 4 == 0) ? 4 : (c % 2 == 0) ? 2 : 1;
+}
+__host__ __device__ inline int swz(int D, int j) {
+    const int g = swz_groups(D);
+    return (j / (8 / g)) & (g - 1);
+}
 
 // List capacity for k neighbours: k plus at least four spare entries, a
 // multiple of 4, at least 8.
@@ -83,17 +100,18 @@ inline size_t fused_smem_bytes(int D, int chunk, int nchunks) {
 }
 
 // Landmarks per shared-memory chunk: all of them when rows and norms fit in
-// 72 KiB (resident), otherwise a multiple of 4 filling 32 KiB per buffer;
-// `forced` > 0 overrides (rounded up to a multiple of 4).
+// 72 KiB (resident), otherwise a multiple of 8 filling 32 KiB per buffer;
+// `forced` > 0 overrides (rounded up to a multiple of 8).  A multiple of 8
+// keeps local and global landmark indices equal modulo 8 (see swz).
 inline int landmark_chunk(int L, int D, int forced) {
     const size_t per = (size_t)D * sizeof(float) + sizeof(float);
     if (forced > 0) {
-        int c = (forced + 3) & ~3;
+        int c = (forced + 7) & ~7;
         return c >= L ? L : c;
     }
     if ((size_t)L * per <= 72 * 1024) return L;
-    int c = (int)((32 * 1024) / per) & ~3;
-    return c < 8 ? 8 : c;
+    int c = (int)((32 * 1024) / per) & ~7;
+    return c < 48 ? 48 : c;
 }
 
 }  // namespace esom

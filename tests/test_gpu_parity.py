@@ -94,12 +94,14 @@ def test_mixture30_d16_full_size_sampled(esom):
     assert np.isfinite(out).all()
 
 
-@pytest.mark.parametrize("chunk", [100, 333, 1000])
+@pytest.mark.parametrize("chunk", [8, 100, 333, 1000])
 def test_chunked_landmarks(esom, chunk):
-    """Landmarks streamed through shared memory in chunks (ragged last chunk)."""
+    """Landmarks streamed through shared memory in chunks (ragged last chunk;
+    a forced chunk is rounded up to a multiple of 8 landmarks)."""
     w = workloads.mixture30_d16(n=6000)
     out, idx, d2, cfg = run_gpu(esom, w, chunk=chunk)
-    assert cfg["landmark_chunks"] == -(-w.L // chunk)
+    assert cfg["landmark_chunk"] == -(-chunk // 8) * 8
+    assert cfg["landmark_chunks"] == -(-w.L // cfg["landmark_chunk"])
     check(w, out, idx, d2, label=f"chunk={chunk}", cfg=cfg)
 
 
