@@ -253,6 +253,22 @@ def run_esom(args, world, rank, local):
     if P.device_status() != 0:
         raise RuntimeError("device status flag raised in the timed region")
 
+    # the k-NN step alone (same kernel, no projection phase): splits the step
+    # time into k-NN and scores + pair sums + solve
+    idx_buf = torch.empty((n, k), dtype=torch.int32, device=dev)
+    knn_ms = []
+    for i in range(args.warmup + min(args.steps, 20)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        binding.check(binding.esom_knn(P.h, X.data_ptr(), n, idx_buf.data_ptr(), None,
+                                       stream.cuda_stream))
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            knn_ms.append(e0.elapsed_time(e1))
+    del idx_buf
+
     # end to end through the host-buffer entry point (pinned host memory)
     Xh = torch.from_numpy(w.X).pin_memory()
     outh = torch.empty((n, 2), dtype=torch.float32).pin_memory()
@@ -297,6 +313,9 @@ def run_esom(args, world, rank, local):
                            "p99": float(np.percentile(step_ms, 99)),
                            "rsd": float(np.std(step_ms) / np.mean(step_ms))},
             "wall_s_timed_region": wall,
+            "phases_ms": {"knn_only": float(np.median(knn_ms)),
+                          "projection_share": 1.0 - float(np.median(knn_ms))
+                          / float(np.median(step_ms))},
             "gpu_launches": args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,

@@ -153,7 +153,6 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
     a.k = h->k;
     a.boost = boost;
     a.adjust = adjust;
-    a.adjust_mode = adjust == 1.0f ? 1 : (adjust == 0.0f ? 2 : 0);
     a.out = out;
     a.idx = idx;
     a.dist2 = dist2;

@@ -126,6 +126,36 @@ __device__ __forceinline__ void copy_pieces(void *dst, const void *src, uint32_t
     }
 }
 
+// Reciprocal by the SFU (one instruction, relative error ~2^-23); used
+// where a correctly rounded division is not needed.
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float log2f_fast(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float exp2f_fast(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// FP64 reciprocal: SFU seed refined by two Newton steps (full double
+// precision for normal inputs), instead of the long division sequence.
+__device__ __forceinline__ double drcp(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    r = r * fma(-x, r, 2.0);
+    r = r * fma(-x, r, 2.0);
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // Screening keys: a 32-bit pattern whose high bits are the FP32 screening
 // value and whose low `b` bits are the landmark index.  Read back as a float
@@ -300,30 +330,35 @@ __device__ __forceinline__ void scan_chunk(const float4 (&x)[D / 4], float hxx, 
                                            uint32_t mask, float (&keys)[KC], ScanState &st,
                                            uint32_t *qk, int tid, int k, float M, float q) {
     const float4 *L4 = reinterpret_cast<const float4 *>(Lc);
-    int j = j_begin;
-    for (; j < cnt && (j & 7) != 0; ++j)
-        push_key<D, KC>(screen_row<D>(x, hxx, Nc[j], L4, j), base + j, mask, st, qk, tid);
-    if (__any_sync(0xffffffffu, st.qn > kQueue - kCheck))
-        queue_flush<KC>(keys, st, qk, tid, k, M, q);
-    for (; j + kCheck <= cnt; j += kCheck) {
-        float v[kCheck];
-        screen_block<D, kCheck>(x, hxx, L4, Nc, j, v);
+    for (int j = j_begin; j < cnt;) {
+        if ((j & 7) == 0 && j + kCheck <= cnt) {
+            float v[kCheck];
+            screen_block<D, kCheck>(x, hxx, L4, Nc, j, v);
 #pragma unroll
-        for (int jj = 0; jj < kCheck; ++jj) push_key<D, KC>(v[jj], base + j + jj, mask, st, qk, tid);
+            for (int jj = 0; jj < kCheck; ++jj)
+                push_key<D, KC>(v[jj], base + j + jj, mask, st, qk, tid);
+            j += kCheck;
+        } else {
+            push_key<D, KC>(screen_row<D>(x, hxx, Nc[j], L4, j), base + j, mask, st, qk, tid);
+            ++j;
+        }
         if (__any_sync(0xffffffffu, st.qn > kQueue - kCheck))
             queue_flush<KC>(keys, st, qk, tid, k, M, q);
     }
-    for (; j < cnt; ++j)
-        push_key<D, KC>(screen_row<D>(x, hxx, Nc[j], L4, j), base + j, mask, st, qk, tid);
-    if (__any_sync(0xffffffffu, st.qn > kQueue - kCheck))
-        queue_flush<KC>(keys, st, qk, tid, k, M, q);
 }
 
 // Exact k-NN of one point by a plain scan (the rare path when the screening
 // certificate fails): difference-form distances, stable shift insertion.
+// Out of line, on local copies, so that the hot path keeps its registers
+// and its instruction footprint.
 template <int D, int KK>
-__device__ __forceinline__ void exact_rescan(const float4 (&x)[D / 4], const float4 *Lg, int L,
-                                          float (&ed)[KK], int (&ei)[KK]) {
+__device__ __noinline__ void exact_rescan(const float4 *xp, const float4 *Lg, int L, float *edp,
+                                          int *eip) {
+    float4 x[D / 4];
+#pragma unroll
+    for (int e = 0; e < D / 4; ++e) x[e] = xp[e];
+    float ed[KK];
+    int ei[KK];
 #pragma unroll
     for (int t = 0; t < KK; ++t) {
         ed[t] = INFINITY;
@@ -346,6 +381,42 @@ __device__ __forceinline__ void exact_rescan(const float4 (&x)[D / 4], const flo
             }
         }
     }
+#pragma unroll
+    for (int t = 0; t < KK; ++t) {
+        edp[t] = ed[t];
+        eip[t] = ei[t];
+    }
+}
+
+// Orders cd/ci by (distance, index) with odd-even transposition passes (the
+// rare path when screening left near ties out of order).  Out of line.
+template <int KC>
+__device__ __noinline__ void repair_order(float *cdp, int *cip) {
+    float cd[KC];
+    int ci[KC];
+#pragma unroll
+    for (int t = 0; t < KC; ++t) {
+        cd[t] = cdp[t];
+        ci[t] = cip[t];
+    }
+    for (int pass = 0; pass < KC; ++pass) {
+#pragma unroll
+        for (int t = 0; t + 1 < KC; ++t) {
+            if ((t & 1) != (pass & 1)) continue;
+            const bool sw = cd[t + 1] < cd[t] || (cd[t + 1] == cd[t] && ci[t + 1] < ci[t]);
+            const float d0 = cd[t], d1 = cd[t + 1];
+            const int i0 = ci[t], i1 = ci[t + 1];
+            cd[t] = sw ? d1 : d0;
+            cd[t + 1] = sw ? d0 : d1;
+            ci[t] = sw ? i1 : i0;
+            ci[t + 1] = sw ? i0 : i1;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < KC; ++t) {
+        cdp[t] = cd[t];
+        cip[t] = ci[t];
+    }
 }
 
 // Exact re-rank of the screened list.  On return ed/ei hold the KK nearest
@@ -364,28 +435,26 @@ __device__ __forceinline__ bool rerank(const float4 (&x)[D / 4], const float (&k
         ci[t] = valid ? min((int)(__float_as_uint(keys[t]) & mask), L - 1) : 0;
         cd[t] = valid ? dist2_row<D>(x, Lg, ci[t]) : INFINITY;
     }
-    // The screened order is the exact order except near ties; repair with
-    // odd-even transposition passes on (distance, index) until sorted.
+    // The screened order is the exact order except near ties; when it is
+    // not, repair it (rare, out of line).
     bool sorted = true;
 #pragma unroll
     for (int t = 0; t + 1 < KC; ++t)
         sorted = sorted && !(cd[t + 1] < cd[t] || (cd[t + 1] == cd[t] && ci[t + 1] < ci[t]));
-    for (int pass = 0; pass < KC && __any_sync(0xffffffffu, !sorted); ++pass) {
+    if (__builtin_expect(!sorted, 0)) {
+        float tcd[KC];
+        int tci[KC];
 #pragma unroll
-        for (int t = 0; t + 1 < KC; ++t) {
-            if ((t & 1) != (pass & 1)) continue;
-            const bool sw = cd[t + 1] < cd[t] || (cd[t + 1] == cd[t] && ci[t + 1] < ci[t]);
-            const float d0 = cd[t], d1 = cd[t + 1];
-            const int i0 = ci[t], i1 = ci[t + 1];
-            cd[t] = sw ? d1 : d0;
-            cd[t + 1] = sw ? d0 : d1;
-            ci[t] = sw ? i1 : i0;
-            ci[t + 1] = sw ? i0 : i1;
+        for (int t = 0; t < KC; ++t) {
+            tcd[t] = cd[t];
+            tci[t] = ci[t];
         }
-        sorted = true;
+        repair_order<KC>(tcd, tci);
 #pragma unroll
-        for (int t = 0; t + 1 < KC; ++t)
-            sorted = sorted && !(cd[t + 1] < cd[t] || (cd[t + 1] == cd[t] && ci[t + 1] < ci[t]));
+        for (int t = 0; t < KC; ++t) {
+            cd[t] = tcd[t];
+            ci[t] = tci[t];
+        }
     }
 #pragma unroll
     for (int t = 0; t < KK; ++t) {
@@ -460,15 +529,13 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
                 const float hx = lvt.x - lut.x, hy = lvt.y - lut.y;
                 const float r = fmaf(hx, hx, hy * hy);
                 if (qq > 0.f && r > 0.f) {
-                    const float ir = __frcp_rn(r);
-                    float w = su * ss[v];
-                    if (a.adjust_mode == 1)
-                        w *= ir;
-                    else if (a.adjust_mode == 0)
-                        w *= exp2f(-a.adjust * log2f(r));
+                    const float ir = rcp_fast(r);
+                    // r^-adjust by the SFU (relative error ~1e-6), the same code
+                    // for every adjust so the loop is not duplicated per case
+                    const float w = su * ss[v] * exp2f_fast(-a.adjust * log2f_fast(r));
                     const float wr = w * ir;
                     if (PASS == 0) {
-                        const float Duv = 0.5f * (du - sd[v] + qq) * __frcp_rn(qq);
+                        const float Duv = 0.5f * (du - sd[v] + qq) * rcp_fast(qq);
                         const float rhs = fmaf(fmaf(hx, lux, hy * luy), ir, Duv);
                         A00 = fmaf(wr * hx, hx, A00);
                         A01 = fmaf(wr * hx, hy, A01);
@@ -486,14 +553,84 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The near-singular solve (rare; out of line).  A00 A11 - A01^2 from FP32
+// sums cannot resolve det/trace^2 below ~1e-6, so the small eigenvalue is
+// recomputed as the Rayleigh quotient n^T A n along the minor eigenvector n
+// of the FP32 matrix -- a sum of non-negative terms w (h.n)^2 / r over the
+// pairs, free of cancellation and accurate to second order in the error of
+// n -- and the branch is taken on det = lmin (trace - lmin): Cramer's rule if
+// det > 1e-10 trace^2, else the least-norm solution about the score-weighted
+// centroid of the scored 2-D landmarks (plain mean if all scores are 0), or
+// the centroid itself when A = 0.
+
+struct SlowSolve {
+    float A00, A01, A11, B0, B1, C0, C1, Ssum, M0, M1;
+    int m;
+};
+
 template <int D, int KK>
-__device__ __forceinline__ float minor_rayleigh(const float (&sd)[KK], const uint32_t *nb,
-                                             const float (&ss)[KK], int m, const float4 *Lg,
-                                             const float2 *lo2, float2 l0, const FusedArgs &a,
-                                             float nx, float ny) {
-    float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f, z4 = 0.f, rho = 0.f;
-    pair_sums<D, KK, 1>(sd, nb, ss, m, Lg, lo2, l0, a, nx, ny, z0, z1, z2, z3, z4, rho);
-    return rho;
+__device__ __noinline__ double2 solve_slow(const SlowSolve in, const float *sdp,
+                                           const float *ssp, const uint32_t *nb,
+                                           const float4 *Lg, const float2 *lo2, float2 l0,
+                                           const FusedArgs &a) {
+    const double a00 = in.A00, a01 = in.A01, a11 = in.A11, b0 = in.B0, b1 = in.B1;
+    double det = a00 * a11 - a01 * a01;
+    const double tr = a00 + a11;
+    if (tr > 0.0) {
+        const double disc = sqrt((a00 - a11) * (a00 - a11) + 4.0 * a01 * a01);
+        const double lmax = 0.5 * (tr + disc);
+        // two candidate major eigenvectors; take the better conditioned one
+        const double va0 = a01, va1 = lmax - a00, vb0 = lmax - a11, vb1 = a01;
+        const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
+        const double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
+        const double nn = sqrt(ga >= gb ? ga : gb);
+        if (nn > 0.0) {
+            // minor direction: the major one turned by 90 degrees
+            float sd[KK], ss[KK];
+#pragma unroll
+            for (int t = 0; t < KK; ++t) {
+                sd[t] = sdp[t];
+                ss[t] = ssp[t];
+            }
+            float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f, z4 = 0.f, rho = 0.f;
+            pair_sums<D, KK, 1>(sd, nb, ss, in.m, Lg, lo2, l0, a, (float)(-v1 / nn),
+                                (float)(v0 / nn), z0, z1, z2, z3, z4, rho);
+            const double lmin = (double)rho;
+            det = lmin * (tr - lmin);
+        }
+    }
+    if (det > kDetEps * tr * tr) {
+        const double id = 1.0 / det;
+        return make_double2((b0 * a11 - a01 * b1) * id, (a00 * b1 - a01 * b0) * id);
+    }
+    double c0, c1;
+    if (in.Ssum > 0.f) {
+        c0 = (double)in.C0 / (double)in.Ssum;
+        c1 = (double)in.C1 / (double)in.Ssum;
+    } else {
+        c0 = (double)in.M0 / (double)in.m;
+        c1 = (double)in.M1 / (double)in.m;
+    }
+    if (tr == 0.0) return make_double2(c0, c1);
+    const double disc = sqrt((a00 - a11) * (a00 - a11) + 4.0 * a01 * a01);
+    const double lam = 0.5 * (tr + disc);
+    double va0 = a01, va1 = lam - a00, vb0 = lam - a11, vb1 = a01;
+    const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
+    double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
+    double nn = ga >= gb ? ga : gb;
+    if (nn == 0.0) {
+        v0 = 1.0;
+        v1 = 0.0;
+        nn = 1.0;
+    }
+    nn = sqrt(nn);
+    v0 /= nn;
+    v1 /= nn;
+    const double r0 = b0 - (a00 * c0 + a01 * c1);
+    const double r1 = b1 - (a01 * c0 + a11 * c1);
+    const double t = (v0 * r0 + v1 * r1) / lam;
+    return make_double2(c0 + t * v0, c1 + t * v1);
 }
 
 // ---------------------------------------------------------------------------
@@ -511,9 +648,11 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
     // spread are 1/i over the m scored neighbours.  exp(boost (d_1 - d_i) /
     // sigma) differs from exp(boost (mean - d_i) / sigma) by one common
     // factor, which cancels in the solve, and it cannot overflow.
+    // Euclidean distances by the SFU reciprocal square root (relative error
+    // ~2^-22, far below what the scores need).
     float del[KK];
 #pragma unroll
-    for (int t = 0; t < KK; ++t) del[t] = sqrtf(sd[t]);
+    for (int t = 0; t < KK; ++t) del[t] = sd[t] > 0.f ? sd[t] * rsqrtf(sd[t]) : 0.f;
     float wsum = 0.f, mean = 0.f;
 #pragma unroll
     for (int t = 0; t < KK; ++t)
@@ -541,8 +680,13 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
     for (int t = 0; t < KK; ++t) {
         float s = 0.f;
         if (t < m) {
-            const float f1 = flat ? 1.f : expf((del[0] - del[t]) * inv_sigma);
-            const float f2 = dk > 0.f ? -expm1f(kScoreEdge * fmaf(del[t], inv_dk, -1.f)) : 1.f;
+            // SFU exponentials (relative error ~1e-6); 1 - e^z by its series
+            // near z = 0, where the subtraction would cancel.
+            const float f1 = flat ? 1.f : __expf((del[0] - del[t]) * inv_sigma);
+            const float z = kScoreEdge * fmaf(del[t], inv_dk, -1.f);
+            const float f2 = dk > 0.f ? (z > -0.03125f ? -z * fmaf(z, fmaf(z, 1.f / 6.f, 0.5f), 1.f)
+                                                       : 1.f - __expf(z))
+                                      : 1.f;
             s = f1 * f2;
         }
         ss[t] = s;
@@ -567,70 +711,28 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
     float A00 = 0.f, A01 = 0.f, A11 = 0.f, B0 = 0.f, B1 = 0.f, rho = 0.f;
     pair_sums<D, KK, 0>(sd, nb, ss, m, Lg, lo2, l0, a, 0.f, 0.f, A00, A01, A11, B0, B1, rho);
 
-    // Step 4: FP64 solve.
+    // Step 4: FP64 solve; near-singular systems go to the out-of-line path.
     const double a00 = A00, a01 = A01, a11 = A11, b0 = B0, b1 = B1;
-    double det = a00 * a11 - a01 * a01;
+    const double det = a00 * a11 - a01 * a01;
     const double tr = a00 + a11;
-    if (tr > 0.0 && det <= kDetRecheck * tr * tr) {
-        // A00 A11 - A01^2 from FP32 sums cannot resolve det/trace^2 below
-        // ~1e-6.  Recompute the small eigenvalue as the Rayleigh quotient
-        // n^T A n along the minor eigenvector n of the FP32 matrix: a sum of
-        // non-negative terms w (h.n)^2 / r over the pairs, free of
-        // cancellation, and accurate to second order in the error of n.
-        const double disc = sqrt((a00 - a11) * (a00 - a11) + 4.0 * a01 * a01);
-        const double lmax = 0.5 * (tr + disc);
-        // two candidate major eigenvectors; take the better conditioned one
-        const double va0 = a01, va1 = lmax - a00, vb0 = lmax - a11, vb1 = a01;
-        const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
-        const double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
-        const double nn = sqrt(ga >= gb ? ga : gb);
-        if (nn > 0.0) {
-            // minor direction: the major one turned by 90 degrees
-            const double lmin = (double)minor_rayleigh<D, KK>(
-                sd, nb, ss, m, Lg, lo2, l0, a, (float)(-v1 / nn), (float)(v0 / nn));
-            det = lmin * (tr - lmin);
-        }
-    }
     double px, py;
-    if (det > kDetEps * tr * tr) {
-        const double id = 1.0 / det;
+    if (__builtin_expect(det > kDetRecheck * tr * tr, 1)) {
+        const double id = drcp(det);
         px = (b0 * a11 - a01 * b1) * id;
         py = (a00 * b1 - a01 * b0) * id;
     } else {
-        // Rank one (or zero): least-norm solution about the score-weighted
-        // centroid of the scored 2-D landmarks (plain mean if all scores are 0).
-        double c0, c1;
-        if (Ssum > 0.f) {
-            c0 = (double)C0 / (double)Ssum;
-            c1 = (double)C1 / (double)Ssum;
-        } else {
-            c0 = (double)M0 / (double)m;
-            c1 = (double)M1 / (double)m;
+        SlowSolve in;
+        in.A00 = A00; in.A01 = A01; in.A11 = A11; in.B0 = B0; in.B1 = B1;
+        in.C0 = C0; in.C1 = C1; in.Ssum = Ssum; in.M0 = M0; in.M1 = M1; in.m = m;
+        float tsd[KK], tss[KK];
+#pragma unroll
+        for (int t = 0; t < KK; ++t) {
+            tsd[t] = sd[t];
+            tss[t] = ss[t];
         }
-        if (tr == 0.0) {
-            px = c0;
-            py = c1;
-        } else {
-            const double disc = sqrt((a00 - a11) * (a00 - a11) + 4.0 * a01 * a01);
-            const double lam = 0.5 * (tr + disc);
-            double va0 = a01, va1 = lam - a00, vb0 = lam - a11, vb1 = a01;
-            const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
-            double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
-            double nn = ga >= gb ? ga : gb;
-            if (nn == 0.0) {
-                v0 = 1.0;
-                v1 = 0.0;
-                nn = 1.0;
-            }
-            nn = sqrt(nn);
-            v0 /= nn;
-            v1 /= nn;
-            const double r0 = b0 - (a00 * c0 + a01 * c1);
-            const double r1 = b1 - (a01 * c0 + a11 * c1);
-            const double t = (v0 * r0 + v1 * r1) / lam;
-            px = c0 + t * v0;
-            py = c1 + t * v1;
-        }
+        const double2 r = solve_slow<D, KK>(in, tsd, tss, nb, Lg, lo2, l0, a);
+        px = r.x;
+        py = r.y;
     }
     return make_float2((float)(px + (double)l0.x), (float)(py + (double)l0.y));
 }
@@ -845,9 +947,19 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
         float sd[KK];
         int si[KK];
         const bool cert = rerank<D, KC, KK>(xr, keys, Lg, mask, a.L, a.k, M, q, sd, si);
-        if (!cert) {
+        if (__builtin_expect(!cert, 0)) {
             if (active) atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
-            exact_rescan<D, KK>(xr, Lg, a.L, sd, si);
+            float4 tx[D / 4];
+            float tsd[KK];
+            int tsi[KK];
+#pragma unroll
+            for (int e = 0; e < D / 4; ++e) tx[e] = xr[e];
+            exact_rescan<D, KK>(tx, Lg, a.L, tsd, tsi);
+#pragma unroll
+            for (int t = 0; t < KK; ++t) {
+                sd[t] = tsd[t];
+                si[t] = tsi[t];
+            }
         }
 
         if (a.mode == kKnn) {

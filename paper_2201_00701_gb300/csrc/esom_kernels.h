@@ -27,7 +27,6 @@ struct FusedArgs {
     const float *lmax;    // largest landmark norm (one float)
     int L, k;
     float boost, adjust;
-    int adjust_mode;      // 0 general, 1 adjust == 1, 2 adjust == 0
     float *out;           // n x 2 (project)
     int *idx;             // n x k (knn)
     float *dist2;         // n x k (knn, nullable)

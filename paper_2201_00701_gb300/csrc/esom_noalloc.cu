@@ -132,7 +132,6 @@ extern "C" esom_status esom_project_noalloc(const float *points, int64_t n, cons
     a.k = k;
     a.boost = boost;
     a.adjust = adjust;
-    a.adjust_mode = adjust == 1.0f ? 1 : (adjust == 0.0f ? 2 : 0);
     a.out = out;
     a.mode = esom::kProject;
     a.chunk = chunk;
