@@ -145,6 +145,44 @@ typedef struct {
 
 esom_status esom_get_config(esom_handle h, esom_config *cfg);
 
+/* ---------------------------------------------------------------------------
+ * Batched projection: many datasets of uneven n, d and L through one plan.
+ * Each item names a handle whose landmarks it uses (d, L and k come from the
+ * handle), its points (n x d device, 16-byte aligned), its output (n x 2
+ * device, 8-byte aligned) and boost/adjust.  The plan groups items by (d, k
+ * capacity); each group is ONE launch of a persistent kernel whose blocks
+ * walk contiguous, cost-balanced ranges of the group's 256-point tiles.
+ * Handles and buffers must stay valid while the plan exists; landmark
+ * updates through the handles are picked up by later runs.  The paper has
+ * no batched form (its benchmark runs one dataset at a time, Section 4.1). */
+typedef struct esom_batch_ctx *esom_batch;
+
+typedef struct {
+    esom_handle landmarks;
+    const float *points;
+    int64_t n;
+    float *out;
+    float boost, adjust;
+} esom_batch_item;
+
+/* Builds the plan (allocates its device tables).  autotune != 0 times
+ * candidate launch shapes of every group on the batch itself (running it a
+ * few times, so the outputs are written) and keeps the fastest. */
+esom_status esom_batch_create(const esom_batch_item *items, int count, int autotune,
+                              esom_batch *out);
+
+/* Enqueues the plan's launches (one per group) on `stream`. */
+esom_status esom_batch_run(esom_batch b, esom_stream_t stream);
+
+/* Same as esom_batch_run, replayed from a CUDA graph captured on the first
+ * call (one graph launch per run). */
+esom_status esom_batch_run_graph(esom_batch b, esom_stream_t stream);
+
+/* JSON description of the plan: groups, tiles, grid, chosen shape. */
+const char *esom_batch_plan(esom_batch b);
+
+esom_status esom_batch_destroy(esom_batch b);
+
 /* Projection without any device allocation, for callers that cannot call
  * cudaMalloc (for example an application whose device memory all belongs to
  * its own pool allocator, or a frame loop that must not risk the device-wide

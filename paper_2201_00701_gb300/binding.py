@@ -38,6 +38,12 @@ class _Stats(ctypes.Structure):
     _fields_ = [("points", ctypes.c_uint64), ("rescans", ctypes.c_uint64)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("landmarks", ctypes.c_void_p), ("points", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("out", ctypes.c_void_p),
+                ("boost", ctypes.c_float), ("adjust", ctypes.c_float)]
+
+
 class _Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("d", "L", "k", "kc", "threads_per_block", "blocks_per_sm", "num_sms",
@@ -76,6 +82,11 @@ def load(build_if_missing: bool = False):
         "esom_get_config": ([P, ctypes.POINTER(_Config)], I),
         "esom_project_noalloc": ([P, I64, P, P, I, I, I, P, F, F, P], I),
         "esom_get_stats": ([P, P, ctypes.POINTER(_Stats), I], I),
+        "esom_batch_create": ([ctypes.POINTER(BatchItem), I, I, ctypes.POINTER(P)], I),
+        "esom_batch_run": ([P, P], I),
+        "esom_batch_run_graph": ([P, P], I),
+        "esom_batch_plan": ([P], ctypes.c_char_p),
+        "esom_batch_destroy": ([P], I),
         "esom_destroy": ([P], I),
         "esom_last_error": ([], ctypes.c_char_p),
         "esom_status_string": ([I], ctypes.c_char_p),
@@ -156,6 +167,30 @@ def esom_project_noalloc(points_ptr: int, n: int, hi_ptr: int, lo_ptr: int, d: i
     """Projection with no device allocation (scratch in a fixed device array)."""
     return load().esom_project_noalloc(points_ptr, n, hi_ptr, lo_ptr, d, L, k, out_ptr, boost,
                                        adjust, stream)
+
+
+def esom_batch_create(items, autotune: bool = False):
+    """items: sequence of BatchItem.  Returns (status, batch)."""
+    arr = (BatchItem * len(items))(*items)
+    b = ctypes.c_void_p()
+    st = load().esom_batch_create(arr, len(items), int(autotune), ctypes.byref(b))
+    return st, b.value
+
+
+def esom_batch_run(b, stream: int = 0) -> int:
+    return load().esom_batch_run(b, stream)
+
+
+def esom_batch_run_graph(b, stream: int = 0) -> int:
+    return load().esom_batch_run_graph(b, stream)
+
+
+def esom_batch_plan(b) -> str:
+    return load().esom_batch_plan(b).decode()
+
+
+def esom_batch_destroy(b) -> int:
+    return load().esom_batch_destroy(b)
 
 
 def esom_destroy(h) -> int:

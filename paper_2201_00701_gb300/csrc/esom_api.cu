@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "esom.h"
+#include "esom_ctx.h"
 #include "esom_kernels.h"
 
 using esom::FusedArgs;
@@ -35,6 +36,28 @@ constexpr long long kHostChunk = 1 << 20;
 }  // namespace
 
 namespace esom {
+void fill_args(const esom_ctx *h, const float *points, long long n, float *out, float boost,
+               float adjust, FusedArgs *a) {
+    memset(a, 0, sizeof(*a));
+    a->X = points;
+    a->n = n;
+    a->hi = h->hi;
+    a->lo = h->lo;
+    a->norms = h->norms;
+    a->lmax = reinterpret_cast<const float *>(h->status + 1);
+    key_layout(h->L, &a->key_mask, &a->key_quant);
+    a->L = h->L;
+    a->k = h->k;
+    a->boost = boost;
+    a->adjust = adjust;
+    a->out = out;
+    a->mode = kProject;
+    a->chunk = h->chunk;
+    a->nchunks = h->nchunks;
+    a->ntiles = (n + kThreads - 1) / kThreads;
+    a->status = h->status;
+}
+
 int set_error(int s, const char *msg) {
     snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
     return s;
@@ -77,28 +100,7 @@ cudaError_t launch_landmark_prep(float *hi, int L, int D, float *norms, float *l
 }
 }  // namespace esom
 
-struct esom_ctx {
-    int d = 0, L = 0, k = 0, kc = 0, dev = 0;
-    float *hi = nullptr;   // L x d
-    float *lo = nullptr;   // L x 2
-    float *norms = nullptr; // squared landmark norms, padded to a multiple of 4
-    int *status = nullptr; // device status word; the float after it: largest norm
-    uint64_t version = 0;
-    const KernelOps *ops = nullptr;
-    int num_sms = 0;
-    int forced_chunk = 0;
-    uint64_t points = 0;   // points handed to the kernels since the last stats reset
-    // launch configuration (derived from L, d and the chunk choice)
-    int chunk = 0, nchunks = 0, blocks_per_sm = 0;
-    size_t smem = 0;
-    // host-buffer pipeline state (created on first use)
-    float *stage_x[2] = {nullptr, nullptr};
-    float *stage_out[2] = {nullptr, nullptr};
-    cudaStream_t s_in = nullptr, s_out = nullptr;
-    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
-                ev_free[2] = {nullptr, nullptr}, ev_start = nullptr;
-    std::mutex host_mu;
-};
+
 
 namespace {
 
@@ -141,26 +143,10 @@ esom_status check_device(const esom_ctx *h) {
 esom_status launch(esom_ctx *h, const float *points, long long n, float *out, int *idx,
                    float *dist2, float boost, float adjust, int mode, cudaStream_t stream) {
     FusedArgs a;
-    memset(&a, 0, sizeof(a));
-    a.X = points;
-    a.n = n;
-    a.hi = h->hi;
-    a.lo = h->lo;
-    a.norms = h->norms;
-    a.lmax = reinterpret_cast<const float *>(h->status + 1);
-    esom::key_layout(h->L, &a.key_mask, &a.key_quant);
-    a.L = h->L;
-    a.k = h->k;
-    a.boost = boost;
-    a.adjust = adjust;
-    a.out = out;
+    esom::fill_args(h, points, n, out, boost, adjust, &a);
     a.idx = idx;
     a.dist2 = dist2;
     a.mode = mode;
-    a.chunk = h->chunk;
-    a.nchunks = h->nchunks;
-    a.ntiles = (n + esom::kThreads - 1) / esom::kThreads;
-    a.status = h->status;
     long long grid = (long long)h->blocks_per_sm * h->num_sms;
     if (grid > a.ntiles) grid = a.ntiles;
     cudaError_t e = h->ops->launch(a, (int)grid, h->smem, stream);

@@ -1,0 +1,38 @@
+// Handle state shared by the C ABI translation units (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "esom_kernels.h"
+
+struct esom_ctx {
+    int d = 0, L = 0, k = 0, kc = 0, dev = 0;
+    float *hi = nullptr;   // L x d
+    float *lo = nullptr;   // L x 2
+    float *norms = nullptr; // squared landmark norms, padded to a multiple of 4
+    int *status = nullptr; // device status word; the float after it: largest norm
+    uint64_t version = 0;
+    const esom::KernelOps *ops = nullptr;
+    int num_sms = 0;
+    int forced_chunk = 0;
+    uint64_t points = 0;   // points handed to the kernels since the last stats reset
+    // launch configuration (derived from L, d and the chunk choice)
+    int chunk = 0, nchunks = 0, blocks_per_sm = 0;
+    size_t smem = 0;
+    // host-buffer pipeline state (created on first use)
+    float *stage_x[2] = {nullptr, nullptr};
+    float *stage_out[2] = {nullptr, nullptr};
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
+                ev_free[2] = {nullptr, nullptr}, ev_start = nullptr;
+    std::mutex host_mu;
+};
+
+namespace esom {
+// Fills the per-launch arguments for `n` points of handle h (mode project).
+void fill_args(const esom_ctx *h, const float *points, long long n, float *out, float boost,
+               float adjust, FusedArgs *a);
+}  // namespace esom

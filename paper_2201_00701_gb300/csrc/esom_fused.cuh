@@ -986,6 +986,204 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched form: several datasets of the same D and list capacity in one
+// launch.  Each block takes a contiguous, cost-balanced range of the global
+// tile list, so it switches dataset at most a few times; a dataset whose
+// landmarks are resident is staged into shared memory when the block reaches
+// its first tile, a chunked one is streamed chunk by chunk through the one
+// landmark buffer.  The per-tile work is the single-launch kernel's.
+
+template <int D, int KC, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchArgs B) {
+    constexpr int KK = KC - 4;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // [0] points, [1] landmarks
+    volatile int &s_abort = *reinterpret_cast<int *>(smem + 64);
+    float *sX = reinterpret_cast<float *>(smem + kBarrierBytes);
+    const long long t0 = B.cta_begin[blockIdx.x], t1 = B.cta_begin[blockIdx.x + 1];
+    if (t0 >= t1) return;
+    // the landmark buffer holds the group's largest resident set or chunk
+    int cap = 0;
+    {
+        const int i0 = B.tile_item[t0], i1 = B.tile_item[t1 - 1];
+        for (int i = i0; i <= i1; ++i) cap = max(cap, B.items[i].chunk);
+    }
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    uint32_t phX = 0, phL = 0;
+    bool pendX = false, pendL = false;
+    int cur = -1;  // dataset whose landmarks are resident in shared memory
+    auto abort_block = [&]() {
+        if (tid == 0) {
+            atomicOr(B.status, kErrWaitTimeout);
+            if (pendX) mbar_wait(&bars[0], phX);
+            if (pendL) mbar_wait(&bars[1], phL);
+        }
+    };
+    constexpr float kGamma = (2.25f * D + 10.f) * kU * 1.25f;
+
+    for (long long t = t0; t < t1; ++t) {
+        const int it = B.tile_item[t];
+        const FusedArgs &a = B.items[it];
+        const long long row0 = (t - B.tile_base[it]) * kThreads;
+        const int rows = (int)(a.n - row0 < kThreads ? a.n - row0 : kThreads);
+        float *sL = sX + kThreads * D;
+        const int cap4 = (cap + 3) & ~3;
+        float *sN = sL + (size_t)cap * D;
+        uint32_t *qk = reinterpret_cast<uint32_t *>(sN + cap4);
+        const size_t chunk_floats = (size_t)a.chunk * D;
+
+        bool ok = true;
+        if (a.nchunks == 1 && it != cur) {
+            __syncthreads();  // the previous landmarks are no longer read
+            if (tid == 0) {
+                const uint32_t rb = (uint32_t)((size_t)a.L * D * sizeof(float));
+                const uint32_t nb = (uint32_t)(((a.L + 3) & ~3) * sizeof(float));
+                mbar_expect_tx(&bars[1], rb + nb);
+                copy_pieces(sL, a.hi, rb, &bars[1]);
+                copy_pieces(sN, a.norms, nb, &bars[1]);
+                pendL = true;
+            }
+            ok = mbar_wait(&bars[1], phL);
+            if (tid == 0 && ok) pendL = false;
+            phL ^= 1;
+            cur = it;
+        }
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)((size_t)rows * D * sizeof(float));
+            mbar_expect_tx(&bars[0], bytes);
+            copy_pieces(sX, a.X + row0 * D, bytes, &bars[0]);
+            pendX = true;
+        }
+        ok = mbar_wait(&bars[0], phX) && ok;
+        if (!ok) s_abort = 1;
+        const bool active = tid < rows;
+        float4 xr[D / 4];
+        const float4 *xs = reinterpret_cast<const float4 *>(sX) + (size_t)tid * (D / 4);
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) xr[e] = active ? xs[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();  // point tile consumed; abort flag visible
+        if (s_abort) {
+            abort_block();
+            return;
+        }
+        phX ^= 1;
+        if (tid == 0) pendX = false;
+
+        float xx = 0.f;
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) {
+            xx = fmaf(xr[e].x, xr[e].x, xx);
+            xx = fmaf(xr[e].y, xr[e].y, xx);
+            xx = fmaf(xr[e].z, xr[e].z, xx);
+            xx = fmaf(xr[e].w, xr[e].w, xx);
+        }
+        const float sx = sqrtf(xx) + *a.lmax;
+        const float M = kGamma * sx * sx;
+        const uint32_t mask = a.key_mask;
+        const float q = a.key_quant;
+        float keys[KC];
+        ScanState st;
+        st.qn = 0;
+        st.thr = INFINITY;
+        for (int c = 0; c < a.nchunks; ++c) {
+            const int base = c * a.chunk;
+            const int cnt = a.L - base < a.chunk ? a.L - base : a.chunk;
+            if (a.nchunks > 1) {
+                __syncthreads();  // the previous chunk (or landmark set) is consumed
+                if (tid == 0) {
+                    const uint32_t rb = (uint32_t)((size_t)cnt * D * sizeof(float));
+                    const uint32_t nb = (uint32_t)(((cnt + 3) & ~3) * sizeof(float));
+                    mbar_expect_tx(&bars[1], rb + nb);
+                    copy_pieces(sL, a.hi + (size_t)c * chunk_floats, rb, &bars[1]);
+                    copy_pieces(sN, a.norms + (size_t)c * a.chunk, nb, &bars[1]);
+                    pendL = true;
+                }
+                if (!mbar_wait(&bars[1], phL)) s_abort = 1;
+                if (tid == 0) pendL = false;
+                phL ^= 1;
+                cur = -1;
+            }
+            int j_begin = 0;
+            if (c == 0) {
+                constexpr int KF = (KC + 7) & ~7;
+                const float4 *L4 = reinterpret_cast<const float4 *>(sL);
+                if (cnt >= KF) {
+                    float v[KF];
+                    screen_block<D, KF>(xr, -0.5f * xx, L4, sN, 0, v);
+#pragma unroll
+                    for (int t2 = 0; t2 < KF; ++t2) v[t2] = make_key(v[t2], (uint32_t)t2, mask);
+                    key_sort<KF>(v);
+#pragma unroll
+                    for (int t2 = 0; t2 < KC; ++t2) keys[t2] = v[t2];
+                    j_begin = KF;
+                } else {
+#pragma unroll
+                    for (int t2 = 0; t2 < KC; ++t2)
+                        keys[t2] = t2 < cnt ? make_key(screen_row<D>(xr, -0.5f * xx, sN[t2], L4,
+                                                                     t2),
+                                                       (uint32_t)t2, mask)
+                                            : INFINITY;
+                    key_sort<KC>(keys);
+                    j_begin = KC < cnt ? KC : cnt;
+                }
+                st.thr = push_threshold(at<KC>(keys, a.k - 1), M, q);
+            }
+            scan_chunk<D, KC>(xr, -0.5f * xx, sL, sN, j_begin, cnt, base, mask, keys, st, qk, tid,
+                              a.k, M, q);
+        }
+        if (a.nchunks > 1) {
+            __syncthreads();
+            if (s_abort) {
+                abort_block();
+                return;
+            }
+        }
+        queue_flush<KC>(keys, st, qk, tid, a.k, M, q);
+
+        const float4 *Lg = a.nchunks == 1 ? reinterpret_cast<const float4 *>(sL)
+                                           : reinterpret_cast<const float4 *>(a.hi);
+        float sd[KK];
+        int si[KK];
+        const bool cert = rerank<D, KC, KK>(xr, keys, Lg, mask, a.L, a.k, M, q, sd, si);
+        if (__builtin_expect(!cert, 0)) {
+            if (active) atomicAdd(reinterpret_cast<unsigned *>(B.status) + 2, 1u);
+            float4 tx[D / 4];
+            float tsd[KK];
+            int tsi[KK];
+#pragma unroll
+            for (int e = 0; e < D / 4; ++e) tx[e] = xr[e];
+            exact_rescan<D, KK>(tx, Lg, a.L, tsd, tsi);
+#pragma unroll
+            for (int t2 = 0; t2 < KK; ++t2) {
+                sd[t2] = tsd[t2];
+                si[t2] = tsi[t2];
+            }
+        }
+        uint32_t *nb = qk + tid;
+#pragma unroll
+        for (int s2 = 0; s2 < KK; s2 += 2)
+            nb[(s2 >> 1) * kThreads] = (uint32_t)si[s2] | ((uint32_t)si[s2 + 1] << 16);
+        const float2 p = project_point<D, KK>(sd, nb, Lg,
+                                              reinterpret_cast<const float2 *>(a.lo), a);
+        if (active) reinterpret_cast<float2 *>(a.out)[row0 + tid] = p;
+    }
+}
+
+template <int D, int KC, int MINB>
+cudaError_t launch_batch(const BatchArgs &b, int grid, size_t smem, cudaStream_t stream) {
+    batch_kernel<D, KC, MINB><<<grid, kThreads, smem, stream>>>(b);
+    return cudaGetLastError();
+}
+
 template <int D, int KC, int MINB>
 cudaError_t launch_fused(const FusedArgs &a, int grid, size_t smem, cudaStream_t stream) {
     fused_kernel<D, KC, MINB><<<grid, kThreads, smem, stream>>>(a);
@@ -1003,7 +1201,9 @@ struct Instance {
 template <int D, int KC>
 const KernelOps Instance<D, KC>::ops = {
     reinterpret_cast<const void *>(&fused_kernel<D, KC, Instance<D, KC>::kMinBlocks>), KC,
-    &launch_fused<D, KC, Instance<D, KC>::kMinBlocks>};
+    &launch_fused<D, KC, Instance<D, KC>::kMinBlocks>,
+    reinterpret_cast<const void *>(&batch_kernel<D, KC, Instance<D, KC>::kMinBlocks>),
+    &launch_batch<D, KC, Instance<D, KC>::kMinBlocks>};
 
 // Table of the list capacities instantiated for each D.
 #define ESOM_DEFINE_D(DV)                                            \

@@ -39,10 +39,24 @@ struct FusedArgs {
     int *status;          // device status words: [0] error bits, [2] rescan count
 };
 
+// Many datasets of one (D, list capacity) in one launch: every block walks a
+// contiguous range [cta_begin[b], cta_begin[b+1]) of the global tile list;
+// tile t belongs to dataset tile_item[t], whose local tile index is
+// t - tile_base[item].
+struct BatchArgs {
+    const FusedArgs *items;     // per dataset (mode = project), device memory
+    const long long *tile_base; // first global tile of each dataset
+    const int *tile_item;       // dataset of each global tile
+    const long long *cta_begin; // grid + 1 range boundaries
+    int *status;                // error bits, as for a single launch
+};
+
 struct KernelOps {
     const void *func;     // the __global__ function (for attributes / occupancy)
     int kc;               // compile-time list capacity
     cudaError_t (*launch)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
+    const void *batch_func;
+    cudaError_t (*launch_batch)(const BatchArgs &, int grid, size_t smem, cudaStream_t);
 };
 
 // Returns the instantiation for dimension D and list capacity kc, or nullptr.
@@ -95,6 +109,17 @@ inline size_t fused_smem_bytes(int D, int chunk, int nchunks) {
     s += nbuf * chunk * D * sizeof(float);                    // landmark rows
     s += nbuf * (size_t)((chunk + 3) & ~3) * sizeof(float);   // landmark norms
     s += (size_t)kQueue * kThreads * sizeof(unsigned);        // candidate queue
+    return s;
+}
+
+// Shared memory of the batched kernel: one landmark buffer of `chunk` rows
+// (the largest resident set or chunk of the group).
+inline size_t batch_smem_bytes(int D, int chunk) {
+    size_t s = kBarrierBytes;
+    s += (size_t)kThreads * D * sizeof(float);
+    s += (size_t)chunk * D * sizeof(float);
+    s += (size_t)((chunk + 3) & ~3) * sizeof(float);
+    s += (size_t)kQueue * kThreads * sizeof(unsigned);
     return s;
 }
 
