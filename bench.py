@@ -337,6 +337,81 @@ def run_esom(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_batch64(args):
+    """--workload batch64: 64 datasets of uneven n, d, L, k.  Times 64 separate
+    esom_project launches, one esom_batch_run (one launch per (d, k-capacity)
+    group, autotuned) and its CUDA-graph replay, on the same buffers."""
+    import torch
+
+    from paper_2201_00701_gb300 import binding, workloads
+
+    torch.cuda.set_device(0)
+    binding.load()
+    params = workloads.batch64(n_max=args.batch_n_max)
+    handles, items, bufs, ws = [], [], [], []
+    for p in params:
+        w = workloads.batch_member(p)
+        P = binding.Projector(w.d, w.L, w.k)
+        hi, lo = torch.from_numpy(w.hi).cuda(), torch.from_numpy(w.lo).cuda()
+        P.set_landmarks(hi, lo)
+        X = torch.from_numpy(w.X).cuda()
+        out = torch.empty((w.n, 2), device="cuda")
+        items.append(binding.BatchItem(P.h, X.data_ptr(), w.n, out.data_ptr(), w.boost, w.adjust))
+        handles.append(P)
+        bufs.append((X, hi, lo, out))
+        ws.append((w.n, w.d, w.L, w.k))
+    total = sum(n for n, _, _, _ in ws)
+    fmas = sum(n * (L * d + k * k * d) for n, d, L, k in ws)
+    st, b = binding.esom_batch_create(items, True)
+    binding.check(st)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def separate():
+        for P, (X, _, _, out), (n, _, _, _), it in zip(handles, bufs, ws, items):
+            binding.check(binding.esom_project(P.h, X.data_ptr(), n, out.data_ptr(), it.boost,
+                                               it.adjust, stream.cuda_stream))
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            flush.zero_()
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    t_sep = timed(separate)
+    t_batch = timed(lambda: binding.check(binding.esom_batch_run(b, stream.cuda_stream)))
+    t_graph = timed(lambda: binding.check(binding.esom_batch_run_graph(b, stream.cuda_stream)))
+    props = torch.cuda.get_device_properties(0)
+    peak = 2.0 * 128 * props.multi_processor_count * 2070e6 / 1e12
+    achieved = 2.0 * fmas / (t_graph / 1e3) / 1e12
+    line = {
+        "metric": baseline_metric(), "value": total / (t_graph / 1e3), "unit": "points/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_graph,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "batch64", "datasets": len(ws), "points": total,
+                   "l2": "flushed between steps by an untimed 256 MiB write",
+                   "plan": json.loads(binding.esom_batch_plan(b))},
+        "batch": {"separate_launches_ms": t_sep, "batch_run_ms": t_batch,
+                  "batch_graph_ms": t_graph, "speedup_vs_separate": t_sep / t_graph},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak},
+    }
+    print(json.dumps(line), flush=True)
+    binding.esom_batch_destroy(b)
+    for P in handles:
+        P.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,10 +422,15 @@ def main():
     ap.add_argument("--ref-points", type=int, default=4000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64"])
+    ap.add_argument("--batch-n-max", type=float, default=2e6)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_setup()
+    if args.workload == "batch64":
+        run_batch64(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

@@ -484,6 +484,67 @@ __device__ __forceinline__ int nb_at(const uint32_t *col, int t) {
 // D_uv uses the law of cosines on the exact squared distances:
 // <X - L_u, L_v - L_u> = (|X - L_u|^2 + |L_v - L_u|^2 - |X - L_v|^2) / 2.
 
+// One pair's contribution: D_uv by the law of cosines, the 2-D operator,
+// the weight w = s_u s_v r^-adjust, and the normal-system terms.  `ok` is
+// false when L_u = L_v or l_u = l_v (the pair is skipped).
+struct PairTerm {
+    float a00, a01, a11, b0, b1, rho;
+    bool ok;
+};
+
+template <int D, int PASS>
+__device__ __forceinline__ PairTerm pair_term(const float4 (&lu)[D / 4], float2 lut, float lux,
+                                              float luy, float su, float du, int iv, float sv,
+                                              float dv, const float4 *Lg, const float2 *lo2,
+                                              float adjust, float nx, float ny) {
+    const float4 *Lv = Lg + (size_t)iv * (D / 4);
+    const int fv = swz(D, iv);
+    float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+#pragma unroll
+    for (int e = 0; e < D / 4; ++e) {
+        const float4 lv = Lv[e ^ fv];
+        const float ex = lv.x - lu[e].x, ey = lv.y - lu[e].y;
+        const float ez = lv.z - lu[e].z, ew = lv.w - lu[e].w;
+        q0 = fmaf(ex, ex, q0);
+        q1 = fmaf(ey, ey, q1);
+        q2 = fmaf(ez, ez, q2);
+        q3 = fmaf(ew, ew, q3);
+    }
+    const float qq = (q0 + q1) + (q2 + q3);
+    const float2 lvt = __ldg(&lo2[iv]);
+    const float hx = lvt.x - lut.x, hy = lvt.y - lut.y;
+    const float r = fmaf(hx, hx, hy * hy);
+    PairTerm t;
+    t.ok = qq > 0.f && r > 0.f;
+    const float ir = rcp_fast(r);
+    // r^-adjust by the SFU (relative error ~1e-6)
+    const float w = su * sv * exp2f_fast(-adjust * log2f_fast(r));
+    const float wr = w * ir;
+    if (PASS == 0) {
+        const float Duv = fmaf(0.5f * (du - dv), rcp_fast(qq), 0.5f);
+        const float rhs = fmaf(fmaf(hx, lux, hy * luy), ir, Duv);
+        t.a00 = wr * hx * hx;
+        t.a01 = wr * hx * hy;
+        t.a11 = wr * hy * hy;
+        const float wrhs = w * rhs;
+        t.b0 = wrhs * hx;
+        t.b1 = wrhs * hy;
+        t.rho = 0.f;
+    } else {
+        const float tt = fmaf(hx, nx, hy * ny);
+        t.rho = wr * tt * tt;
+        t.a00 = t.a01 = t.a11 = t.b0 = t.b1 = 0.f;
+    }
+    return t;
+}
+
+// Step 3: pair terms over u < v < m.  PASS 0 accumulates the normal system
+// (A, b); PASS 1 accumulates rho = sum w (h.n)^2 / r for a unit 2-D direction
+// n (the Rayleigh quotient n^T A n).  D_uv uses the law of cosines on the
+// exact squared distances:
+// <X - L_u, L_v - L_u> = (|X - L_u|^2 + |L_v - L_u|^2 - |X - L_v|^2) / 2.
+// The v loop runs in groups of two pairs with independent chains; pairs
+// outside u < v < m inside a group are masked by selects.
 template <int D, int KK, int PASS>
 __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t *nb,
                                           const float (&ss)[KK], int m, const float4 *Lg,
@@ -508,45 +569,29 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
         const float2 lut = __ldg(&lo2[iu]);
         const float lux = lut.x - l0.x, luy = lut.y - l0.y;  // l_u relative to l_0
 #pragma unroll
-        for (int v = 1; v < KK; ++v) {
-            if (v > u && v < m) {
-                const int iv = nb_at(nb, v);
-                const float4 *Lv = Lg + (size_t)iv * (D / 4);
-                const int fv = swz(D, iv);
-                float q0 = 0.f, q1 = 0.f;
-#pragma unroll
-                for (int e = 0; e < D / 4; ++e) {
-                    const float4 lv = Lv[e ^ fv];
-                    const float ex = lv.x - lu[e].x, ey = lv.y - lu[e].y;
-                    const float ez = lv.z - lu[e].z, ew = lv.w - lu[e].w;
-                    q0 = fmaf(ex, ex, q0);
-                    q1 = fmaf(ey, ey, q1);
-                    q0 = fmaf(ez, ez, q0);
-                    q1 = fmaf(ew, ew, q1);
-                }
-                const float qq = q0 + q1;
-                const float2 lvt = __ldg(&lo2[iv]);
-                const float hx = lvt.x - lut.x, hy = lvt.y - lut.y;
-                const float r = fmaf(hx, hx, hy * hy);
-                if (qq > 0.f && r > 0.f) {
-                    const float ir = rcp_fast(r);
-                    // r^-adjust by the SFU (relative error ~1e-6), the same code
-                    // for every adjust so the loop is not duplicated per case
-                    const float w = su * ss[v] * exp2f_fast(-a.adjust * log2f_fast(r));
-                    const float wr = w * ir;
-                    if (PASS == 0) {
-                        const float Duv = 0.5f * (du - sd[v] + qq) * rcp_fast(qq);
-                        const float rhs = fmaf(fmaf(hx, lux, hy * luy), ir, Duv);
-                        A00 = fmaf(wr * hx, hx, A00);
-                        A01 = fmaf(wr * hx, hy, A01);
-                        A11 = fmaf(wr * hy, hy, A11);
-                        const float wrhs = w * rhs;
-                        B0 = fmaf(wrhs, hx, B0);
-                        B1 = fmaf(wrhs, hy, B1);
-                    } else {
-                        const float t = fmaf(hx, nx, hy * ny);
-                        rho = fmaf(wr * t, t, rho);
-                    }
+        for (int v0 = 1; v0 < KK; v0 += 2) {
+            if (v0 + 1 > u && v0 < m) {
+                const PairTerm c0 = pair_term<D, PASS>(lu, lut, lux, luy, su, du, nb_at(nb, v0),
+                                                       ss[v0], sd[v0], Lg, lo2, a.adjust, nx, ny);
+                const bool k0 = c0.ok && v0 > u;
+                A00 = k0 ? A00 + c0.a00 : A00;
+                A01 = k0 ? A01 + c0.a01 : A01;
+                A11 = k0 ? A11 + c0.a11 : A11;
+                B0 = k0 ? B0 + c0.b0 : B0;
+                B1 = k0 ? B1 + c0.b1 : B1;
+                rho = k0 ? rho + c0.rho : rho;
+                if (v0 + 1 < KK) {
+                    const int v1 = v0 + 1 < KK ? v0 + 1 : v0;
+                    const PairTerm c1 =
+                        pair_term<D, PASS>(lu, lut, lux, luy, su, du, nb_at(nb, v1), ss[v1],
+                                           sd[v1], Lg, lo2, a.adjust, nx, ny);
+                    const bool k1 = c1.ok && v1 < m;
+                    A00 = k1 ? A00 + c1.a00 : A00;
+                    A01 = k1 ? A01 + c1.a01 : A01;
+                    A11 = k1 ? A11 + c1.a11 : A11;
+                    B0 = k1 ? B0 + c1.b0 : B0;
+                    B1 = k1 ? B1 + c1.b1 : B1;
+                    rho = k1 ? rho + c1.rho : rho;
                 }
             }
         }
