@@ -183,6 +183,71 @@ const char *esom_batch_plan(esom_batch b);
 
 esom_status esom_batch_destroy(esom_batch b);
 
+/* ---------------------------------------------------------------------------
+ * SOM landmark update (Section 3.2.2: the high-dimensional landmarks are
+ * trained as SOM weights on the topology of the 2-D landmarks, with a
+ * neighbourhood width sigma and a learning rate alpha).  One batch step:
+ *   L_j += alpha * ( sum_x h(j, b(x)) x / sum_x h(j, b(x)) - L_j ),
+ *   h(j, i) = exp(-|l_j - l_i|^2 / (2 sigma^2)),
+ * over the minibatch points x with best-matching landmarks b(x) =
+ * bmu[x * bmu_stride] (for example column 0 of esom_knn's idx, stride k);
+ * landmarks whose neighbourhood weight sums to ~0 are left unchanged.
+ * hi: L x d device (updated in place); lo: L x 2 device, 8-byte aligned;
+ * batch: b x d device, 16-byte aligned.  The paper gives no formula for the
+ * step; this batch form is this library's reading. */
+esom_status esom_som_update(float *hi, const float *lo, int d, int L, const float *batch,
+                            const int32_t *bmu, int bmu_stride, int64_t b, float alpha,
+                            float sigma, esom_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Frame server: sessions with resident points; each frame request runs one
+ * SOM step on a minibatch window of the session's points (chosen by a
+ * counter-based hash of the seed and the frame number), refreshes the
+ * handle's landmarks and re-projects all the session's points (the paper
+ * re-projects every point each frame, Section 5.1 and Section 6).
+ * Continuous batching: up to max_inflight frames of different sessions run
+ * at once (one stream per session, so they overlap on the GPU); a session's
+ * frames run in order; queued frames start, oldest arrival first, as slots
+ * free up.  A session is admitted only if its device memory fits the
+ * budget (ESOM_ENOMEM otherwise).  Times are seconds on the server's clock
+ * (esom_server_now); completion times come from GPU events. */
+typedef struct esom_server_ctx *esom_server;
+
+typedef struct {
+    int d, L, k;
+    int64_t n;
+    float boost, adjust;
+    float alpha, sigma;  /* SOM step; alpha = 0 or minibatch = 0: projection only */
+    int minibatch;
+    uint64_t seed;
+} esom_session_desc;
+
+typedef struct {
+    int session;
+    uint64_t frame;
+    double arrival, completion;
+} esom_frame_done;
+
+esom_status esom_server_create(uint64_t budget_bytes, int max_inflight, esom_server *out);
+/* points (n x d), hi (L x d), lo (L x 2): host or device; copied. */
+esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc,
+                                    const float *points, const float *hi, const float *lo,
+                                    int *session);
+double esom_server_now(esom_server s);
+/* Queues one frame of `session` that arrived at time `arrival`. */
+esom_status esom_server_submit(esom_server s, int session, double arrival);
+/* Collects finished frames (up to max) and starts queued ones in free
+ * slots; wait_all != 0 blocks until every queued frame has finished (or
+ * max records were filled). */
+esom_status esom_server_poll(esom_server s, int wait_all, esom_frame_done *done, int max,
+                             int *count);
+/* Device pointer to the session's latest coordinates (n x 2) and the
+ * number of frames it has completed. */
+esom_status esom_server_session_output(esom_server s, int session, const float **out,
+                                       uint64_t *frames);
+esom_status esom_server_memory(esom_server s, uint64_t *used, uint64_t *budget);
+esom_status esom_server_destroy(esom_server s);
+
 /* Projection without any device allocation, for callers that cannot call
  * cudaMalloc (for example an application whose device memory all belongs to
  * its own pool allocator, or a frame loop that must not risk the device-wide

@@ -64,6 +64,9 @@ class Oracle:
         lib.esom_oracle_fit.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, P, P,
                                         ctypes.c_double, P, P, P]
         lib.esom_oracle_fit.restype = None
+        lib.esom_oracle_som_step.argtypes = [P, P, ctypes.c_int, ctypes.c_int, P, P,
+                                             ctypes.c_int, ctypes.c_double, ctypes.c_double, P]
+        lib.esom_oracle_som_step.restype = None
         lib.esom_oracle_default_threads.argtypes = []
         lib.esom_oracle_default_threads.restype = ctypes.c_int
         self.lib = lib
@@ -103,6 +106,16 @@ class Oracle:
                                  _ptr(idx), _ptr(s), float(adjust), _ptr(out), _ptr(diag),
                                  ctypes.byref(br))
         return out, diag, int(br.value)
+
+    def som_step(self, hi, lo, batch, bmu, alpha: float, sigma: float):
+        """One batch SOM step; returns the new L x d landmarks (float64)."""
+        hi, lo, batch = _f32(hi), _f32(lo), _f32(batch)
+        bmu = np.ascontiguousarray(bmu, dtype=np.int32)
+        out = np.empty(hi.shape, np.float64)
+        self.lib.esom_oracle_som_step(_ptr(hi), _ptr(lo), hi.shape[1], hi.shape[0], _ptr(batch),
+                                      _ptr(bmu), batch.shape[0], float(alpha), float(sigma),
+                                      _ptr(out))
+        return out
 
     def project(self, X, hi, lo, k: int, boost: float, adjust: float, threads: int = 0,
                 diagnostics: bool = False):
@@ -152,3 +165,7 @@ def fit(x, hi, lo, idx, s, adjust):
 
 def project(X, hi, lo, k, boost, adjust, threads=0, diagnostics=False):
     return get().project(X, hi, lo, k, boost, adjust, threads, diagnostics)
+
+
+def som_step(hi, lo, batch, bmu, alpha, sigma):
+    return get().som_step(hi, lo, batch, bmu, alpha, sigma)

@@ -56,6 +56,8 @@
  *      2-D landmarks is returned: x = c + v (v . (b - A c)) / lambda, with
  *      lambda, v the largest eigenvalue / unit eigenvector of A.  If A = 0,
  *      x = c.  If every score is 0 the centroid is the plain mean.
+ *   R6 SOM step (used by the frame server, not by the projection): see
+ *      esom_oracle_som_step.
  *
  * Build: gcc -O2 -std=c11 -fPIC -shared -pthread (no -ffast-math).
  */
@@ -218,6 +220,35 @@ void esom_oracle_fit(const float *x, const float *hi, const float *lo, int d, in
         diag[5] = tr > 0.0 ? det / (tr * tr) : -1.0;
     }
     if (branch) *branch = br;
+}
+
+/* One batch SOM step on the high-dimensional landmarks (Section 3.2.2: the
+ * landmarks are trained as SOM weights on the topology of the 2-D landmarks,
+ * with neighbourhood width sigma and learning rate alpha).  The paper gives
+ * no formula; the reading used here (R6) is the batch step
+ *   L_j <- L_j + alpha (sum_x h(j,b(x)) x / sum_x h(j,b(x)) - L_j),
+ *   h(j,i) = exp(-|l_j - l_i|^2 / (2 sigma^2)),
+ * with b(x) the best-matching landmark of minibatch point x; a landmark whose
+ * weights sum to 0 is left unchanged.  hi_out (L x d) may not alias hi_in. */
+void esom_oracle_som_step(const float *hi_in, const float *lo, int d, int L, const float *batch,
+                          const int32_t *bmu, int b, double alpha, double sigma, double *hi_out)
+{
+    for (int j = 0; j < L; ++j) {
+        double hs = 0.0;
+        for (int t = 0; t < d; ++t) hi_out[(int64_t)j * d + t] = 0.0;
+        for (int x = 0; x < b; ++x) {
+            const int i = bmu[x];
+            double dx = (double)lo[2 * j] - (double)lo[2 * i];
+            double dy = (double)lo[2 * j + 1] - (double)lo[2 * i + 1];
+            double h = exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma));
+            hs += h;
+            for (int t = 0; t < d; ++t) hi_out[(int64_t)j * d + t] += h * (double)batch[(int64_t)x * d + t];
+        }
+        for (int t = 0; t < d; ++t) {
+            double l = (double)hi_in[(int64_t)j * d + t];
+            hi_out[(int64_t)j * d + t] = hs > 0.0 ? l + alpha * (hi_out[(int64_t)j * d + t] / hs - l) : l;
+        }
+    }
 }
 
 /* ------------------------------------------------------------------------- */

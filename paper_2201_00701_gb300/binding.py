@@ -44,6 +44,18 @@ class BatchItem(ctypes.Structure):
                 ("boost", ctypes.c_float), ("adjust", ctypes.c_float)]
 
 
+class SessionDesc(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("L", ctypes.c_int), ("k", ctypes.c_int),
+                ("n", ctypes.c_int64), ("boost", ctypes.c_float), ("adjust", ctypes.c_float),
+                ("alpha", ctypes.c_float), ("sigma", ctypes.c_float),
+                ("minibatch", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class FrameDone(ctypes.Structure):
+    _fields_ = [("session", ctypes.c_int), ("frame", ctypes.c_uint64),
+                ("arrival", ctypes.c_double), ("completion", ctypes.c_double)]
+
+
 class _Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("d", "L", "k", "kc", "threads_per_block", "blocks_per_sm", "num_sms",
@@ -87,6 +99,16 @@ def load(build_if_missing: bool = False):
         "esom_batch_run_graph": ([P, P], I),
         "esom_batch_plan": ([P], ctypes.c_char_p),
         "esom_batch_destroy": ([P], I),
+        "esom_som_update": ([P, P, I, I, P, P, I, I64, F, F, P], I),
+        "esom_server_create": ([ctypes.c_uint64, I, ctypes.POINTER(P)], I),
+        "esom_server_add_session": ([P, ctypes.POINTER(SessionDesc), P, P, P,
+                                     ctypes.POINTER(I)], I),
+        "esom_server_now": ([P], ctypes.c_double),
+        "esom_server_submit": ([P, I, ctypes.c_double], I),
+        "esom_server_poll": ([P, I, ctypes.POINTER(FrameDone), I, ctypes.POINTER(I)], I),
+        "esom_server_session_output": ([P, I, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_uint64)], I),
+        "esom_server_memory": ([P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], I),
+        "esom_server_destroy": ([P], I),
         "esom_destroy": ([P], I),
         "esom_last_error": ([], ctypes.c_char_p),
         "esom_status_string": ([I], ctypes.c_char_p),
@@ -191,6 +213,59 @@ def esom_batch_plan(b) -> str:
 
 def esom_batch_destroy(b) -> int:
     return load().esom_batch_destroy(b)
+
+
+def esom_som_update(hi_ptr: int, lo_ptr: int, d: int, L: int, batch_ptr: int, bmu_ptr: int,
+                    bmu_stride: int, b: int, alpha: float, sigma: float, stream: int = 0) -> int:
+    return load().esom_som_update(hi_ptr, lo_ptr, d, L, batch_ptr, bmu_ptr, bmu_stride, b, alpha,
+                                  sigma, stream)
+
+
+def esom_server_create(budget_bytes: int, max_inflight: int):
+    s = ctypes.c_void_p()
+    st = load().esom_server_create(int(budget_bytes), max_inflight, ctypes.byref(s))
+    return st, s.value
+
+
+def esom_server_add_session(s, desc: "SessionDesc", points_ptr: int, hi_ptr: int, lo_ptr: int):
+    sid = ctypes.c_int(-1)
+    st = load().esom_server_add_session(s, ctypes.byref(desc), points_ptr, hi_ptr, lo_ptr,
+                                        ctypes.byref(sid))
+    return st, sid.value
+
+
+def esom_server_now(s) -> float:
+    return float(load().esom_server_now(s))
+
+
+def esom_server_submit(s, session: int, arrival: float) -> int:
+    return load().esom_server_submit(s, session, arrival)
+
+
+def esom_server_poll(s, wait_all: bool = False, max_records: int = 1024):
+    """Returns (status, [FrameDone, ...])."""
+    buf = (FrameDone * max_records)()
+    cnt = ctypes.c_int(0)
+    st = load().esom_server_poll(s, int(wait_all), buf, max_records, ctypes.byref(cnt))
+    return st, [buf[i] for i in range(cnt.value)]
+
+
+def esom_server_session_output(s, session: int):
+    """Returns (status, device pointer, frames completed)."""
+    p = ctypes.c_void_p()
+    f = ctypes.c_uint64(0)
+    st = load().esom_server_session_output(s, session, ctypes.byref(p), ctypes.byref(f))
+    return st, p.value, int(f.value)
+
+
+def esom_server_memory(s):
+    u, b = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    st = load().esom_server_memory(s, ctypes.byref(u), ctypes.byref(b))
+    return st, int(u.value), int(b.value)
+
+
+def esom_server_destroy(s) -> int:
+    return load().esom_server_destroy(s)
 
 
 def esom_destroy(h) -> int:

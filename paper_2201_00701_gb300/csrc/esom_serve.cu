@@ -1,0 +1,383 @@
+// SOM landmark update and the frame-serving runtime (C ABI in include/esom.h).
+//
+// The paper's interactive use (Section 3.2.2 and Section 5.1) trains the
+// high-dimensional landmarks as SOM weights while the user watches, and
+// re-projects every point each frame.  A frame here is: one SOM step on a
+// minibatch of the session's own points (best-matching landmark by the k-NN
+// kernel, neighbourhood-weighted batch update), a landmark refresh, and the
+// projection of all the session's points.
+//
+// The server keeps sessions resident on the device, admits a session only if
+// its device memory fits the budget, and runs frames with continuous
+// batching: up to `max_inflight` frames of different sessions are on the GPU
+// at once (each on its session's stream, so they overlap), frames of one
+// session run in order, and a frame starts as soon as a slot frees.  Frame
+// completion times are read from GPU events against a reference event, so
+// latency does not depend on how often the host polls.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <deque>
+#include <mutex>
+#include <vector>
+
+#include "esom.h"
+#include "esom_ctx.h"
+#include "esom_kernels.h"
+
+namespace {
+
+esom_status sfail(esom_status s, const char *msg) {
+    return static_cast<esom_status>(esom::set_error(s, msg));
+}
+
+esom_status scuda(cudaError_t e, const char *what) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    return sfail(ESOM_ECUDA, buf);
+}
+
+// One warp per landmark j: h = exp(-|l_j - l_b(x)|^2 / (2 sigma^2)) over the
+// minibatch, then L_j += alpha (sum h x / sum h - L_j).
+template <int D>
+__global__ void som_update_kernel(float *__restrict__ hi, const float2 *__restrict__ lo, int L,
+                                  const float *__restrict__ batch, const int *__restrict__ bmu,
+                                  int bmu_stride, int b, float alpha, float inv2s2) {
+    const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (j >= L) return;
+    const float2 lj = lo[j];
+    float acc[D];
+#pragma unroll
+    for (int t = 0; t < D; ++t) acc[t] = 0.f;
+    float hs = 0.f;
+    for (int x = lane; x < b; x += 32) {
+        const float2 li = lo[bmu[(size_t)x * bmu_stride]];
+        const float dx = lj.x - li.x, dy = lj.y - li.y;
+        const float h = expf(-(dx * dx + dy * dy) * inv2s2);
+        hs += h;
+        const float4 *row = reinterpret_cast<const float4 *>(batch + (size_t)x * D);
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) {
+            const float4 v = row[e];
+            acc[4 * e] = fmaf(h, v.x, acc[4 * e]);
+            acc[4 * e + 1] = fmaf(h, v.y, acc[4 * e + 1]);
+            acc[4 * e + 2] = fmaf(h, v.z, acc[4 * e + 2]);
+            acc[4 * e + 3] = fmaf(h, v.w, acc[4 * e + 3]);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        hs += __shfl_xor_sync(0xffffffffu, hs, off);
+#pragma unroll
+        for (int t = 0; t < D; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], off);
+    }
+    if (hs > 1e-30f) {
+        const float ih = 1.f / hs;
+#pragma unroll
+        for (int t = 0; t < D; ++t)
+            if ((t & 31) == lane) {
+                float *p = hi + (size_t)j * D + t;
+                *p = fmaf(alpha, fmaf(acc[t], ih, -*p), *p);
+            }
+    }
+}
+
+template <int D>
+cudaError_t launch_som(float *hi, const float *lo, int L, const float *batch, const int *bmu,
+                       int stride, int b, float alpha, float sigma, cudaStream_t st) {
+    const int threads = 256;
+    const int blocks = (int)(((size_t)L * 32 + threads - 1) / threads);
+    som_update_kernel<D><<<blocks, threads, 0, st>>>(hi, reinterpret_cast<const float2 *>(lo), L,
+                                                     batch, bmu, stride, b, alpha,
+                                                     0.5f / (sigma * sigma));
+    return cudaGetLastError();
+}
+
+cudaError_t som_dispatch(int d, float *hi, const float *lo, int L, const float *batch,
+                         const int *bmu, int stride, int b, float alpha, float sigma,
+                         cudaStream_t st) {
+    switch (d) {
+#define ESOM_SOM_CASE(DV) \
+    case DV: return launch_som<DV>(hi, lo, L, batch, bmu, stride, b, alpha, sigma, st);
+        ESOM_SOM_CASE(4) ESOM_SOM_CASE(8) ESOM_SOM_CASE(12) ESOM_SOM_CASE(16)
+        ESOM_SOM_CASE(20) ESOM_SOM_CASE(24) ESOM_SOM_CASE(28) ESOM_SOM_CASE(32)
+        ESOM_SOM_CASE(36) ESOM_SOM_CASE(40) ESOM_SOM_CASE(44) ESOM_SOM_CASE(48)
+        ESOM_SOM_CASE(52) ESOM_SOM_CASE(56) ESOM_SOM_CASE(60) ESOM_SOM_CASE(64)
+#undef ESOM_SOM_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Counter-based choice of the minibatch window of frame f (splitmix64).
+uint64_t mix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+struct Frame {
+    uint64_t id;
+    double arrival;
+};
+
+struct Session {
+    esom_session_desc desc{};
+    esom_handle h = nullptr;
+    float *points = nullptr, *out = nullptr, *hi = nullptr, *lo = nullptr;
+    int *bmu = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    size_t bytes = 0;
+    std::deque<Frame> queue;
+    bool inflight = false;
+    Frame current{};
+    uint64_t submitted = 0, completed = 0;
+};
+
+}  // namespace
+
+struct esom_server_ctx {
+    uint64_t budget = 0, used = 0;
+    int max_inflight = 1, inflight = 0, dev = 0;
+    std::vector<Session *> sessions;
+    cudaEvent_t ref = nullptr;
+    std::chrono::steady_clock::time_point t0;
+    double ref_host = 0.0;
+    std::mutex mu;
+};
+
+namespace {
+
+double host_now(const esom_server_ctx *s) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
+}
+
+// Enqueues one frame of session ss on its stream.
+esom_status launch_frame(esom_server_ctx *s, Session &ss, const Frame &f) {
+    const esom_session_desc &d = ss.desc;
+    cudaStream_t st = ss.stream;
+    const esom_stream_t est = reinterpret_cast<esom_stream_t>(st);
+    esom_status r = ESOM_OK;
+    if (d.minibatch > 0 && d.alpha > 0.f) {
+        const int64_t b = d.minibatch < d.n ? d.minibatch : d.n;
+        const uint64_t span = (uint64_t)(d.n - b) + 1;
+        const int64_t off = (int64_t)(mix64(d.seed ^ (f.id * 0x100000001b3ull)) % span);
+        r = esom_knn(ss.h, ss.points + off * d.d, b, ss.bmu, nullptr, est);
+        if (r != ESOM_OK) return r;
+        cudaError_t e = som_dispatch(d.d, ss.hi, ss.lo, d.L, ss.points + off * d.d, ss.bmu, d.k,
+                                     (int)b, d.alpha, d.sigma, st);
+        if (e != cudaSuccess) return scuda(e, "SOM update");
+        r = esom_set_landmarks(ss.h, ss.hi, ss.lo, est);
+        if (r != ESOM_OK) return r;
+    }
+    r = esom_project(ss.h, ss.points, d.n, ss.out, d.boost, d.adjust, est);
+    if (r != ESOM_OK) return r;
+    const cudaError_t e = cudaEventRecord(ss.done, st);
+    if (e != cudaSuccess) return scuda(e, "frame event");
+    ss.inflight = true;
+    ss.current = f;
+    ++s->inflight;
+    return ESOM_OK;
+}
+
+// Starts queued frames while slots are free, oldest arrival first.
+esom_status fill_slots(esom_server_ctx *s) {
+    while (s->inflight < s->max_inflight) {
+        Session *best = nullptr;
+        for (Session *ss : s->sessions)
+            if (!ss->inflight && !ss->queue.empty() &&
+                (!best || ss->queue.front().arrival < best->queue.front().arrival))
+                best = ss;
+        if (!best) break;
+        const Frame f = best->queue.front();
+        best->queue.pop_front();
+        esom_status r = launch_frame(s, *best, f);
+        if (r != ESOM_OK) return r;
+    }
+    return ESOM_OK;
+}
+
+void free_session(Session *ss) {
+    if (!ss) return;
+    if (ss->stream) cudaStreamSynchronize(ss->stream);
+    esom_destroy(ss->h);
+    cudaFree(ss->points);
+    cudaFree(ss->out);
+    cudaFree(ss->hi);
+    cudaFree(ss->lo);
+    cudaFree(ss->bmu);
+    if (ss->done) cudaEventDestroy(ss->done);
+    if (ss->stream) cudaStreamDestroy(ss->stream);
+    delete ss;
+}
+
+}  // namespace
+
+extern "C" {
+
+esom_status esom_som_update(float *hi, const float *lo, int d, int L, const float *batch,
+                            const int32_t *bmu, int bmu_stride, int64_t b, float alpha,
+                            float sigma, esom_stream_t stream) {
+    if (!hi || !lo || (b > 0 && (!batch || !bmu))) return sfail(ESOM_EINVAL, "null pointer");
+    if (d < 4 || d > ESOM_MAX_D || d % 4) return sfail(ESOM_EINVAL, "d must be a multiple of 4 in [4, 64]");
+    if (L < 1 || b < 0 || b > (1 << 30) || bmu_stride < 1) return sfail(ESOM_EINVAL, "sizes");
+    if (!(sigma > 0.f) || !(alpha >= 0.f)) return sfail(ESOM_EINVAL, "sigma > 0, alpha >= 0");
+    if (((uintptr_t)batch & 15u) || ((uintptr_t)lo & 7u))
+        return sfail(ESOM_EALIGN, "batch 16-byte and lo 8-byte aligned");
+    if (b == 0 || alpha == 0.f) return ESOM_OK;
+    const cudaError_t e = som_dispatch(d, hi, lo, L, batch, bmu, bmu_stride, (int)b, alpha, sigma,
+                                       reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ESOM_OK : scuda(e, "SOM update");
+}
+
+esom_status esom_server_create(uint64_t budget_bytes, int max_inflight, esom_server *out) {
+    if (!out) return sfail(ESOM_EINVAL, "null output");
+    *out = nullptr;
+    if (max_inflight < 1) return sfail(ESOM_EINVAL, "max_inflight < 1");
+    esom_server_ctx *s = new (std::nothrow) esom_server_ctx;
+    if (!s) return sfail(ESOM_ENOMEM, "host allocation");
+    s->budget = budget_bytes;
+    s->max_inflight = max_inflight;
+    cudaError_t e = cudaGetDevice(&s->dev);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->ref);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ref, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(s->ref);
+    if (e != cudaSuccess) {
+        delete s;
+        return scuda(e, "server set-up");
+    }
+    s->t0 = std::chrono::steady_clock::now();
+    s->ref_host = 0.0;
+    *out = s;
+    return ESOM_OK;
+}
+
+double esom_server_now(esom_server s) { return s ? host_now(s) : 0.0; }
+
+esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc,
+                                    const float *points, const float *hi, const float *lo,
+                                    int *session) {
+    if (!s || !desc || !session || !points || !hi || !lo) return sfail(ESOM_EINVAL, "null argument");
+    const esom_session_desc &d = *desc;
+    if (d.n < 1 || d.minibatch < 0 || !(d.boost > 0.f) || !(d.adjust >= 0.f) ||
+        (d.minibatch > 0 && d.alpha > 0.f && !(d.sigma > 0.f)))
+        return sfail(ESOM_EINVAL, "session description");
+    std::lock_guard<std::mutex> lock(s->mu);
+    // resident points and output, the session's landmark copy and the
+    // handle's (rows, 2-D positions, norms), the minibatch k-NN indices
+    const size_t bytes = (size_t)d.n * d.d * 4 + (size_t)d.n * 8 + (size_t)d.L * (d.d + 2) * 4 * 2 +
+                         (size_t)((d.L + 3) & ~3) * 4 + (size_t)d.minibatch * d.k * 4 + 4096;
+    if (s->used + bytes > s->budget)
+        return sfail(ESOM_ENOMEM, "session refused: device memory budget exceeded");
+    Session *ss = new (std::nothrow) Session;
+    if (!ss) return sfail(ESOM_ENOMEM, "host allocation");
+    ss->desc = d;
+    ss->bytes = bytes;
+    esom_status r = esom_create(d.d, d.L, d.k, &ss->h);
+    cudaError_t e = cudaSuccess;
+    if (r == ESOM_OK) {
+        e = cudaMalloc(&ss->points, (size_t)d.n * d.d * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&ss->out, (size_t)d.n * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&ss->hi, (size_t)d.L * d.d * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&ss->lo, (size_t)d.L * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&ss->bmu, (size_t)(d.minibatch > 0 ? d.minibatch : 1) * d.k * 4);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ss->stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreate(&ss->done);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ss->points, points, (size_t)d.n * d.d * 4, cudaMemcpyDefault, ss->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ss->hi, hi, (size_t)d.L * d.d * 4, cudaMemcpyDefault, ss->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ss->lo, lo, (size_t)d.L * 8, cudaMemcpyDefault, ss->stream);
+        if (e == cudaSuccess) {
+            r = esom_set_landmarks(ss->h, ss->hi, ss->lo, reinterpret_cast<esom_stream_t>(ss->stream));
+        }
+        if (e == cudaSuccess && r == ESOM_OK) e = cudaStreamSynchronize(ss->stream);
+    }
+    if (r != ESOM_OK || e != cudaSuccess) {
+        free_session(ss);
+        return r != ESOM_OK ? r : sfail(ESOM_ENOMEM, "session allocation");
+    }
+    s->used += bytes;
+    *session = (int)s->sessions.size();
+    s->sessions.push_back(ss);
+    return ESOM_OK;
+}
+
+esom_status esom_server_submit(esom_server s, int session, double arrival) {
+    if (!s || session < 0 || session >= (int)s->sessions.size() || !s->sessions[(size_t)session])
+        return sfail(ESOM_EINVAL, "no such session");
+    std::lock_guard<std::mutex> lock(s->mu);
+    Session &ss = *s->sessions[(size_t)session];
+    ss.queue.push_back(Frame{ss.submitted++, arrival});
+    return fill_slots(s);
+}
+
+esom_status esom_server_poll(esom_server s, int wait_all, esom_frame_done *done, int max,
+                             int *count) {
+    if (!s || !count || (max > 0 && !done)) return sfail(ESOM_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lock(s->mu);
+    *count = 0;
+    for (;;) {
+        for (size_t i = 0; i < s->sessions.size(); ++i) {
+            Session *ss = s->sessions[i];
+            if (!ss || !ss->inflight) continue;
+            cudaError_t q = wait_all ? cudaEventSynchronize(ss->done) : cudaEventQuery(ss->done);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) return scuda(q, "frame completion");
+            float ms = 0.f;
+            cudaError_t e = cudaEventElapsedTime(&ms, s->ref, ss->done);
+            if (e != cudaSuccess) return scuda(e, "frame timing");
+            if (*count < max) {
+                esom_frame_done &o = done[(*count)++];
+                o.session = (int)i;
+                o.frame = ss->current.id;
+                o.arrival = ss->current.arrival;
+                o.completion = s->ref_host + ms / 1e3;
+            }
+            ss->inflight = false;
+            ++ss->completed;
+            --s->inflight;
+        }
+        esom_status r = fill_slots(s);
+        if (r != ESOM_OK) return r;
+        bool pending = s->inflight > 0;
+        for (Session *ss : s->sessions)
+            if (ss && !ss->queue.empty()) pending = true;
+        if (!wait_all || !pending || *count >= max) break;
+    }
+    return ESOM_OK;
+}
+
+esom_status esom_server_session_output(esom_server s, int session, const float **out,
+                                       uint64_t *frames) {
+    if (!s || session < 0 || session >= (int)s->sessions.size() || !s->sessions[(size_t)session])
+        return sfail(ESOM_EINVAL, "no such session");
+    std::lock_guard<std::mutex> lock(s->mu);
+    const Session &ss = *s->sessions[(size_t)session];
+    if (out) *out = ss.out;
+    if (frames) *frames = ss.completed;
+    return ESOM_OK;
+}
+
+esom_status esom_server_memory(esom_server s, uint64_t *used, uint64_t *budget) {
+    if (!s) return sfail(ESOM_EINVAL, "null server");
+    if (used) *used = s->used;
+    if (budget) *budget = s->budget;
+    return ESOM_OK;
+}
+
+esom_status esom_server_destroy(esom_server s) {
+    if (!s) return ESOM_OK;
+    for (Session *ss : s->sessions) free_session(ss);
+    if (s->ref) cudaEventDestroy(s->ref);
+    delete s;
+    return ESOM_OK;
+}
+
+}  // extern "C"

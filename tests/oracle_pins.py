@@ -362,8 +362,39 @@ def pin_continuity_at_cutoff(O):
     assert checked >= 15, checked
 
 
+# --------------------------------------------------------------------------
+# SOM step (reading R6 of the oracle header; used by the frame server).
+
+def pin_som_step_limits(O):
+    """sigma -> 0: each landmark moves towards the mean of the minibatch
+    points whose best-matching landmarks are the nearest assigned ones to it
+    on the grid (itself, if any point picked it: a k-means step with rate
+    alpha); sigma -> infinity: every landmark moves towards the mean of the
+    whole minibatch; alpha = 0 changes nothing."""
+    r = _rng(13)
+    L, d, b = 16, 5, 200
+    hi = r.standard_normal((L, d)).astype(np.float32)
+    lo = np.stack([np.arange(L) % 4, np.arange(L) // 4], 1).astype(np.float32)
+    batch = r.standard_normal((b, d)).astype(np.float32)
+    bmu = r.integers(0, L - 3, b).astype(np.int32)       # the last landmarks unassigned
+    hi64, batch64 = hi.astype(np.float64), batch.astype(np.float64)
+    for alpha in (0.05, 0.5, 1.0):
+        out = O.som_step(hi, lo, batch, bmu, alpha, 0.05)
+        assigned = np.unique(bmu)
+        for j in range(L):
+            g2 = ((lo[assigned] - lo[j]) ** 2).sum(1)
+            near = assigned[g2 == g2.min()]
+            sel = np.isin(bmu, near)
+            want = hi64[j] + alpha * (batch64[sel].mean(0) - hi64[j])
+            _close(out[j], want, 1e-12, f"som sigma->0 landmark {j}")
+        out = O.som_step(hi, lo, batch, bmu, alpha, 1e6)
+        want = hi64 + alpha * (batch64.mean(0)[None] - hi64)
+        _close(out, want, 1e-9, "som sigma->inf")
+    _close(O.som_step(hi, lo, batch, bmu, 0.0, 1.5), hi64, 0.0, "som alpha=0")
+
+
 ALL_PINS = [pin_knn_bruteforce, pin_k2_nearest_layout_point, pin_k3_closed_form,
             pin_golden_fixtures, pin_plane_recovery, pin_weighted_least_squares,
             pin_collinear_layout, pin_layout_similarity, pin_space_similarity,
             pin_relabelling, pin_score_homogeneity, pin_score_shape,
-            pin_continuity_at_cutoff]
+            pin_continuity_at_cutoff, pin_som_step_limits]

@@ -38,6 +38,10 @@ MUTANTS = [
     ("pairs_skip_last_scored", "for (int v = u + 1; v < m; ++v) {",
      "for (int v = u + 1; v < m - 1; ++v) {"),
     ("knn_drops_nearest", "idx[i] = work[i].j;", "idx[i] = work[i + (i == 0 && k < g)].j;"),
+    ("som_sigma_not_squared", "double h = exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma));",
+     "double h = exp(-(dx * dx + dy * dy) / (2.0 * sigma));"),
+    ("som_step_sign", "l + alpha * (hi_out[(int64_t)j * d + t] / hs - l) : l;",
+     "l - alpha * (hi_out[(int64_t)j * d + t] / hs - l) : l;"),
 ]
 
 
