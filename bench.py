@@ -412,6 +412,95 @@ def run_batch64(args):
         P.close()
 
 
+def run_serve(args):
+    """--workload serve8: the frame server with 8 resident sessions (d=24,
+    k=20, n in {2e5, 1e6, 5e6}, L in {256, 1024}); each frame is one SOM step
+    on a 4096-point minibatch plus a reprojection of the session's points.
+    Frames arrive as Poisson processes (60 frames/s per session) for a fixed
+    time; latency = GPU completion time - arrival time on the server's clock."""
+    import torch
+
+    from paper_2201_00701_gb300 import binding, workloads
+
+    torch.cuda.set_device(0)
+    binding.load()
+    params = workloads.serve8(n_scale=args.serve_scale)
+    srv = binding.Server(int(args.serve_budget_gb * (1 << 30)), args.serve_inflight)
+    sids, sizes = [], {}
+    for p in params:
+        w = workloads.serve_member(p)
+        X = torch.from_numpy(w.X).pin_memory()
+        sid = srv.add_session(X, torch.from_numpy(w.hi), torch.from_numpy(w.lo), w.k, w.boost,
+                              w.adjust, p["alpha"], p["sigma"], p["minibatch"], p["seed"])
+        sids.append(sid)
+        sizes[sid] = (w.n, w.d, w.L, w.k)
+        del X, w
+    used, budget = srv.memory()
+    for _ in range(args.warmup):
+        for sid in sids:
+            srv.submit(sid)
+        srv.poll(wait_all=True)
+    # open-loop Poisson arrivals, seeded, for serve_seconds
+    rng = np.random.default_rng(7)
+    arrivals = []
+    for sid, p in zip(sids, params):
+        t = rng.exponential(1.0 / p["rate"])
+        while t < args.serve_seconds:
+            arrivals.append((t, sid))
+            t += rng.exponential(1.0 / p["rate"])
+    arrivals.sort()
+    props = torch.cuda.get_device_properties(0)
+    uuid = getattr(props, "uuid", None)
+    uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+    sampler = ClockSampler(uuid, 0)
+    recs = []
+    torch.cuda.synchronize()
+    with sampler:
+        t0 = srv.now() + 0.01
+        i = 0
+        while i < len(arrivals):
+            now = srv.now()
+            while i < len(arrivals) and t0 + arrivals[i][0] <= now:
+                srv.submit(arrivals[i][1], t0 + arrivals[i][0])
+                i += 1
+            recs += srv.poll()
+            time.sleep(0.0002)
+        recs += srv.poll(wait_all=True)
+    lat = np.array([1e3 * (c - a) for _, _, a, c in recs])
+    pts = sum(sizes[s][0] for s, _, _, _ in recs)
+    span = max(c for _, _, _, c in recs) - (t0 + arrivals[0][0])
+    offered = sum(p["rate"] * sizes[s][0] for s, p in zip(sids, params))
+    per_session = {}
+    for sid in sids:
+        ls = lat[[j for j, r in enumerate(recs) if r[0] == sid]]
+        n, d, L, k = sizes[sid]
+        per_session[str(sid)] = {"n": n, "L": L, "frames": int(ls.size),
+                                 "p50_ms": float(np.percentile(ls, 50)),
+                                 "p99_ms": float(np.percentile(ls, 99))}
+    line = {
+        "metric": baseline_metric(), "value": pts / span, "unit": "points/s",
+        "n_gpus": 1, "steps": len(recs), "warmup": args.warmup,
+        "ms_per_step": float(np.mean(lat)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve8", "sessions": len(sids), "d": 24, "k": 20,
+                   "points_resident": int(sum(v[0] for v in sizes.values())),
+                   "arrivals": "Poisson, 60 frames/s per session",
+                   "frame": "SOM step (4096-point minibatch, alpha 0.05, sigma 1.5 cells) "
+                            "+ full reprojection",
+                   "seconds": args.serve_seconds, "max_inflight": args.serve_inflight,
+                   "budget_bytes": budget, "admitted_bytes": used,
+                   "l2": "not flushed: inputs (>=19 MB per session, 1.3 GB in all) exceed L2"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "offered_points_per_s": offered,
+        "sessions": per_session,
+        "clocks": sampler.summary(),
+        "gpu_launches": 4 * len(recs),
+    }
+    print(json.dumps(line), flush=True)
+    srv.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -422,14 +511,21 @@ def main():
     ap.add_argument("--ref-points", type=int, default=4000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64", "serve8"])
     ap.add_argument("--batch-n-max", type=float, default=2e6)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-scale", type=float, default=1.0)
+    ap.add_argument("--serve-inflight", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_setup()
     if args.workload == "batch64":
         run_batch64(args)
+        return
+    if args.workload == "serve8":
+        run_serve(args)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

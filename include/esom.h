@@ -191,9 +191,16 @@ esom_status esom_batch_destroy(esom_batch b);
  *   h(j, i) = exp(-|l_j - l_i|^2 / (2 sigma^2)),
  * over the minibatch points x with best-matching landmarks b(x) =
  * bmu[x * bmu_stride] (for example column 0 of esom_knn's idx, stride k);
- * landmarks whose neighbourhood weight sums to ~0 are left unchanged.
- * hi: L x d device (updated in place); lo: L x 2 device, 8-byte aligned;
- * batch: b x d device, 16-byte aligned.  The paper gives no formula for the
+ * entries outside [0, L) skip their point; landmarks whose neighbourhood
+ * weight sums to below 1e-30 (FP32) are left unchanged.
+ * hi: L x d device, row-major, updated in place (the caller owns it; pass it
+ * to esom_set_landmarks afterwards to project with the new rows);
+ * lo: L x 2 device, 8-byte aligned; batch: b x d device, 16-byte aligned;
+ * all three and bmu stay owned by the caller.  Asynchronous on `stream`.
+ * Errors: ESOM_EINVAL for null pointers, d not a multiple of 4 in [4, 64],
+ * L < 1, b < 0 or > 2^30, bmu_stride < 1, sigma <= 0 or alpha < 0;
+ * ESOM_EALIGN for misaligned batch or lo; ESOM_ECUDA for a launch error.
+ * b = 0 or alpha = 0 changes nothing.  The paper gives no formula for the
  * step; this batch form is this library's reading. */
 esom_status esom_som_update(float *hi, const float *lo, int d, int L, const float *batch,
                             const int32_t *bmu, int bmu_stride, int64_t b, float alpha,
@@ -228,8 +235,21 @@ typedef struct {
     double arrival, completion;
 } esom_frame_done;
 
+/* A server on the current device.  budget_bytes: the device memory that
+ * admitted sessions may hold together; max_inflight >= 1: frames on the GPU
+ * at once.  ESOM_EINVAL for max_inflight < 1, ESOM_ECUDA if the device
+ * cannot be set up.  The server is not thread-safe across create/destroy;
+ * submit/poll/session_output may be called from several host threads. */
 esom_status esom_server_create(uint64_t budget_bytes, int max_inflight, esom_server *out);
-/* points (n x d), hi (L x d), lo (L x 2): host or device; copied. */
+/* Admits one session.  points (n x d), hi (L x d), lo (L x 2), float32
+ * row-major, host or device: copied into device memory the server owns
+ * before the call returns (the caller may free them).  ESOM_ENOMEM when the
+ * session's device footprint (points, output, two landmark copies, norms,
+ * minibatch indices) would take the server past its budget (nothing is
+ * allocated then) or an allocation fails; ESOM_EINVAL for a bad
+ * description (n < 1, minibatch < 0, boost <= 0, adjust < 0, sigma <= 0
+ * with a SOM step, or d, L, k that esom_create rejects).  *session gets a
+ * small integer id, 0, 1, ... in admission order. */
 esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc,
                                     const float *points, const float *hi, const float *lo,
                                     int *session);
@@ -241,8 +261,10 @@ esom_status esom_server_submit(esom_server s, int session, double arrival);
  * max records were filled). */
 esom_status esom_server_poll(esom_server s, int wait_all, esom_frame_done *done, int max,
                              int *count);
-/* Device pointer to the session's latest coordinates (n x 2) and the
- * number of frames it has completed. */
+/* Device pointer to the session's latest coordinates (n x 2 float32, owned
+ * by the server, valid until esom_server_destroy; read it only when no
+ * frame of the session is in flight) and the number of frames it has
+ * completed. */
 esom_status esom_server_session_output(esom_server s, int session, const float **out,
                                        uint64_t *frames);
 esom_status esom_server_memory(esom_server s, uint64_t *used, uint64_t *budget);

@@ -380,3 +380,72 @@ class Projector:
         st, cfg = esom_get_config(self.h)
         check(st)
         return cfg
+
+
+def device_view(ptr: int, shape, typestr: str = "<f4"):
+    """A torch tensor viewing device memory the library owns (no copy)."""
+    import torch
+
+    class _View:
+        pass
+
+    v = _View()
+    v.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                  "data": (int(ptr), True), "version": 2, "strides": None}
+    return torch.as_tensor(v, device="cuda")
+
+
+class Server:
+    """The frame server (esom_server_*) on the current CUDA device."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int):
+        st, s = esom_server_create(budget_bytes, max_inflight)
+        check(st)
+        self.s = s
+        self.n = {}
+
+    def close(self):
+        if self.s:
+            esom_server_destroy(self.s)
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_session(self, X, hi, lo, k: int, boost: float = 1.0, adjust: float = 1.0,
+                    alpha: float = 0.0, sigma: float = 1.0, minibatch: int = 0,
+                    seed: int = 0) -> int:
+        """X, hi, lo: contiguous float32 tensors (host or device); copied.
+        Raises EsomError (status ESOM_ENOMEM when the budget refuses it)."""
+        n, d = X.shape
+        desc = SessionDesc(d, hi.shape[0], k, n, boost, adjust, alpha, sigma, minibatch, seed)
+        st, sid = esom_server_add_session(self.s, desc, X.data_ptr(), hi.data_ptr(),
+                                          lo.data_ptr())
+        check(st)
+        self.n[sid] = n
+        return sid
+
+    def now(self) -> float:
+        return esom_server_now(self.s)
+
+    def submit(self, session: int, arrival: float | None = None):
+        check(esom_server_submit(self.s, session, self.now() if arrival is None else arrival))
+
+    def poll(self, wait_all: bool = False, max_records: int = 4096):
+        st, recs = esom_server_poll(self.s, wait_all, max_records)
+        check(st)
+        return [(r.session, int(r.frame), r.arrival, r.completion) for r in recs]
+
+    def output(self, session: int):
+        """(copy of the session's latest n x 2 coordinates, frames completed)."""
+        st, ptr, frames = esom_server_session_output(self.s, session)
+        check(st)
+        return device_view(ptr, (self.n[session], 2)).clone(), frames
+
+    def memory(self):
+        st, used, budget = esom_server_memory(self.s)
+        check(st)
+        return used, budget

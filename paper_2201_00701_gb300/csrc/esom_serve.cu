@@ -55,7 +55,9 @@ __global__ void som_update_kernel(float *__restrict__ hi, const float2 *__restri
     for (int t = 0; t < D; ++t) acc[t] = 0.f;
     float hs = 0.f;
     for (int x = lane; x < b; x += 32) {
-        const float2 li = lo[bmu[(size_t)x * bmu_stride]];
+        const int bi = bmu[(size_t)x * bmu_stride];
+        if ((unsigned)bi >= (unsigned)L) continue;  // not a landmark: the point is skipped
+        const float2 li = lo[bi];
         const float dx = lj.x - li.x, dy = lj.y - li.y;
         const float h = expf(-(dx * dx + dy * dy) * inv2s2);
         hs += h;

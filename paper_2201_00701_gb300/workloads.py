@@ -23,6 +23,8 @@ one is drawn with numpy's PCG64 from an explicit seed, in float32, row-major:
 * ``uniform_d16`` / ``uniform_d32``  the paper's own shape (Section 4.1 and
   the real-time figure of Section 5.1): n=2^20, every coordinate U[0,1],
   L=256 landmarks drawn the same way on a 16x16 grid, k=16.
+* ``serve8``            8 resident sessions for the frame server, d=24,
+  k=20, n in {2e5, 1e6, 5e6}, L in {256, 1024}, SOM step per frame.
 * ``batch64``           64 independent datasets with n log-uniform in
   [1e3, 2e6], d in {8,16,32,48}, L in {100,400,1024,2500}, k in {10,20,30},
   each a 10-40 component Gaussian mixture.
@@ -188,6 +190,33 @@ def batch_member(p: dict, n: int | None = None) -> Workload:
     lo = grid_layout(p["L"], s[1])
     return Workload(f"batch64[{p['index']}]", X, hi, lo, k=p["k"],
                     boost=1.0, adjust=1.0)
+
+
+def serve8(seed: int = 0, sessions: int = 8, n_scale: float = 1.0):
+    """Parameters of the resident sessions of the serving workload: d=24,
+    k=20, n from {2e5, 1e6, 5e6} (each size on every third session, in a
+    seeded order), L from {256, 1024} alternating, a 10-40 component
+    mixture each.  Frames: one SOM step (rate 0.05, neighbourhood sigma 1.5
+    grid cells, 4096-point minibatch) and a full reprojection, arriving as a
+    Poisson process of 60 frames/s per session.  `n_scale` shrinks n for
+    tests."""
+    s = _streams(seed, sessions + 1)
+    sizes = [200_000, 1_000_000, 5_000_000]
+    order = s[0].permutation(sessions)
+    out = []
+    for i in range(sessions):
+        g = s[i + 1]
+        n = max(1, int(round(sizes[int(order[i]) % 3] * n_scale)))
+        out.append(dict(index=i, n=n, d=24, L=[256, 1024][i % 2], k=20,
+                        comps=int(g.integers(10, 41)), seed=seed * 100_000 + 50_000 + i,
+                        alpha=0.05, sigma=1.5, minibatch=4096, rate=60.0))
+    return out
+
+
+def serve_member(p: dict) -> Workload:
+    w = batch_member(p)
+    w.name = f"serve8[{p['index']}]"
+    return w
 
 
 NAMED = {
