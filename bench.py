@@ -137,6 +137,15 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 
+def tensor_peak_tflops() -> float:
+    """Measured sustained dense BF16 tensor rate of this GPU model."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"])
+    except Exception:
+        return 1700.0  # fallback: an earlier sustained measurement on a GB300
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -210,10 +219,15 @@ def run_esom(args, world, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     binding.load()
 
-    w = workloads.mixture30_d16(n=args.n, shard=rank)
+    if args.workload == "student50_d32":
+        w = workloads.student50_d32(n=args.n if args.n else 10_000_000)
+    else:
+        w = workloads.mixture30_d16(n=args.n if args.n else 1_000_000, shard=rank)
     n, d, L, k = w.n, w.d, w.L, w.k
     P = binding.Projector(d, L, k)
     P.set_landmarks(torch.from_numpy(w.hi).to(dev), torch.from_numpy(w.lo).to(dev))
+    modes = {"fp32": binding.ESOM_SCREEN_FP32, "tf32": binding.ESOM_SCREEN_TF32}
+    P.set_screening(modes[args.screen])
     X = torch.from_numpy(w.X).to(dev)
     out = torch.empty((n, 2), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -252,6 +266,23 @@ def run_esom(args, world, rank, local):
     total_s = float(step_ms.sum()) / 1e3
     if P.device_status() != 0:
         raise RuntimeError("device status flag raised in the timed region")
+    main_stats = P.stats(reset=True)
+
+    # the other screening mode on the same buffers (same results, bit for bit)
+    other = "fp32" if args.screen == "tf32" else "tf32"
+    P.set_screening(modes[other])
+    other_ms = []
+    for i in range(args.warmup + min(args.steps, 20)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.project(X, w.boost, w.adjust, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            other_ms.append(e0.elapsed_time(e1))
+    other_stats = P.stats(reset=True)
+    P.set_screening(modes[args.screen])
 
     # the k-NN step alone (same kernel, no projection phase): splits the step
     # time into k-NN and scores + pair sums + solve
@@ -295,15 +326,30 @@ def run_esom(args, world, rank, local):
         achieved = 2.0 * fmas / t_launch / 1e12     # TFLOP/s (FMA = 2 flops)
         clocks = sampler.summary()
         max_mhz = clocks.get("sm_max_mhz") or 2070
-        peak = 2.0 * 128 * props.multi_processor_count * max_mhz * 1e6 / 1e12
-        traffic = profile_traffic()
+        alu_peak = 2.0 * 128 * props.multi_processor_count * max_mhz * 1e6 / 1e12
+        peak = alu_peak
+        roof_note = f"128 FP32 lanes x {props.multi_processor_count} SMs x {max_mhz} MHz x 2"
+        if args.screen == "tf32":
+            # L*d on the tensor pipe (TF32 = half the measured sustained BF16
+            # rate), k^2*d on the FP32 lanes: the effective peak of the mix
+            tf32_peak = tensor_peak_tflops() / 2.0
+            t_roof = 2.0 * n * L * d / (tf32_peak * 1e12) + 2.0 * n * k * k * d / (alu_peak * 1e12)
+            peak = 2.0 * fmas / t_roof / 1e12
+            roof_note = (f"n*L*d on TF32 tensor cores at {tf32_peak:.0f} TFLOP/s (half the "
+                         f"measured sustained BF16 rate) + n*k^2*d on the FP32 lanes at "
+                         f"{alu_peak:.1f} TFLOP/s")
+        traffic = profile_traffic() if args.workload == WORKLOAD else None
         line = {
             "metric": baseline_metric(), "value": value, "unit": "points/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "d": d, "L": L, "k": k,
-                       "boost": w.boost, "adjust": w.adjust, "path": "plain FP32 fused kernel",
+            "config": {"workload": args.workload, "n": n, "d": d, "L": L, "k": k,
+                       "boost": w.boost, "adjust": w.adjust,
+                       "path": ("tensor-core (TF32) screened k-NN + exact FP32 re-rank, fused "
+                                "projection" if args.screen == "tf32" else
+                                "FP32 screened k-NN + exact re-rank, fused projection"),
+                       "screening": args.screen,
                        "parallelism": f"dp{world} (points sharded, no collective)",
                        "l2": "flushed between steps by an untimed 256 MiB write",
                        "launch": {key: cfg[key] for key in ("threads_per_block",
@@ -317,11 +363,14 @@ def run_esom(args, world, rank, local):
                           "projection_share": 1.0 - float(np.median(knn_ms))
                           / float(np.median(step_ms))},
             "gpu_launches": args.steps,
+            "screening_paths_ms": {args.screen: float(np.median(step_ms)),
+                                   other: float(np.median(other_ms))},
+            "rescan_fraction": {args.screen: main_stats["rescans"] / max(main_stats["points"], 1),
+                                other: other_stats["rescans"] / max(other_stats["points"], 1)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "algorithmic": "2 * n * (L*d + k^2*d) FP32 FMA-flops per launch",
-                         "peak_from": f"128 FP32 lanes x {props.multi_processor_count} SMs x "
-                                      f"{max_mhz} MHz x 2",
+                         "algorithmic": "2 * n * (L*d + k^2*d) flops per launch",
+                         "peak_from": roof_note,
                          "frac_at_sampled_clock": (achieved / peak * max_mhz / clocks["sm_mhz"])
                          if clocks.get("sm_mhz") else None},
             "clocks": clocks,
@@ -507,11 +556,13 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="esom", choices=["esom", "reference"])
-    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--n", type=int, default=0, help="points (default: the workload's n)")
+    ap.add_argument("--screen", default="tf32", choices=["fp32", "tf32"])
     ap.add_argument("--ref-points", type=int, default=4000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64", "serve8"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "student50_d32", "batch64", "serve8"])
     ap.add_argument("--batch-n-max", type=float, default=2e6)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-scale", type=float, default=1.0)

@@ -141,9 +141,34 @@ typedef struct {
     int landmark_chunk;         /* landmarks per shared-memory chunk */
     int landmark_chunks;        /* 1: all landmarks resident in shared memory */
     int shared_bytes;           /* dynamic shared memory per block */
+    int screening;              /* ESOM_SCREEN_* in effect (the other fields then
+                                   describe the tensor-core launch: 160 threads,
+                                   128 points a tile, 64-landmark chunks) */
 } esom_config;
 
 esom_status esom_get_config(esom_handle h, esom_config *cfg);
+
+/* ---------------------------------------------------------------------------
+ * Screening precision of the k-NN distance block (Section 4.2's fused
+ * distance + selection; the block is the g x d term of the cost).
+ *   ESOM_SCREEN_FP32  the default: FP32 CUDA-core scan.
+ *   ESOM_SCREEN_TF32  the distance block X . L^T runs on the tensor cores
+ *                     (tcgen05, TF32 operands, FP32 accumulation in tensor
+ *                     memory), 128 points by 64 landmarks an MMA tile.
+ * Either way the listed candidates are re-ranked with exact FP32 distances
+ * and a bound on the screening error certifies that no other landmark can be
+ * among the k nearest (a point that fails is rescanned exactly; see
+ * esom_get_stats), so both modes return the same neighbours, distances and
+ * coordinates, bit for bit; the mode only changes speed.
+ * Switching to TF32 allocates the landmark images (ceil(L/64) * 64 * 128 *
+ * ceil(d/32) bytes, kept until esom_destroy) and, if landmarks are set,
+ * builds them on `stream`; later esom_set_landmarks calls rebuild them.
+ * Errors: ESOM_EINVAL (unknown mode), ESOM_EUNSUPPORTED (device is not
+ * sm_103, or no kernel for this d and k), ESOM_ENOMEM, ESOM_ECUDA.
+ * esom_batch_* and esom_project_noalloc always screen in FP32. */
+#define ESOM_SCREEN_FP32 0
+#define ESOM_SCREEN_TF32 1
+esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Batched projection: many datasets of uneven n, d and L through one plan.

@@ -24,6 +24,8 @@ ESOM_ENOLANDMARKS = -4
 ESOM_ECUDA = -5
 ESOM_EUNSUPPORTED = -6
 ESOM_EDEVICE = -7
+ESOM_SCREEN_FP32 = 0
+ESOM_SCREEN_TF32 = 1
 
 HEADER = os.path.join(_build.INCLUDE, "esom.h")
 
@@ -59,7 +61,7 @@ class FrameDone(ctypes.Structure):
 class _Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("d", "L", "k", "kc", "threads_per_block", "blocks_per_sm", "num_sms",
-                 "landmark_chunk", "landmark_chunks", "shared_bytes")]
+                 "landmark_chunk", "landmark_chunks", "shared_bytes", "screening")]
 
 
 _lib = None
@@ -94,6 +96,7 @@ def load(build_if_missing: bool = False):
         "esom_get_config": ([P, ctypes.POINTER(_Config)], I),
         "esom_project_noalloc": ([P, I64, P, P, I, I, I, P, F, F, P], I),
         "esom_get_stats": ([P, P, ctypes.POINTER(_Stats), I], I),
+        "esom_set_screening": ([P, I, P], I),
         "esom_batch_create": ([ctypes.POINTER(BatchItem), I, I, ctypes.POINTER(P)], I),
         "esom_batch_run": ([P, P], I),
         "esom_batch_run_graph": ([P, P], I),
@@ -181,6 +184,11 @@ def esom_get_stats(h, stream: int = 0, reset: bool = False):
     st_ = _Stats()
     st = load().esom_get_stats(h, stream, ctypes.byref(st_), int(reset))
     return st, {"points": int(st_.points), "rescans": int(st_.rescans)}
+
+
+def esom_set_screening(h, mode: int, stream: int = 0) -> int:
+    """ESOM_SCREEN_FP32 (0) or ESOM_SCREEN_TF32 (1, tensor cores)."""
+    return load().esom_set_screening(h, mode, stream)
 
 
 def esom_project_noalloc(points_ptr: int, n: int, hi_ptr: int, lo_ptr: int, d: int, L: int,
@@ -372,6 +380,10 @@ class Projector:
         st, out = esom_get_stats(self.h, self._stream(), reset)
         check(st)
         return out
+
+    def set_screening(self, mode: int):
+        """ESOM_SCREEN_FP32 or ESOM_SCREEN_TF32; same results, different speed."""
+        check(esom_set_screening(self.h, mode, self._stream()))
 
     def set_landmark_chunk(self, chunk: int):
         check(esom_set_landmark_chunk(self.h, chunk))

@@ -56,6 +56,8 @@ void fill_args(const esom_ctx *h, const float *points, long long n, float *out, 
     a->nchunks = h->nchunks;
     a->ntiles = (n + kThreads - 1) / kThreads;
     a->status = h->status;
+    a->img = h->img;
+    a->tc_chunks = (h->L + kTcN - 1) / kTcN;
 }
 
 int set_error(int s, const char *msg) {
@@ -67,9 +69,9 @@ int set_error(int s, const char *msg) {
 // running maximum of the norms (non-negative floats order like their bit
 // patterns), and the row rewritten in place with its chunks swizzled.
 __global__ void landmark_prep_kernel(float *__restrict__ hi, int L, int D,
-                                     float *__restrict__ norms, float *__restrict__ lmax) {
+                                     float *__restrict__ norms, float *__restrict__ lmax,
+                                     int padded) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int padded = (L + 3) & ~3;
     if (j >= padded) return;
     if (j >= L) {
         norms[j] = 0.f;
@@ -93,9 +95,46 @@ __global__ void landmark_prep_kernel(float *__restrict__ hi, int L, int D,
 }
 
 cudaError_t launch_landmark_prep(float *hi, int L, int D, float *norms, float *lmax,
-                                 cudaStream_t stream) {
-    const int padded = (L + 3) & ~3;
-    landmark_prep_kernel<<<(padded + 255) / 256, 256, 0, stream>>>(hi, L, D, norms, lmax);
+                                 cudaStream_t stream, int pad) {
+    const int padded = (L + pad - 1) / pad * pad;
+    landmark_prep_kernel<<<(padded + 255) / 256, 256, 0, stream>>>(hi, L, D, norms, lmax,
+                                                                   padded);
+    return cudaGetLastError();
+}
+
+// One thread per 16-byte piece of a chunk image: piece c of column block blk
+// of landmark j holds values 4e..4e+3 (e = 8 blk + c) of the row, rounded to
+// TF32 (nearest, ties away), zero beyond d and for rows beyond L.  The rows
+// of hi are chunk-swizzled (logical chunk e at e ^ swz(D, j)).
+__global__ void tc_image_kernel(const float *__restrict__ hi, int L, int D,
+                                unsigned char *__restrict__ img, int Lpad) {
+    const int nb = tc_nblk(D);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)Lpad * nb * 8) return;
+    const int c = (int)(t & 7);
+    const int blk = (int)((t >> 3) % nb);
+    const int j = (int)((t >> 3) / nb);
+    const int e = blk * 8 + c;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j < L && e < D / 4) {
+        v = reinterpret_cast<const float4 *>(hi + (size_t)j * D)[e ^ swz(D, j)];
+        uint32_t r0, r1, r2, r3;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r0) : "f"(v.x));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r1) : "f"(v.y));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r2) : "f"(v.z));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r3) : "f"(v.w));
+        v = make_float4(__uint_as_float(r0), __uint_as_float(r1), __uint_as_float(r2),
+                        __uint_as_float(r3));
+    }
+    unsigned char *chunk = img + (size_t)(j / kTcN) * tc_chunk_bytes(D);
+    *reinterpret_cast<float4 *>(chunk + tc_image_offset(kTcN, j % kTcN, blk, c)) = v;
+}
+
+cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img,
+                            cudaStream_t stream) {
+    const int Lpad = (L + kTcN - 1) / kTcN * kTcN;
+    const long long threads = (long long)Lpad * tc_nblk(D) * 8;
+    tc_image_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(hi, L, D, img, Lpad);
     return cudaGetLastError();
 }
 }  // namespace esom
@@ -147,9 +186,17 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
     a.idx = idx;
     a.dist2 = dist2;
     a.mode = mode;
-    long long grid = (long long)h->blocks_per_sm * h->num_sms;
-    if (grid > a.ntiles) grid = a.ntiles;
-    cudaError_t e = h->ops->launch(a, (int)grid, h->smem, stream);
+    cudaError_t e;
+    if (h->screening) {
+        const long long tiles = (n + esom::kTcRows - 1) / esom::kTcRows;
+        long long grid = (long long)h->tc_blocks_per_sm * h->num_sms;
+        if (grid > tiles) grid = tiles;
+        e = h->tc->launch(a, (int)grid, h->tc_smem, stream);
+    } else {
+        long long grid = (long long)h->blocks_per_sm * h->num_sms;
+        if (grid > a.ntiles) grid = a.ntiles;
+        e = h->ops->launch(a, (int)grid, h->smem, stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     h->points += (uint64_t)n;
     return ESOM_OK;
@@ -196,7 +243,9 @@ esom_status esom_create(int d, int L, int k, esom_handle *out) {
     }
     e = cudaMalloc(&h->hi, (size_t)L * d * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->lo, (size_t)L * 2 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&h->norms, (size_t)((L + 3) & ~3) * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&h->norms, (size_t)((L + esom::kTcN - 1) / esom::kTcN * esom::kTcN) *
+                                      sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->status, 256);
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, 256);
     if (e != cudaSuccess) {
@@ -225,7 +274,9 @@ esom_status esom_set_landmarks(esom_handle h, const float *hi, const float *lo,
         e = cudaMemcpyAsync(h->lo, lo, (size_t)h->L * 2 * sizeof(float), cudaMemcpyDefault, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status + 1, 0, sizeof(float), st);
     if (e == cudaSuccess) e = esom::launch_landmark_prep(h->hi, h->L, h->d, h->norms,
-                                                         reinterpret_cast<float *>(h->status + 1), st);
+                                                         reinterpret_cast<float *>(h->status + 1), st,
+                                                         esom::kTcN);
+    if (e == cudaSuccess && h->screening) e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, st);
     if (e != cudaSuccess) return cuda_fail(e, "landmark copy");
     ++h->version;
     return ESOM_OK;
@@ -390,6 +441,68 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg) {
     cfg->landmark_chunk = h->chunk;
     cfg->landmark_chunks = h->nchunks;
     cfg->shared_bytes = (int)h->smem;
+    cfg->screening = h->screening;
+    if (h->screening) {
+        cfg->threads_per_block = esom::kTcThreads;
+        cfg->blocks_per_sm = h->tc_blocks_per_sm;
+        cfg->landmark_chunk = esom::kTcN;
+        cfg->landmark_chunks = (h->L + esom::kTcN - 1) / esom::kTcN;
+        cfg->shared_bytes = (int)h->tc_smem;
+    }
+    return ESOM_OK;
+}
+
+esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
+    if (!h) return fail(ESOM_EINVAL, "null handle");
+    if (mode != ESOM_SCREEN_FP32 && mode != ESOM_SCREEN_TF32)
+        return fail(ESOM_EINVAL, "unknown screening mode %d", mode);
+    esom_status s = check_device(h);
+    if (s != ESOM_OK) return s;
+    if (mode == ESOM_SCREEN_FP32) {
+        h->screening = 0;
+        return ESOM_OK;
+    }
+    const esom::TcOps *tc = esom::tc_ops(h->d, h->kc);
+    if (!tc) return fail(ESOM_EUNSUPPORTED, "no tensor-core kernel for d = %d, k = %d", h->d, h->k);
+    int major = 0, minor = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(compute capability)");
+    if (major != 10 || minor != 3)
+        return fail(ESOM_EUNSUPPORTED, "tensor-core screening needs sm_103 (device is sm_%d%d)",
+                    major, minor);
+    const size_t smem = esom::tc_smem_bytes(h->d);
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(shared memory opt-in)");
+    if (smem > (size_t)optin)
+        return fail(ESOM_EUNSUPPORTED, "needs %zu bytes of shared memory per block, device has %d",
+                    smem, optin);
+    e = cudaFuncSetAttribute(tc->func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(shared memory)");
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tc->func, esom::kTcThreads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (bps < 1) return fail(ESOM_EUNSUPPORTED, "tensor-core launch does not fit on an SM");
+    // Each block holds kTcCols of the SM's 512 TMEM columns.
+    if (bps * esom::kTcCols > 512) bps = 512 / esom::kTcCols;
+    if (!h->img) {
+        const size_t bytes = (size_t)((h->L + esom::kTcN - 1) / esom::kTcN) * esom::tc_chunk_bytes(h->d);
+        e = cudaMalloc(&h->img, bytes);
+        if (e != cudaSuccess) {
+            h->img = nullptr;
+            return fail(ESOM_ENOMEM, "device allocation of the landmark images: %s",
+                        cudaGetErrorString(e));
+        }
+    }
+    if (h->version > 0) {
+        e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, reinterpret_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return cuda_fail(e, "landmark image build");
+    }
+    h->tc = tc;
+    h->tc_smem = smem;
+    h->tc_blocks_per_sm = bps;
+    h->screening = mode;
     return ESOM_OK;
 }
 
@@ -399,6 +512,7 @@ esom_status esom_destroy(esom_handle h) {
     cudaFree(h->lo);
     cudaFree(h->norms);
     cudaFree(h->status);
+    cudaFree(h->img);
     for (int b = 0; b < 2; ++b) {
         cudaFree(h->stage_x[b]);
         cudaFree(h->stage_out[b]);

@@ -12,7 +12,7 @@ struct esom_ctx {
     int d = 0, L = 0, k = 0, kc = 0, dev = 0;
     float *hi = nullptr;   // L x d
     float *lo = nullptr;   // L x 2
-    float *norms = nullptr; // squared landmark norms, padded to a multiple of 4
+    float *norms = nullptr; // squared landmark norms, zero-padded to a multiple of kTcN
     int *status = nullptr; // device status word; the float after it: largest norm
     uint64_t version = 0;
     const esom::KernelOps *ops = nullptr;
@@ -22,6 +22,13 @@ struct esom_ctx {
     // launch configuration (derived from L, d and the chunk choice)
     int chunk = 0, nchunks = 0, blocks_per_sm = 0;
     size_t smem = 0;
+    // tensor-core screening (esom_set_screening); img holds the landmark
+    // chunk images while it is on
+    int screening = 0;
+    const esom::TcOps *tc = nullptr;
+    unsigned char *img = nullptr;
+    int tc_blocks_per_sm = 0;
+    size_t tc_smem = 0;
     // host-buffer pipeline state (created on first use)
     float *stage_x[2] = {nullptr, nullptr};
     float *stage_out[2] = {nullptr, nullptr};

@@ -31,4 +31,32 @@ const KernelOps *kernel_ops(int D, int kc) {
     }
 }
 
+#define ESOM_DECLARE_TC_D(DV) const TcOps *tc_ops_d##DV(int kc);
+ESOM_DECLARE_TC_D(4) ESOM_DECLARE_TC_D(8) ESOM_DECLARE_TC_D(12) ESOM_DECLARE_TC_D(16)
+ESOM_DECLARE_TC_D(20) ESOM_DECLARE_TC_D(24) ESOM_DECLARE_TC_D(28) ESOM_DECLARE_TC_D(32)
+ESOM_DECLARE_TC_D(36) ESOM_DECLARE_TC_D(40) ESOM_DECLARE_TC_D(44) ESOM_DECLARE_TC_D(48)
+ESOM_DECLARE_TC_D(52) ESOM_DECLARE_TC_D(56) ESOM_DECLARE_TC_D(60) ESOM_DECLARE_TC_D(64)
+
+const TcOps *tc_ops(int D, int kc) {
+    switch (D) {
+        case 4: return tc_ops_d4(kc);
+        case 8: return tc_ops_d8(kc);
+        case 12: return tc_ops_d12(kc);
+        case 16: return tc_ops_d16(kc);
+        case 20: return tc_ops_d20(kc);
+        case 24: return tc_ops_d24(kc);
+        case 28: return tc_ops_d28(kc);
+        case 32: return tc_ops_d32(kc);
+        case 36: return tc_ops_d36(kc);
+        case 40: return tc_ops_d40(kc);
+        case 44: return tc_ops_d44(kc);
+        case 48: return tc_ops_d48(kc);
+        case 52: return tc_ops_d52(kc);
+        case 56: return tc_ops_d56(kc);
+        case 60: return tc_ops_d60(kc);
+        case 64: return tc_ops_d64(kc);
+        default: return nullptr;
+    }
+}
+
 }  // namespace esom

@@ -275,12 +275,12 @@ struct ScanState {
     float thr;     // push threshold
 };
 
-template <int KC>
+template <int KC, int QS = kThreads>
 __device__ __forceinline__ void queue_flush(float (&keys)[KC], ScanState &st, const uint32_t *qk,
                                             int tid, int k, float M, float q) {
     const int mx = __reduce_max_sync(0xffffffffu, st.qn);
     for (int i = 0; i < mx; ++i) {
-        const float v = i < st.qn ? __uint_as_float(qk[i * kThreads + tid]) : INFINITY;
+        const float v = i < st.qn ? __uint_as_float(qk[i * QS + tid]) : INFINITY;
         key_insert<KC>(keys, v);
     }
     st.qn = 0;
@@ -425,7 +425,8 @@ __device__ __noinline__ void repair_order(float *cdp, int *cip) {
 template <int D, int KC, int KK>
 __device__ __forceinline__ bool rerank(const float4 (&x)[D / 4], const float (&keys)[KC],
                                        const float4 *Lg, uint32_t mask, int L, int k, float M,
-                                       float q, float (&ed)[KK], int (&ei)[KK]) {
+                                       float q, float (&ed)[KK], int (&ei)[KK],
+                                       float koff = 0.f) {
     float cd[KC];
     int ci[KC];
 #pragma unroll
@@ -463,18 +464,20 @@ __device__ __forceinline__ bool rerank(const float4 (&x)[D / 4], const float (&k
     }
     // Every landmark left out has a key >= the last key in the list (or was
     // never queued, which push_threshold covers), so its exact distance is at
-    // least last - 2q|last| - M.
+    // least last - 2q|last| - M.  Keys may be offset from distances by a
+    // constant koff of the point (key = distance - koff, up to M).
     const float last = keys[KC - 1];
     if (!(last < INFINITY)) return true;
     const float exact_k = at<KC>(cd, k - 1);
-    return last - 2.f * q * fabsf(last) - M > exact_k;
+    return last - 2.f * q * fabsf(last) - M > exact_k - koff;
 }
 
 // Neighbour indices parked in this thread's own column of the queue buffer
-// (32-bit words col[i * kThreads]; word i holds ranks 2i and 2i+1 as 16-bit
-// halves), so no other thread's words are touched.
+// (32-bit words col[i * QS], QS = threads of the tile; word i holds ranks 2i
+// and 2i+1 as 16-bit halves), so no other thread's words are touched.
+template <int QS = kThreads>
 __device__ __forceinline__ int nb_at(const uint32_t *col, int t) {
-    return (int)((col[(t >> 1) * kThreads] >> ((t & 1) * 16)) & 0xFFFFu);
+    return (int)((col[(t >> 1) * QS] >> ((t & 1) * 16)) & 0xFFFFu);
 }
 
 // ---------------------------------------------------------------------------
@@ -545,7 +548,7 @@ __device__ __forceinline__ PairTerm pair_term(const float4 (&lu)[D / 4], float2 
 // <X - L_u, L_v - L_u> = (|X - L_u|^2 + |L_v - L_u|^2 - |X - L_v|^2) / 2.
 // The v loop runs in groups of two pairs with independent chains; pairs
 // outside u < v < m inside a group are masked by selects.
-template <int D, int KK, int PASS>
+template <int D, int KK, int PASS, int QS = kThreads>
 __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t *nb,
                                           const float (&ss)[KK], int m, const float4 *Lg,
                                           const float2 *lo2, float2 l0, const FusedArgs &a,
@@ -553,7 +556,7 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
                                           float &A11, float &B0, float &B1, float &rho) {
 #pragma unroll 1
     for (int u = 0; u < m - 1; ++u) {
-        const int iu = nb_at(nb, u);
+        const int iu = nb_at<QS>(nb, u);
         float su = ss[0], du = sd[0];
 #pragma unroll
         for (int t = 1; t < KK; ++t)
@@ -571,7 +574,7 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
 #pragma unroll
         for (int v0 = 1; v0 < KK; v0 += 2) {
             if (v0 + 1 > u && v0 < m) {
-                const PairTerm c0 = pair_term<D, PASS>(lu, lut, lux, luy, su, du, nb_at(nb, v0),
+                const PairTerm c0 = pair_term<D, PASS>(lu, lut, lux, luy, su, du, nb_at<QS>(nb, v0),
                                                        ss[v0], sd[v0], Lg, lo2, a.adjust, nx, ny);
                 const bool k0 = c0.ok && v0 > u;
                 A00 = k0 ? A00 + c0.a00 : A00;
@@ -583,7 +586,7 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
                 if (v0 + 1 < KK) {
                     const int v1 = v0 + 1 < KK ? v0 + 1 : v0;
                     const PairTerm c1 =
-                        pair_term<D, PASS>(lu, lut, lux, luy, su, du, nb_at(nb, v1), ss[v1],
+                        pair_term<D, PASS>(lu, lut, lux, luy, su, du, nb_at<QS>(nb, v1), ss[v1],
                                            sd[v1], Lg, lo2, a.adjust, nx, ny);
                     const bool k1 = c1.ok && v1 < m;
                     A00 = k1 ? A00 + c1.a00 : A00;
@@ -614,7 +617,7 @@ struct SlowSolve {
     int m;
 };
 
-template <int D, int KK>
+template <int D, int KK, int QS = kThreads>
 __device__ __noinline__ double2 solve_slow(const SlowSolve in, const float *sdp,
                                            const float *ssp, const uint32_t *nb,
                                            const float4 *Lg, const float2 *lo2, float2 l0,
@@ -639,7 +642,7 @@ __device__ __noinline__ double2 solve_slow(const SlowSolve in, const float *sdp,
                 ss[t] = ssp[t];
             }
             float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f, z4 = 0.f, rho = 0.f;
-            pair_sums<D, KK, 1>(sd, nb, ss, in.m, Lg, lo2, l0, a, (float)(-v1 / nn),
+            pair_sums<D, KK, 1, QS>(sd, nb, ss, in.m, Lg, lo2, l0, a, (float)(-v1 / nn),
                                 (float)(v0 / nn), z0, z1, z2, z3, z4, rho);
             const double lmin = (double)rho;
             det = lmin * (tr - lmin);
@@ -683,7 +686,7 @@ __device__ __noinline__ double2 solve_slow(const SlowSolve in, const float *sdp,
 // exact squared distances of the k nearest; their landmark indices are in
 // this thread's column of shared memory (nb_at(nb, t) for rank t).
 
-template <int D, int KK>
+template <int D, int KK, int QS = kThreads>
 __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uint32_t *nb,
                                                 const float4 *Lg, const float2 *lo2,
                                                 const FusedArgs &a) {
@@ -738,12 +741,12 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
     }
 
     // 2-D coordinates relative to the nearest neighbour's.
-    const float2 l0 = __ldg(&lo2[nb_at(nb, 0)]);
+    const float2 l0 = __ldg(&lo2[nb_at<QS>(nb, 0)]);
     float C0 = 0.f, C1 = 0.f, Ssum = 0.f, M0 = 0.f, M1 = 0.f;
 #pragma unroll
     for (int t = 0; t < KK; ++t)
         if (t < m) {
-            const float2 lt = __ldg(&lo2[nb_at(nb, t)]);
+            const float2 lt = __ldg(&lo2[nb_at<QS>(nb, t)]);
             const float px = lt.x - l0.x, py = lt.y - l0.y;
             C0 = fmaf(ss[t], px, C0);
             C1 = fmaf(ss[t], py, C1);
@@ -754,7 +757,7 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
 
     // Step 3: pair terms, u < v < m.
     float A00 = 0.f, A01 = 0.f, A11 = 0.f, B0 = 0.f, B1 = 0.f, rho = 0.f;
-    pair_sums<D, KK, 0>(sd, nb, ss, m, Lg, lo2, l0, a, 0.f, 0.f, A00, A01, A11, B0, B1, rho);
+    pair_sums<D, KK, 0, QS>(sd, nb, ss, m, Lg, lo2, l0, a, 0.f, 0.f, A00, A01, A11, B0, B1, rho);
 
     // Step 4: FP64 solve; near-singular systems go to the out-of-line path.
     const double a00 = A00, a01 = A01, a11 = A11, b0 = B0, b1 = B1;
@@ -775,7 +778,7 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
             tsd[t] = sd[t];
             tss[t] = ss[t];
         }
-        const double2 r = solve_slow<D, KK>(in, tsd, tss, nb, Lg, lo2, l0, a);
+        const double2 r = solve_slow<D, KK, QS>(in, tsd, tss, nb, Lg, lo2, l0, a);
         px = r.x;
         py = r.y;
     }

@@ -37,6 +37,8 @@ struct FusedArgs {
     unsigned key_mask;    // low bits of a screening key that hold the landmark index
     float key_quant;      // 2^(bits - 23): relative perturbation of a key
     int *status;          // device status words: [0] error bits, [2] rescan count
+    const unsigned char *img;  // tensor-core screening: landmark chunk images
+    int tc_chunks;        // ceil(L / kTcN) chunks in img
 };
 
 // Many datasets of one (D, list capacity) in one launch: every block walks a
@@ -62,14 +64,65 @@ struct KernelOps {
 // Returns the instantiation for dimension D and list capacity kc, or nullptr.
 const KernelOps *kernel_ops(int D, int kc);
 
+// ---------------------------------------------------------------------------
+// Tensor-core screening (tcgen05, TF32): tiles of kTcRows points (the MMA's M
+// and the TMEM lanes), landmark chunks of kTcN (the MMA's N); one block =
+// four selection warps (one thread per point) and one producer warp that
+// streams landmark chunk images and issues the MMAs.
+constexpr int kTcRows = 128;
+constexpr int kTcN = 64;
+constexpr int kTcThreads = 160;
+constexpr int kTcCols = 2 * kTcN;  // TMEM columns: two accumulator buffers
+
+// 128-byte column blocks of a row (32 TF32 values each), pipeline stages of
+// the landmark ring, and resident blocks per SM the launch aims for (three
+// where the registers of the projection fit in 128 a thread, else two).
+__host__ __device__ constexpr int tc_nblk(int D) { return (D + 31) / 32; }
+__host__ __device__ constexpr int tc_stages(int D) { return tc_nblk(D) == 1 ? 3 : 2; }
+__host__ __device__ constexpr int tc_minb(int D, int KC) { return D <= 16 && KC <= 24 ? 3 : 2; }
+
+// Bytes of one chunk image: kTcN rows x 128 bytes per column block, rows in
+// the 128-byte-swizzled K-major order the MMA reads (see tc_image_offset).
+__host__ __device__ inline size_t tc_chunk_bytes(int D) { return (size_t)kTcN * 128 * tc_nblk(D); }
+
+// Byte offset of 16-byte piece c (values 4c..4c+3 of column block blk) of
+// row r inside a 1024-byte-aligned operand of `rows` rows: 8-row groups of
+// 1024 bytes, rows 128 bytes apart, piece c of row r at slot c ^ (r mod 8).
+__host__ __device__ inline unsigned tc_image_offset(int rows, int r, int blk, int c) {
+    return (unsigned)(blk * rows * 128 + (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+}
+
+inline size_t tc_smem_bytes(int D) {
+    const size_t nb = (size_t)tc_nblk(D);
+    return 1024                                  // alignment slack
+           + 2 * (size_t)kTcRows * 128 * nb      // point tiles (double buffered)
+           + (size_t)tc_stages(D) * kTcN * 128 * nb  // landmark chunk ring
+           + (size_t)kQueue * kTcRows * 4        // candidate queue
+           + 256;                                // barriers, TMEM address, flags
+}
+
+struct TcOps {
+    const void *func;
+    int kc;
+    cudaError_t (*launch)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
+};
+
+// Tensor-core instantiation for D and list capacity kc, or nullptr.
+const TcOps *tc_ops(int D, int kc);
+
+// Builds the TF32 chunk images of the landmarks from the (chunk-swizzled)
+// rows of hi: ceil(L / kTcN) images of tc_chunk_bytes(D), rows beyond L zero.
+cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img,
+                            cudaStream_t stream);
+
 // Records `msg` as this host thread's last error message; returns s.
 int set_error(int s, const char *msg);
 
 // Squared landmark norms (norms[j], j < L; zero padding up to a multiple of
-// 4), the largest norm (*lmax, which must hold 0 on entry), and the rows of
-// hi swizzled in place (see swz).
+// `pad`, itself a multiple of 4), the largest norm (*lmax, which must hold 0
+// on entry), and the rows of hi swizzled in place (see swz).
 cudaError_t launch_landmark_prep(float *hi, int L, int D, float *norms, float *lmax,
-                                 cudaStream_t stream);
+                                 cudaStream_t stream, int pad = 4);
 
 // Landmark rows are stored with their 16-byte chunks permuted: logical chunk
 // e of row j sits at physical chunk e ^ swz(j), with g = gcd(d/4, 8) and

@@ -1,0 +1,493 @@
+// Tensor-core screened projection kernel for sm_103a (tcgen05, TF32).
+//
+// Same result as the plain fused kernel (esom_fused.cuh), computed with the
+// distance block of step 1 on the tensor cores.  The paper's k-NN spends its
+// time in the g x d distance block (Section 4.2, and Section 5's remark that
+// the k-NN cost grows with g d); here that block is a dense contraction of a
+// tile of 128 points with chunks of 64 landmarks:
+//
+//   T = X_tile . L_chunk^T        (tcgen05.mma kind::tf32, FP32 accumulators
+//                                  in tensor memory, operands in shared
+//                                  memory in the 128-byte-swizzled K-major
+//                                  layout)
+//   v_j = |L_j|^2 - 2 T_j         (screening value = |X - L_j|^2 - |X|^2,
+//                                  up to the TF32 error)
+//
+// Each selection thread owns one point (one TMEM lane), reads its 64 values
+// of a chunk with one tcgen05.ld, keys them like the plain kernel (value with
+// the landmark index in the low mantissa bits) and keeps the KC smallest.
+// The list is then re-ranked with exact FP32 difference-form distances, and
+// a bound on the TF32 screening error certifies that no landmark outside the
+// list can be among the k nearest; a point that fails is rescanned exactly.
+// So the neighbours, their distances and the coordinates are the plain
+// kernel's, bit for bit; TF32 only decides how often a point is rescanned.
+//
+// Roles: warps 0-3 select (thread t <-> point row t <-> TMEM lane t); warp 4
+// is the producer: one lane streams the landmark chunk images through a ring
+// of shared-memory stages by bulk copies (cp.async.bulk + mbarrier) and
+// issues the MMAs into two TMEM accumulator buffers, so the MMA of chunk c+1
+// overlaps the selection of chunk c.  The selection threads write their
+// next tile's operand (TF32-rounded rows) before they re-rank and project
+// the current one, so the next tile's MMAs overlap the projection.  Every
+// wait is bounded; on a timeout the block raises the status word, drains
+// its own copies and MMAs and frees its tensor memory.
+#pragma once
+
+#include "esom_fused.cuh"
+
+namespace esom {
+
+// ---------------------------------------------------------------------------
+// tcgen05 / tensor-memory helpers (inline PTX).
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzle layout: 8-row groups 1024 bytes apart (stride byte offset), the
+// leading byte offset unused for this layout (1), descriptor version 1,
+// layout type 2 (128-byte swizzle).  The operand base is 1024-byte aligned;
+// a K step inside the 128-byte row moves the start address by its bytes.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A and B TF32
+// (bits 7-9 and 10-12 = 2), both K-major, N / 8 at bits 17-22, M / 16 at
+// bits 24-28.
+__host__ __device__ constexpr uint32_t tc_idesc() {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+           ((uint32_t)(kTcRows >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrives on `bar` once every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// 64 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes
+// 32 (w mod 4) ..), waited for inside the same statement so that no use of
+// the values can be scheduled before the load has completed.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
+        "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
+        "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, "
+        "[%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]),
+          "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
+          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+          "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]),
+          "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]),
+          "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// FP32 -> TF32, round to nearest (ties away from zero); low 13 bits zero.
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Bound on the TF32 part of the screening error per unit |X| max|L|: both
+// operands rounded to 11 significant bits (relative 2^-11 each, so 2^-10 on
+// a product), accumulation of D exact products with at most D + 1 FP32
+// roundings (2^-23 each, relative to the sum of |products|); twice that in
+// v_j = |L_j|^2 - 2 T_j, and a factor 2 of margin.
+template <int D>
+__device__ __forceinline__ float tc_dot_bound() {
+    return 4.f * (9.765625e-4f + (float)(D + 1) * 1.1920929e-7f);
+}
+
+// ---------------------------------------------------------------------------
+
+template <int D, int KC>
+__global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const FusedArgs a) {
+    static_assert(D % 4 == 0 && D >= 4 && D <= 64, "D must be a multiple of 4 in [4, 64]");
+    static_assert(KC >= 8 && KC <= 36 && KC % 4 == 0, "list capacity out of range");
+    static_assert((KC - 4) / 2 <= kQueue, "neighbour indices must fit in the thread's queue column");
+    constexpr int KK = KC - 4;
+    constexpr int NB = tc_nblk(D);
+    constexpr int S = tc_stages(D);
+    constexpr int KS = (D + 7) / 8;  // MMA K steps of 8 TF32 values (32 bytes)
+    constexpr uint32_t kABytes = kTcRows * 128 * NB;
+    constexpr uint32_t kBBytes = kTcN * 128 * NB;
+    constexpr uint32_t kIdesc = tc_idesc();
+    constexpr int QS = kTcRows;  // queue stride: one column per selection thread
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    unsigned char *sA = base;                      // 2 point tiles
+    unsigned char *sB = base + 2 * kABytes;        // S landmark chunk stages
+    uint32_t *qk = reinterpret_cast<uint32_t *>(sB + S * kBBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(qk + kQueue * kTcRows);
+    uint64_t *l_full = bars, *l_empty = bars + S;
+    uint64_t *t_full = bars + 2 * S, *t_empty = bars + 2 * S + 2;
+    uint64_t *a_ready = bars + 2 * S + 4, *done_bar = bars + 2 * S + 6;
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bars + 2 * S + 8);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(s_tmem + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long ntiles = (a.n + kTcRows - 1) / kTcRows;
+    const long long first = blockIdx.x;
+    const long long my_tiles =
+        first < ntiles ? (ntiles - 1 - first) / (long long)gridDim.x + 1 : 0;
+    if (my_tiles == 0) return;  // whole block, before any barrier or TMEM use
+    const int nch = a.tc_chunks;
+
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&l_full[i], 1);
+            mbar_init(&l_empty[i], 1);
+        }
+        mbar_init(&t_full[0], 1);
+        mbar_init(&t_full[1], 1);
+        mbar_init(&t_empty[0], 4);
+        mbar_init(&t_empty[1], 4);
+        mbar_init(&a_ready[0], 4);
+        mbar_init(&a_ready[1], 4);
+        mbar_init(done_bar, 1);
+        fence_mbar_init();
+        *s_abort = 0;
+    }
+    if (warp == 4) {
+        tmem_alloc(s_tmem, kTcCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    auto raise_abort = [&]() {
+        *s_abort = 1;
+        atomicOr(a.status, kErrWaitTimeout);
+    };
+
+    if (warp == 4) {
+        // ------------------------------------------------------------------
+        // Producer: lane 0 streams chunk images and issues the MMAs.
+        if (lane == 0) {
+            const long long total = my_tiles * nch;
+            long long issued = 0, landed = 0;
+            auto issue = [&](long long g) {
+                const int s = (int)(g % S);
+                const int c = (int)(g % nch);
+                mbar_expect_tx(&l_full[s], kBBytes);
+                bulk_g2s(sB + (size_t)s * kBBytes, a.img + (size_t)c * kBBytes, kBBytes,
+                         &l_full[s]);
+            };
+            for (; issued < total && issued < S; ++issued) issue(issued);
+            bool ok = true;
+            long long g = 0;
+            for (long long i = 0; i < my_tiles && ok; ++i) {
+                const int buf = (int)(i & 1);
+                if (!mbar_wait(&a_ready[buf], (uint32_t)((i >> 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t aaddr = smem_u32(sA + (size_t)buf * kABytes);
+                for (int c = 0; c < nch; ++c, ++g) {
+                    const int s = (int)(g % S), tb = (int)(g & 1);
+                    if (*s_abort || !mbar_wait(&l_full[s], (uint32_t)((g / S) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    landed = g + 1;
+                    if (!mbar_wait(&t_empty[tb], (uint32_t)(((g >> 1) & 1) ^ 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t baddr = smem_u32(sB + (size_t)s * kBBytes);
+#pragma unroll
+                    for (int ks = 0; ks < KS; ++ks) {
+                        const uint32_t ka = (uint32_t)((ks >> 2) * kTcRows * 128 + (ks & 3) * 32);
+                        const uint32_t kb = (uint32_t)((ks >> 2) * kTcN * 128 + (ks & 3) * 32);
+                        mma_tf32(tmem + (uint32_t)(tb * kTcN), sw128_desc(aaddr + ka),
+                                 sw128_desc(baddr + kb), kIdesc, ks > 0 ? 1u : 0u);
+                    }
+                    mma_commit(&t_full[tb]);
+                    mma_commit(&l_empty[s]);
+                    // Refill the stage of the previous step (its MMA was
+                    // issued one step ago) with the chunk S steps after it.
+                    if (g >= 1 && g - 1 + S < total && issued == g - 1 + S) {
+                        const long long h = g - 1;
+                        if (!mbar_wait(&l_empty[h % S], (uint32_t)((h / S) & 1))) {
+                            ok = false;
+                            break;
+                        }
+                        issue(issued++);
+                    }
+                }
+            }
+            if (!ok) raise_abort();
+            // Drain: every MMA issued, then every copy issued but not waited.
+            mma_commit(done_bar);
+            mbar_wait(done_bar, 0);
+            for (long long h = landed; h < issued; ++h)
+                mbar_wait(&l_full[h % S], (uint32_t)((h / S) & 1));
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------------
+        // Selection: thread tid owns row tid of every tile of this block.
+        const uint32_t mask = a.key_mask;
+        const float q = a.key_quant;
+        const float lmax = *a.lmax;
+        const float4 *Lg = reinterpret_cast<const float4 *>(a.hi);
+        const float2 *lo2 = reinterpret_cast<const float2 *>(a.lo);
+        const uint32_t my_lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        constexpr float kGamma = (2.25f * D + 10.f) * kU * 1.25f;
+
+        // Writes this thread's row of tile `tile` (TF32, swizzled) into
+        // point buffer `buf` and returns |x|^2 (FP32, exact row).
+        auto write_tile = [&](long long tile, int buf) -> float {
+            const long long row = tile * kTcRows + tid;
+            const bool act = row < a.n;
+            const float4 *xp = reinterpret_cast<const float4 *>(a.X) + (act ? row : 0) * (D / 4);
+            unsigned char *A = sA + (size_t)buf * kABytes;
+            float xx = 0.f;
+#pragma unroll
+            for (int blk = 0; blk < NB; ++blk)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int e = blk * 8 + c;  // float4 index of the row
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (e < D / 4 && act) {
+                        v = __ldg(xp + e);
+                        xx = fmaf(v.x, v.x, xx);
+                        xx = fmaf(v.y, v.y, xx);
+                        xx = fmaf(v.z, v.z, xx);
+                        xx = fmaf(v.w, v.w, xx);
+                        v = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
+                    }
+                    if (e < 2 * KS)  // pieces the MMA K steps read
+                        *reinterpret_cast<float4 *>(A + tc_image_offset(kTcRows, tid, blk, c)) = v;
+                }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_ready[buf]);
+            return xx;
+        };
+
+        bool ok = true;
+        float xx_next = write_tile(first, 0);
+        long long g = 0;
+        long long tile = first;
+        for (long long i = 0; i < my_tiles && ok; ++i, tile += gridDim.x) {
+            const long long row = tile * kTcRows + tid;
+            const bool active = row < a.n;
+            const float xx = xx_next;
+            const float xn = sqrtf(xx);
+            const float sx = xn + lmax;
+            // |v_j - (exact FP32 distance - |x|^2)| <= M
+            const float M = tc_dot_bound<D>() * xn * lmax + 2.f * kGamma * sx * sx;
+
+            float keys[KC];
+            ScanState st;
+            st.qn = 0;
+            st.thr = INFINITY;
+            for (int c = 0; c < nch; ++c, ++g) {
+                const int tb = (int)(g & 1);
+                const bool w = mbar_wait(&t_full[tb], (uint32_t)((g >> 1) & 1));
+                if (!__all_sync(0xffffffffu, w)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                float v[64];
+                tmem_ld64(my_lane_addr + (uint32_t)(tb * kTcN), v);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&t_empty[tb]);
+
+                const int base = c * kTcN;
+                const int cnt = a.L - base < kTcN ? a.L - base : kTcN;
+                const float4 *N4 = reinterpret_cast<const float4 *>(a.norms + base);
+                int jstart = 0;
+                if (c == 0) {
+                    // The first KF values go straight into the list (one
+                    // sorting network); the KF - KC largest are dropped,
+                    // which the certificate covers like any key pushed out.
+                    constexpr int KF = (KC + 7) & ~7;
+                    float kv[KF];
+#pragma unroll
+                    for (int t = 0; t < KF; ++t)
+                        kv[t] = t < cnt ? make_key(fmaf(-2.f, v[t], __ldg(a.norms + t)),
+                                                   (uint32_t)t, mask)
+                                        : INFINITY;
+                    key_sort<KF>(kv);
+#pragma unroll
+                    for (int t = 0; t < KC; ++t) keys[t] = kv[t];
+                    st.thr = push_threshold(at<KC>(keys, a.k - 1), M, q);
+                    jstart = KF;
+                }
+#pragma unroll
+                for (int jb = 0; jb < kTcN; jb += 8) {
+                    if (jb < jstart) continue;
+                    const float4 n0 = __ldg(N4 + jb / 4), n1 = __ldg(N4 + jb / 4 + 1);
+                    const float nn[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float key =
+                            make_key(fmaf(-2.f, v[jb + e], nn[e]), (uint32_t)(base + jb + e), mask);
+                        if (key < st.thr && jb + e < cnt) {
+                            qk[st.qn * QS + tid] = __float_as_uint(key);
+                            ++st.qn;
+                        }
+                    }
+                    if (__any_sync(0xffffffffu, st.qn > kQueue - 8))
+                        queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
+                }
+            }
+            if (!ok) break;
+            queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
+
+            // The next tile's operand, so that its MMAs run while this tile
+            // is re-ranked and projected.
+            if (i + 1 < my_tiles) xx_next = write_tile(tile + gridDim.x, (int)((i + 1) & 1));
+
+            // Step 1b: exact re-rank of the list, certificate, rare rescan.
+            float4 xr[D / 4];
+            const float4 *xp = reinterpret_cast<const float4 *>(a.X) + (active ? row : 0) * (D / 4);
+#pragma unroll
+            for (int e = 0; e < D / 4; ++e)
+                xr[e] = active ? __ldg(xp + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            float sd[KK];
+            int si[KK];
+            const bool cert = rerank<D, KC, KK>(xr, keys, Lg, mask, a.L, a.k, M, q, sd, si, xx);
+            if (__builtin_expect(!cert, 0)) {
+                if (active) atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
+                float4 tx[D / 4];
+                float tsd[KK];
+                int tsi[KK];
+#pragma unroll
+                for (int e = 0; e < D / 4; ++e) tx[e] = xr[e];
+                exact_rescan<D, KK>(tx, Lg, a.L, tsd, tsi);
+#pragma unroll
+                for (int t = 0; t < KK; ++t) {
+                    sd[t] = tsd[t];
+                    si[t] = tsi[t];
+                }
+            }
+
+            if (a.mode == kKnn) {
+                if (active) {
+#pragma unroll
+                    for (int s2 = 0; s2 < KK; ++s2)
+                        if (s2 < a.k) {
+                            a.idx[row * a.k + s2] = si[s2];
+                            if (a.dist2) a.dist2[row * a.k + s2] = sd[s2];
+                        }
+                }
+                continue;
+            }
+            uint32_t *nb = qk + tid;
+#pragma unroll
+            for (int s2 = 0; s2 < KK; s2 += 2)
+                nb[(s2 >> 1) * QS] = (uint32_t)si[s2] | ((uint32_t)si[s2 + 1] << 16);
+            const float2 p = project_point<D, KK, QS>(sd, nb, Lg, lo2, a);
+            if (active) reinterpret_cast<float2 *>(a.out)[row] = p;
+        }
+        if (!ok) raise_abort();
+    }
+
+    // Teardown: every MMA has completed (the producer waited for its last
+    // commit) and every tensor-memory read has been waited for.
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTcCols);
+    }
+}
+
+template <int D, int KC>
+cudaError_t launch_tc(const FusedArgs &a, int grid, size_t smem, cudaStream_t stream) {
+    tc_kernel<D, KC><<<grid, kTcThreads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D, int KC>
+struct TcInstance {
+    static const TcOps ops;
+};
+
+template <int D, int KC>
+const TcOps TcInstance<D, KC>::ops = {reinterpret_cast<const void *>(&tc_kernel<D, KC>), KC,
+                                      &launch_tc<D, KC>};
+
+#define ESOM_DEFINE_TC_D(DV)                                         \
+    const TcOps *tc_ops_d##DV(int kc) {                              \
+        switch (kc) {                                                \
+            case 8: return &TcInstance<DV, 8>::ops;                  \
+            case 12: return &TcInstance<DV, 12>::ops;                \
+            case 16: return &TcInstance<DV, 16>::ops;                \
+            case 20: return &TcInstance<DV, 20>::ops;                \
+            case 24: return &TcInstance<DV, 24>::ops;                \
+            case 28: return &TcInstance<DV, 28>::ops;                \
+            case 32: return &TcInstance<DV, 32>::ops;                \
+            case 36: return &TcInstance<DV, 36>::ops;                \
+            default: return nullptr;                                 \
+        }                                                            \
+    }
+
+}  // namespace esom

@@ -86,7 +86,7 @@ def test_som_update_bmu_from_knn(esom):
     assert st == 0, esom.esom_last_error()
     torch.cuda.synchronize()
     bmu = idx[:, 0].cpu().numpy()
-    oidx, od2 = oracle.knn(w.X[:4096], w.hi, 1)
+    oidx, od2 = oracle.knn(w.X[:4096], w.hi, 2)
     differ = np.nonzero(bmu != oidx[:, 0])[0]
     for i in differ:  # only ties of the nearest distance may differ
         dd = ((w.X[i].astype(np.float64) - w.hi[bmu[i]].astype(np.float64)) ** 2).sum()
