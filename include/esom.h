@@ -57,18 +57,21 @@ typedef enum {
 /* Creates a projection context for points of dimension d, L landmarks and k
  * neighbours (Section 3.1 step 1 requires 3 <= k <= L; k = 2 is accepted as
  * a degenerate case whose result is the nearest landmark's 2-D position).
- * Allocates the device copies of the landmarks, their squared norms and a
- * device status word on the current device.  On success *out receives the
- * handle. */
+ * Allocates the device copies of the landmarks, their squared norms, a
+ * device status word and, for L <= 4096, an L x L table of squared landmark
+ * distances (L*L*4 bytes: 64 MiB at L = 4096) on the current device.  On
+ * success *out receives the handle. */
 esom_status esom_create(int d, int L, int k, esom_handle *out);
 
 /* Copies the landmarks into the handle (Section 3.1: L is g x d, l is g x 2;
  * the paper's g is L here).  hi: L x d float32, lo: L x 2 float32, host or
  * device pointers (copied with cudaMemcpyDefault on `stream`).  The caller
  * keeps ownership and may reuse the buffers once the copy has run on the
- * stream.  A small kernel on the same stream then computes the landmarks'
- * squared norms for the screening scan.  Each call increments the landmark
- * version.  Projections queued on other streams are not ordered against this
+ * stream.  Small kernels on the same stream then compute the landmarks'
+ * squared norms for the screening scan and, for L <= 4096, the table of
+ * squared distances |L_u - L_v|^2 that the pair loop of step 3 reads (the
+ * values the loop would otherwise compute per point, bit for bit).  Each
+ * call increments the landmark version.  Projections queued on other streams are not ordered against this
  * copy by the library. */
 esom_status esom_set_landmarks(esom_handle h, const float *hi, const float *lo,
                                esom_stream_t stream);
@@ -153,15 +156,18 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg);
  * distance + selection; the block is the g x d term of the cost).
  *   ESOM_SCREEN_FP32  the default: FP32 CUDA-core scan.
  *   ESOM_SCREEN_TF32  the distance block X . L^T runs on the tensor cores
- *                     (tcgen05, TF32 operands, FP32 accumulation in tensor
- *                     memory), 128 points by 64 landmarks an MMA tile.
+ *                     (tcgen05, FP32 accumulation in tensor memory, 128
+ *                     points by 64 landmarks an MMA tile) with operands
+ *                     split into two TF32 parts, x = x_hi + x_lo, and the
+ *                     three products x_hi l_hi + x_lo l_hi + x_hi l_lo
+ *                     (screening error ~2^-21 relative, like FP32's).
  * Either way the listed candidates are re-ranked with exact FP32 distances
  * and a bound on the screening error certifies that no other landmark can be
  * among the k nearest (a point that fails is rescanned exactly; see
  * esom_get_stats), so both modes return the same neighbours, distances and
  * coordinates, bit for bit; the mode only changes speed.
- * Switching to TF32 allocates the landmark images (ceil(L/64) * 64 * 128 *
- * ceil(d/32) bytes, kept until esom_destroy) and, if landmarks are set,
+ * Switching to TF32 allocates the landmark images (2 * ceil(L/64) * 64 * 128
+ * * ceil(d/32) bytes, kept until esom_destroy) and, if landmarks are set,
  * builds them on `stream`; later esom_set_landmarks calls rebuild them.
  * Errors: ESOM_EINVAL (unknown mode), ESOM_EUNSUPPORTED (device is not
  * sm_103, or no kernel for this d and k), ESOM_ENOMEM, ESOM_ECUDA.
@@ -281,6 +287,19 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
 double esom_server_now(esom_server s);
 /* Queues one frame of `session` that arrived at time `arrival`. */
 esom_status esom_server_submit(esom_server s, int session, double arrival);
+/* Coalescing (off by default): when a session's frames have queued up
+ * behind its frame in flight, start them together -- their SOM steps in
+ * order, then one projection that completes all of them.  The landmarks
+ * follow the same trajectory as frame by frame, so the output after the
+ * last frame is the same; only the intermediate projections are skipped
+ * (an interactive view shows the newest one).  Keeps latency bounded when
+ * frames arrive faster than the GPU projects them. */
+esom_status esom_server_set_coalescing(esom_server s, int on);
+/* Screening mode (ESOM_SCREEN_*) of the handles of sessions added from now
+ * on; only before the first esom_server_add_session (ESOM_EINVAL after).
+ * Results are the same in either mode; TF32 adds the landmark images to each
+ * session's footprint. */
+esom_status esom_server_set_screening(esom_server s, int mode);
 /* Collects finished frames (up to max) and starts queued ones in free
  * slots; wait_all != 0 blocks until every queued frame has finished (or
  * max records were filled). */

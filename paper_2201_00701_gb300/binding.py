@@ -107,6 +107,8 @@ def load(build_if_missing: bool = False):
         "esom_server_add_session": ([P, ctypes.POINTER(SessionDesc), P, P, P,
                                      ctypes.POINTER(I)], I),
         "esom_server_now": ([P], ctypes.c_double),
+        "esom_server_set_coalescing": ([P, I], I),
+        "esom_server_set_screening": ([P, I], I),
         "esom_server_submit": ([P, I, ctypes.c_double], I),
         "esom_server_poll": ([P, I, ctypes.POINTER(FrameDone), I, ctypes.POINTER(I)], I),
         "esom_server_session_output": ([P, I, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_uint64)], I),
@@ -244,6 +246,14 @@ def esom_server_add_session(s, desc: "SessionDesc", points_ptr: int, hi_ptr: int
 
 def esom_server_now(s) -> float:
     return float(load().esom_server_now(s))
+
+
+def esom_server_set_coalescing(s, on: bool) -> int:
+    return load().esom_server_set_coalescing(s, int(on))
+
+
+def esom_server_set_screening(s, mode: int) -> int:
+    return load().esom_server_set_screening(s, mode)
 
 
 def esom_server_submit(s, session: int, arrival: float) -> int:
@@ -403,7 +413,7 @@ def device_view(ptr: int, shape, typestr: str = "<f4"):
 
     v = _View()
     v.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
-                                  "data": (int(ptr), True), "version": 2, "strides": None}
+                                  "data": (int(ptr), False), "version": 2, "strides": None}
     return torch.as_tensor(v, device="cuda")
 
 
@@ -442,6 +452,12 @@ class Server:
 
     def now(self) -> float:
         return esom_server_now(self.s)
+
+    def set_coalescing(self, on: bool):
+        check(esom_server_set_coalescing(self.s, on))
+
+    def set_screening(self, mode: int):
+        check(esom_server_set_screening(self.s, mode))
 
     def submit(self, session: int, arrival: float | None = None):
         check(esom_server_submit(self.s, session, self.now() if arrival is None else arrival))

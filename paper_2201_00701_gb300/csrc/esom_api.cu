@@ -57,6 +57,7 @@ void fill_args(const esom_ctx *h, const float *points, long long n, float *out, 
     a->ntiles = (n + kThreads - 1) / kThreads;
     a->status = h->status;
     a->img = h->img;
+    a->qtab = h->qtab;
     a->tc_chunks = (h->L + kTcN - 1) / kTcN;
 }
 
@@ -103,9 +104,17 @@ cudaError_t launch_landmark_prep(float *hi, int L, int D, float *norms, float *l
 }
 
 // One thread per 16-byte piece of a chunk image: piece c of column block blk
-// of landmark j holds values 4e..4e+3 (e = 8 blk + c) of the row, rounded to
-// TF32 (nearest, ties away), zero beyond d and for rows beyond L.  The rows
-// of hi are chunk-swizzled (logical chunk e at e ^ swz(D, j)).
+// of landmark j holds values 4e..4e+3 (e = 8 blk + c) of the row split into
+// TF32 parts -- hi = tf32(v) in the first half of the image, lo = tf32(v -
+// hi) in the second (nearest, ties away) -- zero beyond d and for rows
+// beyond L.  The rows of hi are chunk-swizzled (logical chunk e at
+// e ^ swz(D, j)).
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 __global__ void tc_image_kernel(const float *__restrict__ hi, int L, int D,
                                 unsigned char *__restrict__ img, int Lpad) {
     const int nb = tc_nblk(D);
@@ -115,19 +124,17 @@ __global__ void tc_image_kernel(const float *__restrict__ hi, int L, int D,
     const int blk = (int)((t >> 3) % nb);
     const int j = (int)((t >> 3) / nb);
     const int e = blk * 8 + c;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
     if (j < L && e < D / 4) {
-        v = reinterpret_cast<const float4 *>(hi + (size_t)j * D)[e ^ swz(D, j)];
-        uint32_t r0, r1, r2, r3;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r0) : "f"(v.x));
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r1) : "f"(v.y));
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r2) : "f"(v.z));
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r3) : "f"(v.w));
-        v = make_float4(__uint_as_float(r0), __uint_as_float(r1), __uint_as_float(r2),
-                        __uint_as_float(r3));
+        const float4 v = reinterpret_cast<const float4 *>(hi + (size_t)j * D)[e ^ swz(D, j)];
+        h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+        l = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z),
+                        tf32_rna(v.w - h.w));
     }
     unsigned char *chunk = img + (size_t)(j / kTcN) * tc_chunk_bytes(D);
-    *reinterpret_cast<float4 *>(chunk + tc_image_offset(kTcN, j % kTcN, blk, c)) = v;
+    const unsigned off = tc_image_offset(kTcN, j % kTcN, blk, c);
+    *reinterpret_cast<float4 *>(chunk + off) = h;
+    *reinterpret_cast<float4 *>(chunk + tc_chunk_bytes(D) / 2 + off) = l;
 }
 
 cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img,
@@ -246,6 +253,8 @@ esom_status esom_create(int d, int L, int k, esom_handle *out) {
     if (e == cudaSuccess)
         e = cudaMalloc(&h->norms, (size_t)((L + esom::kTcN - 1) / esom::kTcN * esom::kTcN) *
                                       sizeof(float));
+    if (e == cudaSuccess && L <= esom::kQtabMaxL)
+        e = cudaMalloc(&h->qtab, (size_t)L * L * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->status, 256);
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, 256);
     if (e != cudaSuccess) {
@@ -276,6 +285,7 @@ esom_status esom_set_landmarks(esom_handle h, const float *hi, const float *lo,
     if (e == cudaSuccess) e = esom::launch_landmark_prep(h->hi, h->L, h->d, h->norms,
                                                          reinterpret_cast<float *>(h->status + 1), st,
                                                          esom::kTcN);
+    if (e == cudaSuccess && h->qtab) e = h->ops->launch_qtab(h->hi, h->L, h->qtab, st);
     if (e == cudaSuccess && h->screening) e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, st);
     if (e != cudaSuccess) return cuda_fail(e, "landmark copy");
     ++h->version;
@@ -480,12 +490,22 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
                     smem, optin);
     e = cudaFuncSetAttribute(tc->func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(shared memory)");
-    int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tc->func, esom::kTcThreads, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (bps < 1) return fail(ESOM_EUNSUPPORTED, "tensor-core launch does not fit on an SM");
-    // Each block holds kTcCols of the SM's 512 TMEM columns.
+    // Resident blocks per SM from the kernel's registers (allocated per warp
+    // in units of 256) and shared memory (plus the 1 KiB the driver reserves
+    // per block), at most 512 / kTcCols for the TMEM columns.
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, tc->func);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+    int smem_sm = 0, regs_sm = 0;
+    e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, h->dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(SM resources)");
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+    int bps = regs_sm / (warp_regs * (esom::kTcThreads / 32));
+    const int by_smem = smem_sm / (int)(smem + 1024);
+    if (by_smem < bps) bps = by_smem;
     if (bps * esom::kTcCols > 512) bps = 512 / esom::kTcCols;
+    if (bps < 1) return fail(ESOM_EUNSUPPORTED, "tensor-core launch does not fit on an SM");
     if (!h->img) {
         const size_t bytes = (size_t)((h->L + esom::kTcN - 1) / esom::kTcN) * esom::tc_chunk_bytes(h->d);
         e = cudaMalloc(&h->img, bytes);
@@ -513,6 +533,7 @@ esom_status esom_destroy(esom_handle h) {
     cudaFree(h->norms);
     cudaFree(h->status);
     cudaFree(h->img);
+    cudaFree(h->qtab);
     for (int b = 0; b < 2; ++b) {
         cudaFree(h->stage_x[b]);
         cudaFree(h->stage_out[b]);

@@ -14,6 +14,7 @@ struct esom_ctx {
     float *lo = nullptr;   // L x 2
     float *norms = nullptr; // squared landmark norms, zero-padded to a multiple of kTcN
     int *status = nullptr; // device status word; the float after it: largest norm
+    float *qtab = nullptr; // L x L squared landmark distances (L <= kQtabMaxL)
     uint64_t version = 0;
     const esom::KernelOps *ops = nullptr;
     int num_sms = 0;

@@ -495,13 +495,11 @@ struct PairTerm {
     bool ok;
 };
 
-template <int D, int PASS>
-__device__ __forceinline__ PairTerm pair_term(const float4 (&lu)[D / 4], float2 lut, float lux,
-                                              float luy, float su, float du, int iv, float sv,
-                                              float dv, const float4 *Lg, const float2 *lo2,
-                                              float adjust, float nx, float ny) {
-    const float4 *Lv = Lg + (size_t)iv * (D / 4);
-    const int fv = swz(D, iv);
+// |L_v - L_u|^2 in the FP32 difference form with four partial sums; the
+// table of squared landmark distances (landmark_dist_kernel) holds exactly
+// these values.
+template <int D>
+__device__ __forceinline__ float pair_q(const float4 (&lu)[D / 4], const float4 *Lv, int fv) {
     float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
 #pragma unroll
     for (int e = 0; e < D / 4; ++e) {
@@ -513,7 +511,19 @@ __device__ __forceinline__ PairTerm pair_term(const float4 (&lu)[D / 4], float2 
         q2 = fmaf(ez, ez, q2);
         q3 = fmaf(ew, ew, q3);
     }
-    const float qq = (q0 + q1) + (q2 + q3);
+    return (q0 + q1) + (q2 + q3);
+}
+
+// qrow: row u of the squared-distance table, or null (then q is computed
+// from the rows).
+template <int D, int PASS>
+__device__ __forceinline__ PairTerm pair_term(const float4 (&lu)[D / 4], float2 lut, float lux,
+                                              float luy, float su, float du, int iv, float sv,
+                                              float dv, const float4 *Lg, const float2 *lo2,
+                                              float adjust, float nx, float ny,
+                                              const float *qrow) {
+    const float qq = qrow ? __ldg(qrow + iv)
+                          : pair_q<D>(lu, Lg + (size_t)iv * (D / 4), swz(D, iv));
     const float2 lvt = __ldg(&lo2[iv]);
     const float hx = lvt.x - lut.x, hy = lvt.y - lut.y;
     const float r = fmaf(hx, hx, hy * hy);
@@ -564,18 +574,21 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
                 su = ss[t];
                 du = sd[t];
             }
+        const float *qrow = a.qtab ? a.qtab + (size_t)iu * a.L : nullptr;
         const float4 *Lu = Lg + (size_t)iu * (D / 4);
         const int fu = swz(D, iu);
         float4 lu[D / 4];
 #pragma unroll
-        for (int e = 0; e < D / 4; ++e) lu[e] = Lu[e ^ fu];
+        for (int e = 0; e < D / 4; ++e)
+            lu[e] = qrow ? make_float4(0.f, 0.f, 0.f, 0.f) : Lu[e ^ fu];
         const float2 lut = __ldg(&lo2[iu]);
         const float lux = lut.x - l0.x, luy = lut.y - l0.y;  // l_u relative to l_0
 #pragma unroll
         for (int v0 = 1; v0 < KK; v0 += 2) {
             if (v0 + 1 > u && v0 < m) {
-                const PairTerm c0 = pair_term<D, PASS>(lu, lut, lux, luy, su, du, nb_at<QS>(nb, v0),
-                                                       ss[v0], sd[v0], Lg, lo2, a.adjust, nx, ny);
+                const PairTerm c0 =
+                    pair_term<D, PASS>(lu, lut, lux, luy, su, du, nb_at<QS>(nb, v0), ss[v0],
+                                       sd[v0], Lg, lo2, a.adjust, nx, ny, qrow);
                 const bool k0 = c0.ok && v0 > u;
                 A00 = k0 ? A00 + c0.a00 : A00;
                 A01 = k0 ? A01 + c0.a01 : A01;
@@ -587,7 +600,7 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
                     const int v1 = v0 + 1 < KK ? v0 + 1 : v0;
                     const PairTerm c1 =
                         pair_term<D, PASS>(lu, lut, lux, luy, su, du, nb_at<QS>(nb, v1), ss[v1],
-                                           sd[v1], Lg, lo2, a.adjust, nx, ny);
+                                           sd[v1], Lg, lo2, a.adjust, nx, ny, qrow);
                     const bool k1 = c1.ok && v1 < m;
                     A00 = k1 ? A00 + c1.a00 : A00;
                     A01 = k1 ? A01 + c1.a01 : A01;
@@ -1226,6 +1239,30 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchArgs B
     }
 }
 
+// One thread per ordered pair (u, v): the squared distance table of the pair
+// loop, computed by the loop's own pair_q.
+template <int D>
+__global__ void landmark_dist_kernel(const float *__restrict__ hi, int L,
+                                     float *__restrict__ qtab) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)L * L) return;
+    const int u = (int)(t / L), v = (int)(t - (long long)u * L);
+    const float4 *Lg = reinterpret_cast<const float4 *>(hi);
+    const float4 *Lu = Lg + (size_t)u * (D / 4);
+    const int fu = swz(D, u);
+    float4 lu[D / 4];
+#pragma unroll
+    for (int e = 0; e < D / 4; ++e) lu[e] = __ldg(Lu + (e ^ fu));
+    qtab[t] = pair_q<D>(lu, Lg + (size_t)v * (D / 4), swz(D, v));
+}
+
+template <int D>
+cudaError_t launch_qtab(const float *hi, int L, float *qtab, cudaStream_t stream) {
+    const long long pairs = (long long)L * L;
+    landmark_dist_kernel<D><<<(unsigned)((pairs + 255) / 256), 256, 0, stream>>>(hi, L, qtab);
+    return cudaGetLastError();
+}
+
 template <int D, int KC, int MINB>
 cudaError_t launch_batch(const BatchArgs &b, int grid, size_t smem, cudaStream_t stream) {
     batch_kernel<D, KC, MINB><<<grid, kThreads, smem, stream>>>(b);
@@ -1251,7 +1288,7 @@ const KernelOps Instance<D, KC>::ops = {
     reinterpret_cast<const void *>(&fused_kernel<D, KC, Instance<D, KC>::kMinBlocks>), KC,
     &launch_fused<D, KC, Instance<D, KC>::kMinBlocks>,
     reinterpret_cast<const void *>(&batch_kernel<D, KC, Instance<D, KC>::kMinBlocks>),
-    &launch_batch<D, KC, Instance<D, KC>::kMinBlocks>};
+    &launch_batch<D, KC, Instance<D, KC>::kMinBlocks>, &launch_qtab<D>};
 
 // Table of the list capacities instantiated for each D.
 #define ESOM_DEFINE_D(DV)                                            \

@@ -39,6 +39,7 @@ struct FusedArgs {
     int *status;          // device status words: [0] error bits, [2] rescan count
     const unsigned char *img;  // tensor-core screening: landmark chunk images
     int tc_chunks;        // ceil(L / kTcN) chunks in img
+    const float *qtab;    // L x L squared landmark distances (pair_q values), or null
 };
 
 // Many datasets of one (D, list capacity) in one launch: every block walks a
@@ -59,10 +60,19 @@ struct KernelOps {
     cudaError_t (*launch)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
     const void *batch_func;
     cudaError_t (*launch_batch)(const BatchArgs &, int grid, size_t smem, cudaStream_t);
+    // Fills qtab[u * L + v] = |L_v - L_u|^2 from the (chunk-swizzled) rows
+    // of hi with the pair loop's own arithmetic (pair_q), so the table holds
+    // exactly the values the loop would compute.
+    cudaError_t (*launch_qtab)(const float *hi, int L, float *qtab, cudaStream_t);
 };
 
 // Returns the instantiation for dimension D and list capacity kc, or nullptr.
 const KernelOps *kernel_ops(int D, int kc);
+
+// Largest L for which a handle keeps the L x L table of squared landmark
+// distances (64 MiB at 4096); above it the pair loop computes them.
+constexpr int kQtabMaxL = 4096;
+
 
 // ---------------------------------------------------------------------------
 // Tensor-core screening (tcgen05, TF32): tiles of kTcRows points (the MMA's M
@@ -75,15 +85,18 @@ constexpr int kTcThreads = 160;
 constexpr int kTcCols = 2 * kTcN;  // TMEM columns: two accumulator buffers
 
 // 128-byte column blocks of a row (32 TF32 values each), pipeline stages of
-// the landmark ring, and resident blocks per SM the launch aims for (three
-// where the registers of the projection fit in 128 a thread, else two).
+// the landmark ring, and resident blocks per SM the launch aims for (shared
+// memory admits two).
 __host__ __device__ constexpr int tc_nblk(int D) { return (D + 31) / 32; }
 __host__ __device__ constexpr int tc_stages(int D) { return tc_nblk(D) == 1 ? 3 : 2; }
-__host__ __device__ constexpr int tc_minb(int D, int KC) { return D <= 16 && KC <= 24 ? 3 : 2; }
+__host__ __device__ constexpr int tc_minb(int, int) { return 2; }
 
-// Bytes of one chunk image: kTcN rows x 128 bytes per column block, rows in
-// the 128-byte-swizzled K-major order the MMA reads (see tc_image_offset).
-__host__ __device__ inline size_t tc_chunk_bytes(int D) { return (size_t)kTcN * 128 * tc_nblk(D); }
+// Bytes of one chunk image: the high TF32 parts of kTcN rows, then the low
+// parts, each kTcN rows x 128 bytes per column block, rows in the
+// 128-byte-swizzled K-major order the MMA reads (see tc_image_offset).
+__host__ __device__ inline size_t tc_chunk_bytes(int D) {
+    return (size_t)2 * kTcN * 128 * tc_nblk(D);
+}
 
 // Byte offset of 16-byte piece c (values 4c..4c+3 of column block blk) of
 // row r inside a 1024-byte-aligned operand of `rows` rows: 8-row groups of
@@ -95,8 +108,8 @@ __host__ __device__ inline unsigned tc_image_offset(int rows, int r, int blk, in
 inline size_t tc_smem_bytes(int D) {
     const size_t nb = (size_t)tc_nblk(D);
     return 1024                                  // alignment slack
-           + 2 * (size_t)kTcRows * 128 * nb      // point tiles (double buffered)
-           + (size_t)tc_stages(D) * kTcN * 128 * nb  // landmark chunk ring
+           + 2 * (size_t)kTcRows * 128 * nb      // point tile (high and low parts)
+           + (size_t)tc_stages(D) * tc_chunk_bytes(D)  // landmark chunk ring
            + (size_t)kQueue * kTcRows * 4        // candidate queue
            + 256;                                // barriers, TMEM address, flags
 }

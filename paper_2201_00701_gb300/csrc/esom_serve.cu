@@ -137,7 +137,8 @@ struct Session {
     size_t bytes = 0;
     std::deque<Frame> queue;
     bool inflight = false;
-    Frame current{};
+    std::vector<Frame> current;  // frames the work in flight completes
+    std::deque<esom_frame_done> finished;  // completed, not yet reported
     uint64_t submitted = 0, completed = 0;
 };
 
@@ -146,6 +147,8 @@ struct Session {
 struct esom_server_ctx {
     uint64_t budget = 0, used = 0;
     int max_inflight = 1, inflight = 0, dev = 0;
+    int coalesce = 0;  // run a session's queued frames' SOM steps, then one projection
+    int screening = ESOM_SCREEN_FP32;  // screening mode of the sessions' handles
     std::vector<Session *> sessions;
     cudaEvent_t ref = nullptr;
     std::chrono::steady_clock::time_point t0;
@@ -159,8 +162,9 @@ double host_now(const esom_server_ctx *s) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
 }
 
-// Enqueues one frame of session ss on its stream.
-esom_status launch_frame(esom_server_ctx *s, Session &ss, const Frame &f) {
+// One SOM step of frame f of session ss on its stream: k-NN of the frame's
+// minibatch window, the update, the landmark refresh.
+esom_status som_frame_step(Session &ss, const Frame &f) {
     const esom_session_desc &d = ss.desc;
     cudaStream_t st = ss.stream;
     const esom_stream_t est = reinterpret_cast<esom_stream_t>(st);
@@ -177,12 +181,27 @@ esom_status launch_frame(esom_server_ctx *s, Session &ss, const Frame &f) {
         r = esom_set_landmarks(ss.h, ss.hi, ss.lo, est);
         if (r != ESOM_OK) return r;
     }
-    r = esom_project(ss.h, ss.points, d.n, ss.out, d.boost, d.adjust, est);
+    return ESOM_OK;
+}
+
+// Enqueues the queue's front frame of session ss -- or, when the server
+// coalesces, every queued frame: their SOM steps in order, then one
+// projection, which all of them complete with -- and the completion event.
+esom_status launch_frames(esom_server_ctx *s, Session &ss) {
+    const esom_session_desc &d = ss.desc;
+    ss.current.clear();
+    do {
+        ss.current.push_back(ss.queue.front());
+        ss.queue.pop_front();
+        esom_status r = som_frame_step(ss, ss.current.back());
+        if (r != ESOM_OK) return r;
+    } while (s->coalesce && !ss.queue.empty());
+    esom_status r = esom_project(ss.h, ss.points, d.n, ss.out, d.boost, d.adjust,
+                                 reinterpret_cast<esom_stream_t>(ss.stream));
     if (r != ESOM_OK) return r;
-    const cudaError_t e = cudaEventRecord(ss.done, st);
+    const cudaError_t e = cudaEventRecord(ss.done, ss.stream);
     if (e != cudaSuccess) return scuda(e, "frame event");
     ss.inflight = true;
-    ss.current = f;
     ++s->inflight;
     return ESOM_OK;
 }
@@ -196,9 +215,7 @@ esom_status fill_slots(esom_server_ctx *s) {
                 (!best || ss->queue.front().arrival < best->queue.front().arrival))
                 best = ss;
         if (!best) break;
-        const Frame f = best->queue.front();
-        best->queue.pop_front();
-        esom_status r = launch_frame(s, *best, f);
+        esom_status r = launch_frames(s, *best);
         if (r != ESOM_OK) return r;
     }
     return ESOM_OK;
@@ -261,6 +278,23 @@ esom_status esom_server_create(uint64_t budget_bytes, int max_inflight, esom_ser
 
 double esom_server_now(esom_server s) { return s ? host_now(s) : 0.0; }
 
+esom_status esom_server_set_screening(esom_server s, int mode) {
+    if (!s) return sfail(ESOM_EINVAL, "null server");
+    if (mode != ESOM_SCREEN_FP32 && mode != ESOM_SCREEN_TF32)
+        return sfail(ESOM_EINVAL, "unknown screening mode");
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (!s->sessions.empty()) return sfail(ESOM_EINVAL, "set the screening mode before adding sessions");
+    s->screening = mode;
+    return ESOM_OK;
+}
+
+esom_status esom_server_set_coalescing(esom_server s, int on) {
+    if (!s) return sfail(ESOM_EINVAL, "null server");
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->coalesce = on ? 1 : 0;
+    return ESOM_OK;
+}
+
 esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc,
                                     const float *points, const float *hi, const float *lo,
                                     int *session) {
@@ -271,9 +305,15 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
         return sfail(ESOM_EINVAL, "session description");
     std::lock_guard<std::mutex> lock(s->mu);
     // resident points and output, the session's landmark copy and the
-    // handle's (rows, 2-D positions, norms), the minibatch k-NN indices
+    // handle's (rows, 2-D positions, norms, squared-distance table), the
+    // minibatch k-NN indices
+    const size_t qtab = d.L <= esom::kQtabMaxL ? (size_t)d.L * d.L * 4 : 0;
+    const size_t img = s->screening == ESOM_SCREEN_TF32
+                           ? (size_t)((d.L + esom::kTcN - 1) / esom::kTcN) * esom::tc_chunk_bytes(d.d)
+                           : 0;
     const size_t bytes = (size_t)d.n * d.d * 4 + (size_t)d.n * 8 + (size_t)d.L * (d.d + 2) * 4 * 2 +
-                         (size_t)((d.L + 3) & ~3) * 4 + (size_t)d.minibatch * d.k * 4 + 4096;
+                         (size_t)((d.L + 63) & ~63) * 4 + qtab + img +
+                         (size_t)d.minibatch * d.k * 4 + 4096;
     if (s->used + bytes > s->budget)
         return sfail(ESOM_ENOMEM, "session refused: device memory budget exceeded");
     Session *ss = new (std::nothrow) Session;
@@ -281,6 +321,8 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
     ss->desc = d;
     ss->bytes = bytes;
     esom_status r = esom_create(d.d, d.L, d.k, &ss->h);
+    if (r == ESOM_OK && s->screening != ESOM_SCREEN_FP32)
+        r = esom_set_screening(ss->h, s->screening, nullptr);
     cudaError_t e = cudaSuccess;
     if (r == ESOM_OK) {
         e = cudaMalloc(&ss->points, (size_t)d.n * d.d * 4);
@@ -335,19 +377,27 @@ esom_status esom_server_poll(esom_server s, int wait_all, esom_frame_done *done,
             float ms = 0.f;
             cudaError_t e = cudaEventElapsedTime(&ms, s->ref, ss->done);
             if (e != cudaSuccess) return scuda(e, "frame timing");
-            if (*count < max) {
-                esom_frame_done &o = done[(*count)++];
+            for (const Frame &f : ss->current) {
+                esom_frame_done o;
                 o.session = (int)i;
-                o.frame = ss->current.id;
-                o.arrival = ss->current.arrival;
+                o.frame = f.id;
+                o.arrival = f.arrival;
                 o.completion = s->ref_host + ms / 1e3;
+                ss->finished.push_back(o);
             }
+            ss->completed += ss->current.size();
+            ss->current.clear();
             ss->inflight = false;
-            ++ss->completed;
             --s->inflight;
         }
         esom_status r = fill_slots(s);
         if (r != ESOM_OK) return r;
+        // report completed frames, oldest completion first within a session
+        for (Session *ss : s->sessions)
+            while (ss && !ss->finished.empty() && *count < max) {
+                done[(*count)++] = ss->finished.front();
+                ss->finished.pop_front();
+            }
         bool pending = s->inflight > 0;
         for (Session *ss : s->sessions)
             if (ss && !ss->queue.empty()) pending = true;

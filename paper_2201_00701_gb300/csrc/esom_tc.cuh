@@ -11,7 +11,13 @@
 //                                  memory in the 128-byte-swizzled K-major
 //                                  layout)
 //   v_j = |L_j|^2 - 2 T_j         (screening value = |X - L_j|^2 - |X|^2,
-//                                  up to the TF32 error)
+//                                  up to the screening error)
+//
+// Each operand is split into two TF32 parts, x = x_hi + x_lo (x_hi the TF32
+// rounding of x, x_lo that of the remainder), and T accumulates the three
+// products x_hi l_hi + x_lo l_hi + x_hi l_lo: the dropped terms are below
+// 2^-21 relative, so the screening error is of the order of an FP32 dot
+// product's and the certificate almost never fails.
 //
 // Each selection thread owns one point (one TMEM lane), reads its 64 values
 // of a chunk with one tcgen05.ld, keys them like the plain kernel (value with
@@ -26,9 +32,11 @@
 // is the producer: one lane streams the landmark chunk images through a ring
 // of shared-memory stages by bulk copies (cp.async.bulk + mbarrier) and
 // issues the MMAs into two TMEM accumulator buffers, so the MMA of chunk c+1
-// overlaps the selection of chunk c.  The selection threads write their
-// next tile's operand (TF32-rounded rows) before they re-rank and project
-// the current one, so the next tile's MMAs overlap the projection.  Every
+// overlaps the selection of chunk c.  As soon as a tile's last chunk has
+// been read (every MMA of the tile is then complete), the selection threads
+// write the next tile's operand (split rows) into the one point buffer and
+// only then re-rank and project the current tile, so the next tile's MMAs
+// overlap that work.  Every
 // wait is bounded; on a timeout the block raises the status word, drains
 // its own copies and MMAs and frees its tensor memory.
 #pragma once
@@ -145,14 +153,16 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
-// Bound on the TF32 part of the screening error per unit |X| max|L|: both
-// operands rounded to 11 significant bits (relative 2^-11 each, so 2^-10 on
-// a product), accumulation of D exact products with at most D + 1 FP32
-// roundings (2^-23 each, relative to the sum of |products|); twice that in
+// Bound on the tensor-core part of the screening error per unit |X| max|L|.
+// With x_hi = tf32(x), x_lo = tf32(x - x_hi): |x - x_hi| <= 2^-11 |x| and
+// |x - x_hi - x_lo| <= 2^-22 |x|, so the dropped terms x_lo l_lo and the two
+// remainders are <= 3 2^-22 |x_i||l_i| per coordinate; the 3D products are
+// exact in FP32 and accumulated with at most 3D + 1 roundings (2^-23 each,
+// relative to the sum of |products| <= |x||l|).  Twice that in
 // v_j = |L_j|^2 - 2 T_j, and a factor 2 of margin.
 template <int D>
 __device__ __forceinline__ float tc_dot_bound() {
-    return 4.f * (9.765625e-4f + (float)(D + 1) * 1.1920929e-7f);
+    return 4.f * (3.f * 2.3841858e-7f + (float)(3 * D + 1) * 1.1920929e-7f);
 }
 
 // ---------------------------------------------------------------------------
@@ -166,21 +176,22 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
     constexpr int NB = tc_nblk(D);
     constexpr int S = tc_stages(D);
     constexpr int KS = (D + 7) / 8;  // MMA K steps of 8 TF32 values (32 bytes)
-    constexpr uint32_t kABytes = kTcRows * 128 * NB;
-    constexpr uint32_t kBBytes = kTcN * 128 * NB;
+    constexpr uint32_t kAPart = kTcRows * 128 * NB;  // x_hi (then x_lo) of a tile
+    constexpr uint32_t kBPart = kTcN * 128 * NB;     // l_hi (then l_lo) of a chunk
+    constexpr uint32_t kBBytes = 2 * kBPart;
     constexpr uint32_t kIdesc = tc_idesc();
     constexpr int QS = kTcRows;  // queue stride: one column per selection thread
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-    unsigned char *sA = base;                      // 2 point tiles
-    unsigned char *sB = base + 2 * kABytes;        // S landmark chunk stages
+    unsigned char *sA = base;                      // point tile: x_hi, x_lo
+    unsigned char *sB = base + 2 * kAPart;         // S landmark chunk stages
     uint32_t *qk = reinterpret_cast<uint32_t *>(sB + S * kBBytes);
     uint64_t *bars = reinterpret_cast<uint64_t *>(qk + kQueue * kTcRows);
     uint64_t *l_full = bars, *l_empty = bars + S;
     uint64_t *t_full = bars + 2 * S, *t_empty = bars + 2 * S + 2;
-    uint64_t *a_ready = bars + 2 * S + 4, *done_bar = bars + 2 * S + 6;
+    uint64_t *a_ready = bars + 2 * S + 4, *done_bar = bars + 2 * S + 5;
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bars + 2 * S + 8);
     volatile int *s_abort = reinterpret_cast<volatile int *>(s_tmem + 1);
 
@@ -201,8 +212,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         mbar_init(&t_full[1], 1);
         mbar_init(&t_empty[0], 4);
         mbar_init(&t_empty[1], 4);
-        mbar_init(&a_ready[0], 4);
-        mbar_init(&a_ready[1], 4);
+        mbar_init(a_ready, 4);
         mbar_init(done_bar, 1);
         fence_mbar_init();
         *s_abort = 0;
@@ -237,13 +247,12 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
             for (; issued < total && issued < S; ++issued) issue(issued);
             bool ok = true;
             long long g = 0;
+            const uint32_t ahi = smem_u32(sA), alo = ahi + kAPart;
             for (long long i = 0; i < my_tiles && ok; ++i) {
-                const int buf = (int)(i & 1);
-                if (!mbar_wait(&a_ready[buf], (uint32_t)((i >> 1) & 1))) {
+                if (!mbar_wait(a_ready, (uint32_t)(i & 1))) {
                     ok = false;
                     break;
                 }
-                const uint32_t aaddr = smem_u32(sA + (size_t)buf * kABytes);
                 for (int c = 0; c < nch; ++c, ++g) {
                     const int s = (int)(g % S), tb = (int)(g & 1);
                     if (*s_abort || !mbar_wait(&l_full[s], (uint32_t)((g / S) & 1))) {
@@ -256,13 +265,16 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t baddr = smem_u32(sB + (size_t)s * kBBytes);
+                    const uint32_t bhi = smem_u32(sB + (size_t)s * kBBytes), blo = bhi + kBPart;
+                    const uint32_t dt = tmem + (uint32_t)(tb * kTcN);
 #pragma unroll
                     for (int ks = 0; ks < KS; ++ks) {
                         const uint32_t ka = (uint32_t)((ks >> 2) * kTcRows * 128 + (ks & 3) * 32);
                         const uint32_t kb = (uint32_t)((ks >> 2) * kTcN * 128 + (ks & 3) * 32);
-                        mma_tf32(tmem + (uint32_t)(tb * kTcN), sw128_desc(aaddr + ka),
-                                 sw128_desc(baddr + kb), kIdesc, ks > 0 ? 1u : 0u);
+                        mma_tf32(dt, sw128_desc(ahi + ka), sw128_desc(bhi + kb), kIdesc,
+                                 ks > 0 ? 1u : 0u);
+                        mma_tf32(dt, sw128_desc(alo + ka), sw128_desc(bhi + kb), kIdesc, 1u);
+                        mma_tf32(dt, sw128_desc(ahi + ka), sw128_desc(blo + kb), kIdesc, 1u);
                     }
                     mma_commit(&t_full[tb]);
                     mma_commit(&l_empty[s]);
@@ -297,39 +309,44 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         const uint32_t my_lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         constexpr float kGamma = (2.25f * D + 10.f) * kU * 1.25f;
 
-        // Writes this thread's row of tile `tile` (TF32, swizzled) into
-        // point buffer `buf` and returns |x|^2 (FP32, exact row).
-        auto write_tile = [&](long long tile, int buf) -> float {
+        // Writes this thread's row of tile `tile`, split into TF32 parts
+        // (swizzled), into the point buffer and returns |x|^2 (FP32, exact
+        // row).
+        auto write_tile = [&](long long tile) -> float {
             const long long row = tile * kTcRows + tid;
             const bool act = row < a.n;
             const float4 *xp = reinterpret_cast<const float4 *>(a.X) + (act ? row : 0) * (D / 4);
-            unsigned char *A = sA + (size_t)buf * kABytes;
             float xx = 0.f;
 #pragma unroll
             for (int blk = 0; blk < NB; ++blk)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int e = blk * 8 + c;  // float4 index of the row
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
                     if (e < D / 4 && act) {
-                        v = __ldg(xp + e);
+                        const float4 v = __ldg(xp + e);
                         xx = fmaf(v.x, v.x, xx);
                         xx = fmaf(v.y, v.y, xx);
                         xx = fmaf(v.z, v.z, xx);
                         xx = fmaf(v.w, v.w, xx);
-                        v = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
+                        h = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
+                        l = make_float4(to_tf32(v.x - h.x), to_tf32(v.y - h.y), to_tf32(v.z - h.z),
+                                        to_tf32(v.w - h.w));
                     }
-                    if (e < 2 * KS)  // pieces the MMA K steps read
-                        *reinterpret_cast<float4 *>(A + tc_image_offset(kTcRows, tid, blk, c)) = v;
+                    if (e < 2 * KS) {  // pieces the MMA K steps read
+                        const unsigned off = tc_image_offset(kTcRows, tid, blk, c);
+                        *reinterpret_cast<float4 *>(sA + off) = h;
+                        *reinterpret_cast<float4 *>(sA + kAPart + off) = l;
+                    }
                 }
             fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&a_ready[buf]);
+            if (lane == 0) mbar_arrive(a_ready);
             return xx;
         };
 
         bool ok = true;
-        float xx_next = write_tile(first, 0);
+        float xx_next = write_tile(first);
         long long g = 0;
         long long tile = first;
         for (long long i = 0; i < my_tiles && ok; ++i, tile += gridDim.x) {
@@ -399,11 +416,11 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                 }
             }
             if (!ok) break;
+            // Every MMA of this tile has completed (its last chunk has been
+            // read): the next tile's operand replaces this one's, so that its
+            // MMAs run while this tile is re-ranked and projected.
+            if (i + 1 < my_tiles) xx_next = write_tile(tile + gridDim.x);
             queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
-
-            // The next tile's operand, so that its MMAs run while this tile
-            // is re-ranked and projected.
-            if (i + 1 < my_tiles) xx_next = write_tile(tile + gridDim.x, (int)((i + 1) & 1));
 
             // Step 1b: exact re-rank of the list, certificate, rare rescan.
             float4 xr[D / 4];

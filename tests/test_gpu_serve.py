@@ -266,3 +266,54 @@ def test_fifo_start_order(esom):
         recs = srv.poll(wait_all=True)
     order = [r[0] for r in sorted(recs, key=lambda r: r[3])]
     assert order == [sids[0], sids[2], sids[1]]
+
+
+def test_coalesced_frames_equal_strict(esom):
+    """Coalescing runs queued frames' SOM steps in order and projects once:
+    the final output equals frame-by-frame serving bit for bit, and every
+    frame is reported, in order."""
+    ps = workloads.serve8(n_scale=0.02)[:2]
+    arrs = [_session_arrays(p) for p in ps]
+    frames = 6
+    outs = []
+    for coalesce in (False, True):
+        with esom.Server(1 << 30, 1) as srv:
+            srv.set_coalescing(coalesce)
+            sids = []
+            for (w, X, h, l), p in zip(arrs, ps):
+                sids.append(srv.add_session(X, h, l, w.k, w.boost, w.adjust, p["alpha"],
+                                            p["sigma"], minibatch=p["minibatch"], seed=p["seed"]))
+            for f in range(frames):
+                for s in sids:
+                    srv.submit(s)
+            recs = srv.poll(wait_all=True)
+            outs.append([srv.output(s) for s in sids])
+            for s in sids:
+                own = [r for r in recs if r[0] == s]
+                assert [r[1] for r in own] == list(range(frames))
+            if coalesce:
+                # frames queued behind the first were started together
+                comp = sorted({round(r[3], 9) for r in recs if r[0] == sids[0]})
+                assert len(comp) < frames
+    for (a, fa), (b, fb) in zip(outs[0], outs[1]):
+        assert fa == fb == frames
+        assert torch.equal(a, b)
+
+
+def test_server_tf32_sessions_equal_fp32(esom):
+    """Sessions whose handles screen on the tensor cores give the same bits."""
+    p = workloads.serve8(n_scale=0.01)[3]
+    w, X, h, l = _session_arrays(p)
+    outs = []
+    for mode in (esom.ESOM_SCREEN_FP32, esom.ESOM_SCREEN_TF32):
+        with esom.Server(1 << 30, 2) as srv:
+            srv.set_screening(mode)
+            s = srv.add_session(X, h, l, w.k, w.boost, w.adjust, p["alpha"], p["sigma"],
+                                minibatch=p["minibatch"], seed=p["seed"])
+            for _ in range(3):
+                srv.submit(s)
+            srv.poll(wait_all=True)
+            outs.append(srv.output(s)[0])
+            with pytest.raises(esom.EsomError):
+                srv.set_screening(esom.ESOM_SCREEN_FP32)  # sessions exist already
+    assert torch.equal(outs[0], outs[1])
