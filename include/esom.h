@@ -166,9 +166,14 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg);
  * among the k nearest (a point that fails is rescanned exactly; see
  * esom_get_stats), so both modes return the same neighbours, distances and
  * coordinates, bit for bit; the mode only changes speed.
- * Switching to TF32 allocates the landmark images (2 * ceil(L/64) * 64 * 128
- * * ceil(d/32) bytes, kept until esom_destroy) and, if landmarks are set,
- * builds them on `stream`; later esom_set_landmarks calls rebuild them.
+ * With TF32, esom_project runs the tensor-core k-NN kernel and then a
+ * projection kernel over passes of 2^19 points, exchanging the neighbours
+ * through a scratch buffer of the handle (2^19 * k * 8 bytes): projections
+ * of one handle on different streams must then not overlap.
+ * Switching to TF32 allocates the landmark images (2 * ceil(L/64) * 64 *
+ * row bytes, row bytes = 64 for d <= 16, else 128 * ceil(d/32)) and the
+ * scratch, kept until esom_destroy, and, if landmarks are set, builds the
+ * images on `stream`; later esom_set_landmarks calls rebuild them.
  * Errors: ESOM_EINVAL (unknown mode), ESOM_EUNSUPPORTED (device is not
  * sm_103, or no kernel for this d and k), ESOM_ENOMEM, ESOM_ECUDA.
  * esom_batch_* and esom_project_noalloc always screen in FP32. */

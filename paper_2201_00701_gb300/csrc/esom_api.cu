@@ -57,7 +57,10 @@ void fill_args(const esom_ctx *h, const float *points, long long n, float *out, 
     a->ntiles = (n + kThreads - 1) / kThreads;
     a->status = h->status;
     a->img = h->img;
-    a->qtab = h->qtab;
+    // The pair loop reads the distance table when its landmark rows are not
+    // in shared memory (streamed chunks); with resident rows recomputing from
+    // shared memory is faster than the L2 gathers.
+    a->qtab = h->nchunks > 1 ? h->qtab : nullptr;
     a->tc_chunks = (h->L + kTcN - 1) / kTcN;
 }
 
@@ -104,10 +107,10 @@ cudaError_t launch_landmark_prep(float *hi, int L, int D, float *norms, float *l
 }
 
 // One thread per 16-byte piece of a chunk image: piece c of column block blk
-// of landmark j holds values 4e..4e+3 (e = 8 blk + c) of the row split into
-// TF32 parts -- hi = tf32(v) in the first half of the image, lo = tf32(v -
-// hi) in the second (nearest, ties away) -- zero beyond d and for rows
-// beyond L.  The rows of hi are chunk-swizzled (logical chunk e at
+// of landmark j holds values 4e..4e+3 (e = blk * pieces + c) of the row
+// split into TF32 parts -- hi = tf32(v) in the first half of the image,
+// lo = tf32(v - hi) in the second (nearest, ties away) -- zero beyond d and
+// for rows beyond L.  The rows of hi are chunk-swizzled (logical chunk e at
 // e ^ swz(D, j)).
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
@@ -117,13 +120,13 @@ __device__ __forceinline__ float tf32_rna(float x) {
 
 __global__ void tc_image_kernel(const float *__restrict__ hi, int L, int D,
                                 unsigned char *__restrict__ img, int Lpad) {
-    const int nb = tc_nblk(D);
+    const int nb = tc_nblk(D), ppb = tc_row_bytes(D) / 16;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)Lpad * nb * 8) return;
-    const int c = (int)(t & 7);
-    const int blk = (int)((t >> 3) % nb);
-    const int j = (int)((t >> 3) / nb);
-    const int e = blk * 8 + c;
+    if (t >= (long long)Lpad * nb * ppb) return;
+    const int c = (int)(t % ppb);
+    const int blk = (int)((t / ppb) % nb);
+    const int j = (int)(t / ppb / nb);
+    const int e = blk * ppb + c;
     float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
     if (j < L && e < D / 4) {
         const float4 v = reinterpret_cast<const float4 *>(hi + (size_t)j * D)[e ^ swz(D, j)];
@@ -132,7 +135,7 @@ __global__ void tc_image_kernel(const float *__restrict__ hi, int L, int D,
                         tf32_rna(v.w - h.w));
     }
     unsigned char *chunk = img + (size_t)(j / kTcN) * tc_chunk_bytes(D);
-    const unsigned off = tc_image_offset(kTcN, j % kTcN, blk, c);
+    const unsigned off = tc_image_offset(D, kTcN, j % kTcN, blk, c);
     *reinterpret_cast<float4 *>(chunk + off) = h;
     *reinterpret_cast<float4 *>(chunk + tc_chunk_bytes(D) / 2 + off) = l;
 }
@@ -140,7 +143,7 @@ __global__ void tc_image_kernel(const float *__restrict__ hi, int L, int D,
 cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img,
                             cudaStream_t stream) {
     const int Lpad = (L + kTcN - 1) / kTcN * kTcN;
-    const long long threads = (long long)Lpad * tc_nblk(D) * 8;
+    const long long threads = (long long)Lpad * tc_nblk(D) * (tc_row_bytes(D) / 16);
     tc_image_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(hi, L, D, img, Lpad);
     return cudaGetLastError();
 }
@@ -193,12 +196,44 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
     a.idx = idx;
     a.dist2 = dist2;
     a.mode = mode;
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     if (h->screening) {
-        const long long tiles = (n + esom::kTcRows - 1) / esom::kTcRows;
-        long long grid = (long long)h->tc_blocks_per_sm * h->num_sms;
-        if (grid > tiles) grid = tiles;
-        e = h->tc->launch(a, (int)grid, h->tc_smem, stream);
+        // Tensor-core k-NN; for a projection, in passes of kTcPass points
+        // through the handle's neighbour scratch, each followed by the
+        // projection kernel.
+        auto knn = [&](FusedArgs k, long long cnt) -> cudaError_t {
+            const long long tiles = (cnt + esom::kTcRows - 1) / esom::kTcRows;
+            long long grid = (long long)h->tc_blocks_per_sm * h->num_sms;
+            if (grid > tiles) grid = tiles;
+            k.mode = esom::kKnn;
+            return h->tc->launch(k, (int)grid, h->tc_smem, stream);
+        };
+        if (mode == esom::kKnn) {
+            e = knn(a, n);
+        } else {
+            for (long long off = 0; off < n && e == cudaSuccess; off += esom::kTcPass) {
+                const long long cnt = n - off < esom::kTcPass ? n - off : esom::kTcPass;
+                FusedArgs k = a;
+                k.X = points + off * h->d;
+                k.n = cnt;
+                k.idx = h->tc_idx;
+                k.dist2 = h->tc_d2;
+                e = knn(k, cnt);
+                if (e != cudaSuccess) break;
+                FusedArgs p = k;
+                p.out = out + off * 2;
+                p.mode = esom::kProject;
+                // rows resident when they fit the configured shared memory
+                const bool res = h->nchunks == 1 &&
+                                 esom::project_smem_bytes(h->d, h->L, true) <= h->proj_smem;
+                p.nchunks = res ? 1 : 2;
+                p.qtab = res ? nullptr : h->qtab;
+                p.ntiles = (cnt + esom::kThreads - 1) / esom::kThreads;
+                long long grid = (long long)h->proj_blocks_per_sm * h->num_sms;
+                if (grid > p.ntiles) grid = p.ntiles;
+                e = h->ops->launch_proj(p, (int)grid, h->proj_smem, stream);
+            }
+        }
     } else {
         long long grid = (long long)h->blocks_per_sm * h->num_sms;
         if (grid > a.ntiles) grid = a.ntiles;
@@ -453,6 +488,8 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg) {
     cfg->shared_bytes = (int)h->smem;
     cfg->screening = h->screening;
     if (h->screening) {
+        // the tensor-core k-NN kernel (the projection kernel that follows it
+        // uses 256 threads and the landmark rows of the plain kernel)
         cfg->threads_per_block = esom::kTcThreads;
         cfg->blocks_per_sm = h->tc_blocks_per_sm;
         cfg->landmark_chunk = esom::kTcN;
@@ -506,11 +543,29 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
     if (by_smem < bps) bps = by_smem;
     if (bps * esom::kTcCols > 512) bps = 512 / esom::kTcCols;
     if (bps < 1) return fail(ESOM_EUNSUPPORTED, "tensor-core launch does not fit on an SM");
+    // the projection kernel that follows each k-NN pass
+    const bool resident = h->nchunks == 1;
+    const size_t psmem = esom::project_smem_bytes(h->d, h->L, resident);
+    if (psmem > (size_t)optin)
+        return fail(ESOM_EUNSUPPORTED, "projection needs %zu bytes of shared memory", psmem);
+    e = cudaFuncSetAttribute(h->ops->proj_func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(projection shared memory)");
+    int pbps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pbps, h->ops->proj_func, esom::kThreads, psmem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (pbps < 1) return fail(ESOM_EUNSUPPORTED, "projection launch does not fit on an SM");
     if (!h->img) {
         const size_t bytes = (size_t)((h->L + esom::kTcN - 1) / esom::kTcN) * esom::tc_chunk_bytes(h->d);
         e = cudaMalloc(&h->img, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&h->tc_idx, (size_t)esom::kTcPass * h->k * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&h->tc_d2, (size_t)esom::kTcPass * h->k * sizeof(float));
         if (e != cudaSuccess) {
+            cudaFree(h->img);
+            cudaFree(h->tc_idx);
+            cudaFree(h->tc_d2);
             h->img = nullptr;
+            h->tc_idx = nullptr;
+            h->tc_d2 = nullptr;
             return fail(ESOM_ENOMEM, "device allocation of the landmark images: %s",
                         cudaGetErrorString(e));
         }
@@ -522,6 +577,8 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
     h->tc = tc;
     h->tc_smem = smem;
     h->tc_blocks_per_sm = bps;
+    h->proj_smem = psmem;
+    h->proj_blocks_per_sm = pbps;
     h->screening = mode;
     return ESOM_OK;
 }
@@ -534,6 +591,8 @@ esom_status esom_destroy(esom_handle h) {
     cudaFree(h->status);
     cudaFree(h->img);
     cudaFree(h->qtab);
+    cudaFree(h->tc_idx);
+    cudaFree(h->tc_d2);
     for (int b = 0; b < 2; ++b) {
         cudaFree(h->stage_x[b]);
         cudaFree(h->stage_out[b]);

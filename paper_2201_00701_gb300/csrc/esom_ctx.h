@@ -30,6 +30,11 @@ struct esom_ctx {
     unsigned char *img = nullptr;
     int tc_blocks_per_sm = 0;
     size_t tc_smem = 0;
+    // neighbours of one k-NN pass (kTcPass x k) for the projection kernel
+    int *tc_idx = nullptr;
+    float *tc_d2 = nullptr;
+    int proj_blocks_per_sm = 0;
+    size_t proj_smem = 0;
     // host-buffer pipeline state (created on first use)
     float *stage_x[2] = {nullptr, nullptr};
     float *stage_out[2] = {nullptr, nullptr};

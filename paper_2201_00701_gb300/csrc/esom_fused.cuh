@@ -1239,6 +1239,74 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchArgs B
     }
 }
 
+// ---------------------------------------------------------------------------
+// Steps 2-4 from given neighbours: one thread per point reads its k indices
+// and exact squared distances (ascending, as a k-NN kernel wrote them) and
+// runs the fused kernel's projection.  Landmark rows are copied into shared
+// memory once per block when they fit (a.nchunks == 1), else read from
+// global memory; the pair loop uses the distance table when a.qtab is set.
+
+template <int D, int KC, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) project_kernel(const FusedArgs a) {
+    constexpr int KK = KC - 4;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    float *sL = reinterpret_cast<float *>(smem + kBarrierBytes);
+    const bool resident = a.nchunks == 1;
+    uint32_t *qk = reinterpret_cast<uint32_t *>(sL + (resident ? (size_t)a.L * D : 0));
+    const int tid = threadIdx.x;
+    const long long ntiles = (a.n + kThreads - 1) / kThreads;
+    if ((long long)blockIdx.x >= ntiles) return;
+    if (resident) {
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)((size_t)a.L * D * sizeof(float));
+            mbar_expect_tx(bar, bytes);
+            copy_pieces(sL, a.hi, bytes, bar);
+        }
+        const bool ok = mbar_wait(bar, 0);
+        if (!__syncthreads_and(ok)) {
+            // the copy did not land in time: report, drain it (bounded), leave
+            if (tid == 0) {
+                atomicOr(a.status, kErrWaitTimeout);
+                mbar_wait(bar, 0);
+            }
+            return;
+        }
+    }
+    const float4 *Lg = resident ? reinterpret_cast<const float4 *>(sL)
+                                : reinterpret_cast<const float4 *>(a.hi);
+    const float2 *lo2 = reinterpret_cast<const float2 *>(a.lo);
+    uint32_t *nb = qk + tid;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long row = tile * kThreads + tid;
+        const bool active = row < a.n;
+        float sd[KK];
+        int si[KK];
+#pragma unroll
+        for (int t = 0; t < KK; ++t) {
+            const bool have = active && t < a.k;
+            si[t] = have ? min(max(a.idx[row * a.k + t], 0), a.L - 1) : 0;
+            sd[t] = have ? a.dist2[row * a.k + t] : 0.f;
+        }
+#pragma unroll
+        for (int t = 0; t < KK; t += 2)
+            nb[(t >> 1) * kThreads] = (uint32_t)si[t] | ((uint32_t)si[t + 1] << 16);
+        const float2 p = project_point<D, KK>(sd, nb, Lg, lo2, a);
+        if (active) reinterpret_cast<float2 *>(a.out)[row] = p;
+    }
+}
+
+template <int D, int KC, int MINB>
+cudaError_t launch_project(const FusedArgs &a, int grid, size_t smem, cudaStream_t stream) {
+    project_kernel<D, KC, MINB><<<grid, kThreads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
 // One thread per ordered pair (u, v): the squared distance table of the pair
 // loop, computed by the loop's own pair_q.
 template <int D>
@@ -1288,7 +1356,9 @@ const KernelOps Instance<D, KC>::ops = {
     reinterpret_cast<const void *>(&fused_kernel<D, KC, Instance<D, KC>::kMinBlocks>), KC,
     &launch_fused<D, KC, Instance<D, KC>::kMinBlocks>,
     reinterpret_cast<const void *>(&batch_kernel<D, KC, Instance<D, KC>::kMinBlocks>),
-    &launch_batch<D, KC, Instance<D, KC>::kMinBlocks>, &launch_qtab<D>};
+    &launch_batch<D, KC, Instance<D, KC>::kMinBlocks>, &launch_qtab<D>,
+    reinterpret_cast<const void *>(&project_kernel<D, KC, Instance<D, KC>::kMinBlocks>),
+    &launch_project<D, KC, Instance<D, KC>::kMinBlocks>};
 
 // Table of the list capacities instantiated for each D.
 #define ESOM_DEFINE_D(DV)                                            \

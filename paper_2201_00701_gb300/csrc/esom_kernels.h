@@ -64,6 +64,11 @@ struct KernelOps {
     // of hi with the pair loop's own arithmetic (pair_q), so the table holds
     // exactly the values the loop would compute.
     cudaError_t (*launch_qtab)(const float *hi, int L, float *qtab, cudaStream_t);
+    // Projection from given neighbours (FusedArgs idx / dist2, k per point):
+    // steps 2-4 of the fused kernel, landmark rows resident in shared memory
+    // when a.nchunks == 1 (project_smem_bytes).
+    const void *proj_func;
+    cudaError_t (*launch_proj)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
 };
 
 // Returns the instantiation for dimension D and list capacity kc, or nullptr.
@@ -78,47 +83,63 @@ constexpr int kQtabMaxL = 4096;
 // Tensor-core screening (tcgen05, TF32): tiles of kTcRows points (the MMA's M
 // and the TMEM lanes), landmark chunks of kTcN (the MMA's N); one block =
 // four selection warps (one thread per point) and one producer warp that
-// streams landmark chunk images and issues the MMAs.
+// streams landmark chunk images and issues the MMAs.  The kernel finds the k
+// nearest; a second kernel (project_kernel) projects from them.
 constexpr int kTcRows = 128;
 constexpr int kTcN = 64;
 constexpr int kTcThreads = 160;
 constexpr int kTcCols = 2 * kTcN;  // TMEM columns: two accumulator buffers
 
-// 128-byte column blocks of a row (32 TF32 values each), pipeline stages of
-// the landmark ring, and resident blocks per SM the launch aims for (shared
-// memory admits two).
-__host__ __device__ constexpr int tc_nblk(int D) { return (D + 31) / 32; }
-__host__ __device__ constexpr int tc_stages(int D) { return tc_nblk(D) == 1 ? 3 : 2; }
-__host__ __device__ constexpr int tc_minb(int, int) { return 2; }
+// Operand layout: rows of tc_row_bytes per column block (64 bytes = 16 TF32
+// values with the 64-byte swizzle for d <= 16, else 128 bytes = 32 values
+// with the 128-byte swizzle), tc_nblk column blocks; pipeline stages of the
+// landmark ring; resident blocks per SM the launch aims for.
+__host__ __device__ constexpr int tc_row_bytes(int D) { return D <= 16 ? 64 : 128; }
+__host__ __device__ constexpr int tc_nblk(int D) { return D <= 16 ? 1 : (D + 31) / 32; }
+__host__ __device__ constexpr int tc_stages(int D) { return D <= 32 ? 3 : 2; }
+__host__ __device__ constexpr int tc_minb(int D, int KC) { return D <= 16 ? (KC <= 16 ? 4 : 3) : 2; }
 
 // Bytes of one chunk image: the high TF32 parts of kTcN rows, then the low
-// parts, each kTcN rows x 128 bytes per column block, rows in the
-// 128-byte-swizzled K-major order the MMA reads (see tc_image_offset).
+// parts, in the swizzled K-major order the MMA reads (see tc_image_offset).
 __host__ __device__ inline size_t tc_chunk_bytes(int D) {
-    return (size_t)2 * kTcN * 128 * tc_nblk(D);
+    return (size_t)2 * kTcN * tc_row_bytes(D) * tc_nblk(D);
 }
 
-// Byte offset of 16-byte piece c (values 4c..4c+3 of column block blk) of
-// row r inside a 1024-byte-aligned operand of `rows` rows: 8-row groups of
-// 1024 bytes, rows 128 bytes apart, piece c of row r at slot c ^ (r mod 8).
-__host__ __device__ inline unsigned tc_image_offset(int rows, int r, int blk, int c) {
-    return (unsigned)(blk * rows * 128 + (r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+// Byte offset of 16-byte piece c of column block blk of row r inside an
+// operand of `rows` rows (base aligned to 1024 bytes): 8-row groups of
+// 8 * row_bytes, piece c of row r at slot c ^ (r mod 8) (128-byte swizzle)
+// or c ^ ((r / 2) mod 4) (64-byte swizzle).
+__host__ __device__ inline unsigned tc_image_offset(int D, int rows, int r, int blk, int c) {
+    const int rb = tc_row_bytes(D);
+    const int sw = rb == 64 ? ((r >> 1) & 3) : (r & 7);
+    return (unsigned)(blk * rows * rb + (r >> 3) * 8 * rb + (r & 7) * rb + ((c ^ sw) << 4));
 }
 
 inline size_t tc_smem_bytes(int D) {
-    const size_t nb = (size_t)tc_nblk(D);
+    const size_t rb = (size_t)tc_row_bytes(D) * tc_nblk(D);
     return 1024                                  // alignment slack
-           + 2 * (size_t)kTcRows * 128 * nb      // point tile (high and low parts)
+           + 2 * (size_t)kTcRows * rb            // point tile (high and low parts)
            + (size_t)tc_stages(D) * tc_chunk_bytes(D)  // landmark chunk ring
            + (size_t)kQueue * kTcRows * 4        // candidate queue
            + 256;                                // barriers, TMEM address, flags
 }
+
+// Points per tensor-core k-NN pass of esom_project: the pass writes their
+// neighbours (k indices and squared distances each) to the handle's scratch,
+// the projection kernel reads them.
+constexpr long long kTcPass = 1 << 19;
 
 struct TcOps {
     const void *func;
     int kc;
     cudaError_t (*launch)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
 };
+
+
+inline size_t project_smem_bytes(int D, int L, bool resident) {
+    return kBarrierBytes + (resident ? (size_t)L * D * sizeof(float) : 0) +
+           (size_t)kQueue * kThreads * sizeof(unsigned);
+}
 
 // Tensor-core instantiation for D and list capacity kc, or nullptr.
 const TcOps *tc_ops(int D, int kc);

@@ -308,8 +308,10 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
     // handle's (rows, 2-D positions, norms, squared-distance table), the
     // minibatch k-NN indices
     const size_t qtab = d.L <= esom::kQtabMaxL ? (size_t)d.L * d.L * 4 : 0;
+    // tensor-core screening: landmark images and the neighbour scratch
     const size_t img = s->screening == ESOM_SCREEN_TF32
-                           ? (size_t)((d.L + esom::kTcN - 1) / esom::kTcN) * esom::tc_chunk_bytes(d.d)
+                           ? (size_t)((d.L + esom::kTcN - 1) / esom::kTcN) * esom::tc_chunk_bytes(d.d) +
+                                 (size_t)esom::kTcPass * d.k * 8
                            : 0;
     const size_t bytes = (size_t)d.n * d.d * 4 + (size_t)d.n * 8 + (size_t)d.L * (d.d + 2) * 4 * 2 +
                          (size_t)((d.L + 63) & ~63) * 4 + qtab + img +

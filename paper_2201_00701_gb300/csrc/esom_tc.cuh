@@ -1,7 +1,10 @@
-// Tensor-core screened projection kernel for sm_103a (tcgen05, TF32).
+// Tensor-core screened k-NN kernel for sm_103a (tcgen05, TF32).
 //
-// Same result as the plain fused kernel (esom_fused.cuh), computed with the
-// distance block of step 1 on the tensor cores.  The paper's k-NN spends its
+// Step 1 of the projection with the same result as the plain fused kernel
+// (esom_fused.cuh), computed with the distance block on the tensor cores;
+// esom_project follows it with project_kernel (steps 2-4 from the
+// neighbours), as the paper runs k-NN and projection as two kernels with an
+// exchange buffer (Section 4.4).  The paper's k-NN spends its
 // time in the g x d distance block (Section 4.2, and Section 5's remark that
 // the k-NN cost grows with g d); here that block is a dense contraction of a
 // tile of 128 points with chunks of 64 landmarks:
@@ -25,8 +28,9 @@
 // The list is then re-ranked with exact FP32 difference-form distances, and
 // a bound on the TF32 screening error certifies that no landmark outside the
 // list can be among the k nearest; a point that fails is rescanned exactly.
-// So the neighbours, their distances and the coordinates are the plain
-// kernel's, bit for bit; TF32 only decides how often a point is rescanned.
+// So the neighbours and their distances are the plain kernel's, bit for
+// bit (and so are the coordinates projected from them); the screening
+// precision only decides how often a point is rescanned.
 //
 // Roles: warps 0-3 select (thread t <-> point row t <-> TMEM lane t); warp 4
 // is the producer: one lane streams the landmark chunk images through a ring
@@ -35,8 +39,8 @@
 // overlaps the selection of chunk c.  As soon as a tile's last chunk has
 // been read (every MMA of the tile is then complete), the selection threads
 // write the next tile's operand (split rows) into the one point buffer and
-// only then re-rank and project the current tile, so the next tile's MMAs
-// overlap that work.  Every
+// only then re-rank the current tile, so the next tile's MMAs overlap that
+// work.  Every
 // wait is bounded; on a timeout the block raises the status word, drains
 // its own copies and MMAs and frees its tensor memory.
 #pragma once
@@ -80,14 +84,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Shared-memory matrix descriptor of a K-major operand in the 128-byte
-// swizzle layout: 8-row groups 1024 bytes apart (stride byte offset), the
-// leading byte offset unused for this layout (1), descriptor version 1,
-// layout type 2 (128-byte swizzle).  The operand base is 1024-byte aligned;
-// a K step inside the 128-byte row moves the start address by its bytes.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major operand in a swizzled
+// layout: 8-row groups SBO bytes apart, the leading byte offset unused for
+// these layouts (1), descriptor version 1, layout type 2 (128-byte swizzle)
+// or 4 (64-byte swizzle).  The operand base is 1024-byte aligned; a K step
+// inside the row moves the start address by its bytes.
+template <int ROWB>
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
+    constexpr uint64_t kLayout = ROWB == 128 ? 2 : 4;
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
-           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+           ((uint64_t)((8 * ROWB) >> 4) << 32) | ((uint64_t)1 << 46) | (kLayout << 61);
 }
 
 // Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A and B TF32
@@ -116,34 +122,26 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
         : "memory");
 }
 
-// 64 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes
-// 32 (w mod 4) ..), waited for inside the same statement so that no use of
-// the values can be scheduled before the load has completed.
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
-    uint32_t r[64];
+// 32 consecutive FP32 columns of this thread's TMEM lane, waited for inside
+// the same statement.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
-        "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
-        "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, "
-        "[%64];\n\t"
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "[%32];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
           "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
           "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]),
-          "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
-          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
-          "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]),
-          "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]),
-          "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+          "=r"(r[31])
         : "r"(taddr)
         : "memory");
 #pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // FP32 -> TF32, round to nearest (ties away from zero); low 13 bits zero.
@@ -171,16 +169,19 @@ template <int D, int KC>
 __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const FusedArgs a) {
     static_assert(D % 4 == 0 && D >= 4 && D <= 64, "D must be a multiple of 4 in [4, 64]");
     static_assert(KC >= 8 && KC <= 36 && KC % 4 == 0, "list capacity out of range");
-    static_assert((KC - 4) / 2 <= kQueue, "neighbour indices must fit in the thread's queue column");
     constexpr int KK = KC - 4;
+    constexpr int RB = tc_row_bytes(D);          // bytes of a row per column block
     constexpr int NB = tc_nblk(D);
+    constexpr int PPB = RB / 16;                 // 16-byte pieces per block row
+    constexpr int KPB = RB / 32;                 // K steps (8 TF32) per block row
     constexpr int S = tc_stages(D);
-    constexpr int KS = (D + 7) / 8;  // MMA K steps of 8 TF32 values (32 bytes)
-    constexpr uint32_t kAPart = kTcRows * 128 * NB;  // x_hi (then x_lo) of a tile
-    constexpr uint32_t kBPart = kTcN * 128 * NB;     // l_hi (then l_lo) of a chunk
+    constexpr int KS = (D + 7) / 8;              // MMA K steps of 8 TF32 values
+    constexpr uint32_t kAPart = kTcRows * RB * NB;  // x_hi (then x_lo) of a tile
+    constexpr uint32_t kBPart = kTcN * RB * NB;     // l_hi (then l_lo) of a chunk
     constexpr uint32_t kBBytes = 2 * kBPart;
     constexpr uint32_t kIdesc = tc_idesc();
     constexpr int QS = kTcRows;  // queue stride: one column per selection thread
+    constexpr int KF = ((KC + 7) & ~7) < 32 ? ((KC + 7) & ~7) : 32;  // first sorted block
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -269,12 +270,12 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                     const uint32_t dt = tmem + (uint32_t)(tb * kTcN);
 #pragma unroll
                     for (int ks = 0; ks < KS; ++ks) {
-                        const uint32_t ka = (uint32_t)((ks >> 2) * kTcRows * 128 + (ks & 3) * 32);
-                        const uint32_t kb = (uint32_t)((ks >> 2) * kTcN * 128 + (ks & 3) * 32);
-                        mma_tf32(dt, sw128_desc(ahi + ka), sw128_desc(bhi + kb), kIdesc,
+                        const uint32_t ka = (uint32_t)((ks / KPB) * kTcRows * RB + (ks % KPB) * 32);
+                        const uint32_t kb = (uint32_t)((ks / KPB) * kTcN * RB + (ks % KPB) * 32);
+                        mma_tf32(dt, sw_desc<RB>(ahi + ka), sw_desc<RB>(bhi + kb), kIdesc,
                                  ks > 0 ? 1u : 0u);
-                        mma_tf32(dt, sw128_desc(alo + ka), sw128_desc(bhi + kb), kIdesc, 1u);
-                        mma_tf32(dt, sw128_desc(ahi + ka), sw128_desc(blo + kb), kIdesc, 1u);
+                        mma_tf32(dt, sw_desc<RB>(alo + ka), sw_desc<RB>(bhi + kb), kIdesc, 1u);
+                        mma_tf32(dt, sw_desc<RB>(ahi + ka), sw_desc<RB>(blo + kb), kIdesc, 1u);
                     }
                     mma_commit(&t_full[tb]);
                     mma_commit(&l_empty[s]);
@@ -305,7 +306,6 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         const float q = a.key_quant;
         const float lmax = *a.lmax;
         const float4 *Lg = reinterpret_cast<const float4 *>(a.hi);
-        const float2 *lo2 = reinterpret_cast<const float2 *>(a.lo);
         const uint32_t my_lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         constexpr float kGamma = (2.25f * D + 10.f) * kU * 1.25f;
 
@@ -320,8 +320,8 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
 #pragma unroll
             for (int blk = 0; blk < NB; ++blk)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int e = blk * 8 + c;  // float4 index of the row
+                for (int c = 0; c < PPB; ++c) {
+                    const int e = blk * PPB + c;  // float4 index of the row
                     float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
                     if (e < D / 4 && act) {
                         const float4 v = __ldg(xp + e);
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                                         to_tf32(v.w - h.w));
                     }
                     if (e < 2 * KS) {  // pieces the MMA K steps read
-                        const unsigned off = tc_image_offset(kTcRows, tid, blk, c);
+                        const unsigned off = tc_image_offset(D, kTcRows, tid, blk, c);
                         *reinterpret_cast<float4 *>(sA + off) = h;
                         *reinterpret_cast<float4 *>(sA + kAPart + off) = l;
                     }
@@ -343,6 +343,30 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
             __syncwarp();
             if (lane == 0) mbar_arrive(a_ready);
             return xx;
+        };
+
+        // Keys of 32 values of chunk base (columns h32 .. h32 + 31) into the
+        // queue, flushing when a lane's queue may overflow.
+        auto push32 = [&](const float (&v)[32], int base, int h32, int cnt, float (&keys)[KC],
+                          ScanState &st, float M) {
+            const float4 *N4 = reinterpret_cast<const float4 *>(a.norms + base + h32);
+#pragma unroll
+            for (int jb = 0; jb < 32; jb += 8) {
+                const float4 n0 = __ldg(N4 + jb / 4), n1 = __ldg(N4 + jb / 4 + 1);
+                const float nn[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int j = h32 + jb + e;
+                    const float key =
+                        make_key(fmaf(-2.f, v[jb + e], nn[e]), (uint32_t)(base + j), mask);
+                    if (key < st.thr && j < cnt) {
+                        qk[st.qn * QS + tid] = __float_as_uint(key);
+                        ++st.qn;
+                    }
+                }
+                if (__any_sync(0xffffffffu, st.qn > kQueue - 8))
+                    queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
+            }
         };
 
         bool ok = true;
@@ -370,21 +394,15 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                     break;
                 }
                 tc_fence_after();
-                float v[64];
-                tmem_ld64(my_lane_addr + (uint32_t)(tb * kTcN), v);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&t_empty[tb]);
-
                 const int base = c * kTcN;
                 const int cnt = a.L - base < kTcN ? a.L - base : kTcN;
-                const float4 *N4 = reinterpret_cast<const float4 *>(a.norms + base);
-                int jstart = 0;
+                const uint32_t col = my_lane_addr + (uint32_t)(tb * kTcN);
+                float v[32];
+                tmem_ld32(col, v);
                 if (c == 0) {
                     // The first KF values go straight into the list (one
-                    // sorting network); the KF - KC largest are dropped,
+                    // sorting network); any of them beyond KC are dropped,
                     // which the certificate covers like any key pushed out.
-                    constexpr int KF = (KC + 7) & ~7;
                     float kv[KF];
 #pragma unroll
                     for (int t = 0; t < KF; ++t)
@@ -393,32 +411,35 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                                         : INFINITY;
                     key_sort<KF>(kv);
 #pragma unroll
-                    for (int t = 0; t < KC; ++t) keys[t] = kv[t];
+                    for (int t = 0; t < KC; ++t) keys[t] = t < KF ? kv[t] : INFINITY;
                     st.thr = push_threshold(at<KC>(keys, a.k - 1), M, q);
-                    jstart = KF;
-                }
+                    if (KF < 32) {
+                        // the rest of the first half
 #pragma unroll
-                for (int jb = 0; jb < kTcN; jb += 8) {
-                    if (jb < jstart) continue;
-                    const float4 n0 = __ldg(N4 + jb / 4), n1 = __ldg(N4 + jb / 4 + 1);
-                    const float nn[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const float key =
-                            make_key(fmaf(-2.f, v[jb + e], nn[e]), (uint32_t)(base + jb + e), mask);
-                        if (key < st.thr && jb + e < cnt) {
-                            qk[st.qn * QS + tid] = __float_as_uint(key);
-                            ++st.qn;
-                        }
-                    }
-                    if (__any_sync(0xffffffffu, st.qn > kQueue - 8))
+                        for (int t = 0; t < 32; ++t)
+                            if (t >= KF && t < cnt) {
+                                const float key = make_key(fmaf(-2.f, v[t], __ldg(a.norms + t)),
+                                                           (uint32_t)t, mask);
+                                if (key < st.thr) {
+                                    qk[st.qn * QS + tid] = __float_as_uint(key);
+                                    ++st.qn;
+                                }
+                            }
                         queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
+                    }
+                } else {
+                    push32(v, base, 0, cnt, keys, st, M);
                 }
+                tmem_ld32(col + 32, v);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&t_empty[tb]);
+                push32(v, base, 32, cnt, keys, st, M);
             }
             if (!ok) break;
             // Every MMA of this tile has completed (its last chunk has been
             // read): the next tile's operand replaces this one's, so that its
-            // MMAs run while this tile is re-ranked and projected.
+            // MMAs run while this tile is re-ranked.
             if (i + 1 < my_tiles) xx_next = write_tile(tile + gridDim.x);
             queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
 
@@ -445,24 +466,14 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                     si[t] = tsi[t];
                 }
             }
-
-            if (a.mode == kKnn) {
-                if (active) {
+            if (active) {
 #pragma unroll
-                    for (int s2 = 0; s2 < KK; ++s2)
-                        if (s2 < a.k) {
-                            a.idx[row * a.k + s2] = si[s2];
-                            if (a.dist2) a.dist2[row * a.k + s2] = sd[s2];
-                        }
-                }
-                continue;
+                for (int s2 = 0; s2 < KK; ++s2)
+                    if (s2 < a.k) {
+                        a.idx[row * a.k + s2] = si[s2];
+                        if (a.dist2) a.dist2[row * a.k + s2] = sd[s2];
+                    }
             }
-            uint32_t *nb = qk + tid;
-#pragma unroll
-            for (int s2 = 0; s2 < KK; s2 += 2)
-                nb[(s2 >> 1) * QS] = (uint32_t)si[s2] | ((uint32_t)si[s2 + 1] << 16);
-            const float2 p = project_point<D, KK, QS>(sd, nb, Lg, lo2, a);
-            if (active) reinterpret_cast<float2 *>(a.out)[row] = p;
         }
         if (!ok) raise_abort();
     }
