@@ -181,6 +181,16 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg);
 #define ESOM_SCREEN_TF32 1
 esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream);
 
+/* on != 0: esom_project with FP32 screening runs as two kernels, as the
+ * paper's pipeline does (Section 4.4): the k-NN kernel writes each point's
+ * neighbours to the handle's scratch (2^19 * k * 8 bytes, allocated here),
+ * then the projection kernel reads them, in passes of 2^19 points; on = 0:
+ * one fused kernel (the default).  Same results either way; projections of
+ * one handle on different streams must not overlap while split (the
+ * scratch is shared).  Tensor-core screening always runs split.
+ * Errors: ESOM_ENOMEM, ESOM_EUNSUPPORTED, ESOM_ECUDA. */
+esom_status esom_set_split(esom_handle h, int on);
+
 /* ---------------------------------------------------------------------------
  * Batched projection: many datasets of uneven n, d and L through one plan.
  * Each item names a handle whose landmarks it uses (d, L and k come from the
@@ -203,11 +213,16 @@ typedef struct {
 
 /* Builds the plan (allocates its device tables).  autotune != 0 times
  * candidate launch shapes of every group on the batch itself (running it a
- * few times, so the outputs are written) and keeps the fastest. */
+ * few times, so the outputs are written) and keeps the fastest: landmark
+ * chunking (each dataset's own, or forced chunks of 512 or 256), blocks per
+ * SM (occupancy limit or 1), or one single-dataset launch per dataset (for
+ * large datasets the persistent group launch may not pay).  Handles are used
+ * with FP32 screening and the fused kernel whatever their own settings. */
 esom_status esom_batch_create(const esom_batch_item *items, int count, int autotune,
                               esom_batch *out);
 
-/* Enqueues the plan's launches (one per group) on `stream`. */
+/* Enqueues the plan's launches (one per group, or one per dataset of a
+ * group whose chosen shape is separate launches) on `stream`. */
 esom_status esom_batch_run(esom_batch b, esom_stream_t stream);
 
 /* Same as esom_batch_run, replayed from a CUDA graph captured on the first

@@ -97,6 +97,7 @@ def load(build_if_missing: bool = False):
         "esom_project_noalloc": ([P, I64, P, P, I, I, I, P, F, F, P], I),
         "esom_get_stats": ([P, P, ctypes.POINTER(_Stats), I], I),
         "esom_set_screening": ([P, I, P], I),
+        "esom_set_split": ([P, I], I),
         "esom_batch_create": ([ctypes.POINTER(BatchItem), I, I, ctypes.POINTER(P)], I),
         "esom_batch_run": ([P, P], I),
         "esom_batch_run_graph": ([P, P], I),
@@ -191,6 +192,11 @@ def esom_get_stats(h, stream: int = 0, reset: bool = False):
 def esom_set_screening(h, mode: int, stream: int = 0) -> int:
     """ESOM_SCREEN_FP32 (0) or ESOM_SCREEN_TF32 (1, tensor cores)."""
     return load().esom_set_screening(h, mode, stream)
+
+
+def esom_set_split(h, on: bool) -> int:
+    """Two kernels (k-NN, then projection from neighbours) instead of one."""
+    return load().esom_set_split(h, int(on))
 
 
 def esom_project_noalloc(points_ptr: int, n: int, hi_ptr: int, lo_ptr: int, d: int, L: int,
@@ -394,6 +400,9 @@ class Projector:
     def set_screening(self, mode: int):
         """ESOM_SCREEN_FP32 or ESOM_SCREEN_TF32; same results, different speed."""
         check(esom_set_screening(self.h, mode, self._stream()))
+
+    def set_split(self, on: bool):
+        check(esom_set_split(self.h, on))
 
     def set_landmark_chunk(self, chunk: int):
         check(esom_set_landmark_chunk(self.h, chunk))

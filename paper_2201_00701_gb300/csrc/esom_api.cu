@@ -78,7 +78,9 @@ __global__ void landmark_prep_kernel(float *__restrict__ hi, int L, int D,
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= padded) return;
     if (j >= L) {
-        norms[j] = 0.f;
+        // padding: NaN, so a screening value built from it never passes a
+        // threshold (every comparison with NaN is false)
+        norms[j] = __int_as_float(0x7fc00000);
         return;
     }
     float4 *row = reinterpret_cast<float4 *>(hi + (size_t)j * D);
@@ -197,16 +199,22 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
     a.dist2 = dist2;
     a.mode = mode;
     cudaError_t e = cudaSuccess;
-    if (h->screening) {
-        // Tensor-core k-NN; for a projection, in passes of kTcPass points
-        // through the handle's neighbour scratch, each followed by the
-        // projection kernel.
+    if (h->screening || (h->split && mode == esom::kProject)) {
+        // Split execution: the k-NN kernel (tensor-core or plain); for a
+        // projection, in passes of kTcPass points through the handle's
+        // neighbour scratch, each followed by the projection kernel.
         auto knn = [&](FusedArgs k, long long cnt) -> cudaError_t {
-            const long long tiles = (cnt + esom::kTcRows - 1) / esom::kTcRows;
-            long long grid = (long long)h->tc_blocks_per_sm * h->num_sms;
-            if (grid > tiles) grid = tiles;
             k.mode = esom::kKnn;
-            return h->tc->launch(k, (int)grid, h->tc_smem, stream);
+            if (h->screening) {
+                const long long tiles = (cnt + esom::kTcRows - 1) / esom::kTcRows;
+                long long grid = (long long)h->tc_blocks_per_sm * h->num_sms;
+                if (grid > tiles) grid = tiles;
+                return h->tc->launch(k, (int)grid, h->tc_smem, stream);
+            }
+            k.ntiles = (cnt + esom::kThreads - 1) / esom::kThreads;
+            long long grid = (long long)h->blocks_per_sm * h->num_sms;
+            if (grid > k.ntiles) grid = k.ntiles;
+            return h->ops->launch(k, (int)grid, h->smem, stream);
         };
         if (mode == esom::kKnn) {
             e = knn(a, n);
@@ -499,6 +507,53 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg) {
     return ESOM_OK;
 }
 
+namespace {
+// Configures the projection-from-neighbours kernel and allocates the
+// neighbour scratch of the split (two-kernel) execution.
+esom_status prepare_split(esom_ctx *h) {
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(shared memory opt-in)");
+    const bool resident = h->nchunks == 1;
+    const size_t psmem = esom::project_smem_bytes(h->d, h->L, resident);
+    if (psmem > (size_t)optin)
+        return fail(ESOM_EUNSUPPORTED, "projection needs %zu bytes of shared memory", psmem);
+    e = cudaFuncSetAttribute(h->ops->proj_func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(projection shared memory)");
+    int pbps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pbps, h->ops->proj_func, esom::kThreads, psmem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (pbps < 1) return fail(ESOM_EUNSUPPORTED, "projection launch does not fit on an SM");
+    if (!h->tc_idx) {
+        e = cudaMalloc(&h->tc_idx, (size_t)esom::kTcPass * h->k * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&h->tc_d2, (size_t)esom::kTcPass * h->k * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaFree(h->tc_idx);
+            cudaFree(h->tc_d2);
+            h->tc_idx = nullptr;
+            h->tc_d2 = nullptr;
+            return fail(ESOM_ENOMEM, "device allocation of the neighbour scratch: %s",
+                        cudaGetErrorString(e));
+        }
+    }
+    h->proj_smem = psmem;
+    h->proj_blocks_per_sm = pbps;
+    return ESOM_OK;
+}
+}  // namespace
+
+esom_status esom_set_split(esom_handle h, int on) {
+    if (!h) return fail(ESOM_EINVAL, "null handle");
+    esom_status s = check_device(h);
+    if (s != ESOM_OK) return s;
+    if (on) {
+        s = prepare_split(h);
+        if (s != ESOM_OK) return s;
+    }
+    h->split = on ? 1 : 0;
+    return ESOM_OK;
+}
+
 esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
     if (!h) return fail(ESOM_EINVAL, "null handle");
     if (mode != ESOM_SCREEN_FP32 && mode != ESOM_SCREEN_TF32)
@@ -544,28 +599,13 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
     if (bps * esom::kTcCols > 512) bps = 512 / esom::kTcCols;
     if (bps < 1) return fail(ESOM_EUNSUPPORTED, "tensor-core launch does not fit on an SM");
     // the projection kernel that follows each k-NN pass
-    const bool resident = h->nchunks == 1;
-    const size_t psmem = esom::project_smem_bytes(h->d, h->L, resident);
-    if (psmem > (size_t)optin)
-        return fail(ESOM_EUNSUPPORTED, "projection needs %zu bytes of shared memory", psmem);
-    e = cudaFuncSetAttribute(h->ops->proj_func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(projection shared memory)");
-    int pbps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pbps, h->ops->proj_func, esom::kThreads, psmem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (pbps < 1) return fail(ESOM_EUNSUPPORTED, "projection launch does not fit on an SM");
+    s = prepare_split(h);
+    if (s != ESOM_OK) return s;
     if (!h->img) {
         const size_t bytes = (size_t)((h->L + esom::kTcN - 1) / esom::kTcN) * esom::tc_chunk_bytes(h->d);
         e = cudaMalloc(&h->img, bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&h->tc_idx, (size_t)esom::kTcPass * h->k * sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc(&h->tc_d2, (size_t)esom::kTcPass * h->k * sizeof(float));
         if (e != cudaSuccess) {
-            cudaFree(h->img);
-            cudaFree(h->tc_idx);
-            cudaFree(h->tc_d2);
             h->img = nullptr;
-            h->tc_idx = nullptr;
-            h->tc_d2 = nullptr;
             return fail(ESOM_ENOMEM, "device allocation of the landmark images: %s",
                         cudaGetErrorString(e));
         }
@@ -577,8 +617,6 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
     h->tc = tc;
     h->tc_smem = smem;
     h->tc_blocks_per_sm = bps;
-    h->proj_smem = psmem;
-    h->proj_blocks_per_sm = pbps;
     h->screening = mode;
     return ESOM_OK;
 }

@@ -40,6 +40,7 @@ esom_status bcuda(cudaError_t e, const char *what) {
 struct Shape {
     int forced_chunk;   // 0: each dataset's own choice; > 0: stream landmarks in chunks of this
     int blocks_per_sm;  // blocks per SM (1 .. occupancy limit)
+    int separate = 0;   // 1: each dataset by its own single-dataset launch
 };
 
 struct Group {
@@ -83,8 +84,22 @@ long long point_cost(const esom_ctx *h) {
 }
 
 // Applies a launch shape: per-dataset chunking, shared memory, grid and the
-// cost-balanced tile ranges (uploaded to the device).
+// cost-balanced tile ranges (uploaded to the device); or, for `separate`,
+// each dataset's own launch configuration.
 esom_status apply_shape(esom_batch_ctx *b, Group &g, const Shape &sh) {
+    if (sh.separate) {
+        for (size_t i = 0; i < g.items.size(); ++i) {
+            const esom_ctx *h = b->items[g.items[i]].landmarks;
+            FusedArgs &a = g.args[i];
+            a.chunk = h->chunk;
+            a.nchunks = h->nchunks;
+            a.qtab = h->nchunks > 1 ? h->qtab : nullptr;
+        }
+        g.shape = Shape{0, 0, 1};
+        g.grid = 0;
+        g.smem = 0;
+        return ESOM_OK;
+    }
     int cap = 0;
     for (size_t i = 0; i < g.items.size(); ++i) {
         const esom_ctx *h = b->items[g.items[i]].landmarks;
@@ -94,6 +109,7 @@ esom_status apply_shape(esom_batch_ctx *b, Group &g, const Shape &sh) {
             chunk = esom::landmark_chunk(h->L, h->d, sh.forced_chunk);
         a.chunk = chunk;
         a.nchunks = (h->L + chunk - 1) / chunk;
+        a.qtab = a.nchunks > 1 ? h->qtab : nullptr;
         cap = std::max(cap, chunk);
     }
     const size_t smem = esom::batch_smem_bytes(g.D, cap);
@@ -133,12 +149,24 @@ esom_status apply_shape(esom_batch_ctx *b, Group &g, const Shape &sh) {
     if (e != cudaSuccess) return bcuda(e, "batch plan upload");
     g.grid = (int)grid;
     g.smem = smem;
-    g.shape = Shape{sh.forced_chunk, use};
+    g.shape = Shape{sh.forced_chunk, use, 0};
     return ESOM_OK;
 }
 
 esom_status launch_group(esom_batch_ctx *b, const Group &g, cudaStream_t st) {
     if (g.tiles == 0) return ESOM_OK;
+    if (g.shape.separate) {
+        for (size_t i = 0; i < g.items.size(); ++i) {
+            const esom_ctx *h = b->items[g.items[i]].landmarks;
+            const FusedArgs &a = g.args[i];
+            if (a.n == 0) continue;
+            long long grid = (long long)h->blocks_per_sm * h->num_sms;
+            if (grid > a.ntiles) grid = a.ntiles;
+            const cudaError_t e = h->ops->launch(a, (int)grid, h->smem, st);
+            if (e != cudaSuccess) return bcuda(e, "batch launch (separate)");
+        }
+        return ESOM_OK;
+    }
     BatchArgs a;
     a.items = g.d_items;
     a.tile_base = g.d_tile_base;
@@ -153,12 +181,13 @@ esom_status launch_group(esom_batch_ctx *b, const Group &g, cudaStream_t st) {
 esom_status autotune(esom_batch_ctx *b, Group &g) {
     std::vector<Shape> cands;
     for (int fc : {0, 512, 256})
-        for (int bps : {0, 1}) cands.push_back(Shape{fc, bps});
+        for (int bps : {0, 1}) cands.push_back(Shape{fc, bps, 0});
+    cands.push_back(Shape{0, 0, 1});
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    Shape best_shape{0, 0};
+    Shape best_shape{0, 0, 0};
     for (const Shape &c : cands) {
         if (apply_shape(b, g, c) != ESOM_OK) continue;
         float ms = 0.f, tot = 0.f;
@@ -191,9 +220,9 @@ void describe(esom_batch_ctx *b) {
         snprintf(buf, sizeof(buf),
                  "%s{\"d\": %d, \"kc\": %d, \"datasets\": %zu, \"tiles\": %lld, \"grid\": %d, "
                  "\"shared_bytes\": %zu, \"forced_chunk\": %d, \"blocks_per_sm\": %d, "
-                 "\"tuned_ms\": %.4f}",
+                 "\"separate\": %d, \"tuned_ms\": %.4f}",
                  i ? ", " : "", g.D, g.kc, g.items.size(), g.tiles, g.grid, g.smem,
-                 g.shape.forced_chunk, g.shape.blocks_per_sm, g.tuned_ms);
+                 g.shape.forced_chunk, g.shape.blocks_per_sm, g.shape.separate, g.tuned_ms);
         out += buf;
     }
     out += "]}";
@@ -283,7 +312,7 @@ esom_status esom_batch_create(const esom_batch_item *items, int count, int autot
             break;
         }
         if (g.tiles == 0) continue;
-        s = autotune_flag ? autotune(b, g) : apply_shape(b, g, Shape{0, 0});
+        s = autotune_flag ? autotune(b, g) : apply_shape(b, g, Shape{0, 0, 0});
     }
     if (s != ESOM_OK) {
         esom_batch_destroy(b);

@@ -26,6 +26,7 @@ struct esom_ctx {
     // tensor-core screening (esom_set_screening); img holds the landmark
     // chunk images while it is on
     int screening = 0;
+    int split = 0;  // k-NN kernel + projection kernel instead of the fused one
     const esom::TcOps *tc = nullptr;
     unsigned char *img = nullptr;
     int tc_blocks_per_sm = 0;

@@ -152,7 +152,7 @@ cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img,
 // Records `msg` as this host thread's last error message; returns s.
 int set_error(int s, const char *msg);
 
-// Squared landmark norms (norms[j], j < L; zero padding up to a multiple of
+// Squared landmark norms (norms[j], j < L; NaN padding up to a multiple of
 // `pad`, itself a multiple of 4), the largest norm (*lmax, which must hold 0
 // on entry), and the rows of hi swizzled in place (see swz).
 cudaError_t launch_landmark_prep(float *hi, int L, int D, float *norms, float *lmax,

@@ -346,25 +346,32 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         };
 
         // Keys of 32 values of chunk base (columns h32 .. h32 + 31) into the
-        // queue, flushing when a lane's queue may overflow.
-        auto push32 = [&](const float (&v)[32], int base, int h32, int cnt, float (&keys)[KC],
-                          ScanState &st, float M) {
-            const float4 *N4 = reinterpret_cast<const float4 *>(a.norms + base + h32);
+        // queue: one FMA for the screening value, the key, the threshold
+        // test and a predicated push.  Padding columns (beyond L) have NaN
+        // norms, so they never pass.  The queue is flushed after every 16
+        // values when a lane may not have room for 16 more.
+        auto push32 = [&](const float (&v)[32], int jbase, float (&keys)[KC], ScanState &st,
+                          float M) {
+            const float4 *N4 = reinterpret_cast<const float4 *>(a.norms + jbase);
 #pragma unroll
-            for (int jb = 0; jb < 32; jb += 8) {
-                const float4 n0 = __ldg(N4 + jb / 4), n1 = __ldg(N4 + jb / 4 + 1);
-                const float nn[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+            for (int hb = 0; hb < 32; hb += 16) {
+                uint32_t *qp = qk + st.qn * QS + tid;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int j = h32 + jb + e;
-                    const float key =
-                        make_key(fmaf(-2.f, v[jb + e], nn[e]), (uint32_t)(base + j), mask);
-                    if (key < st.thr && j < cnt) {
-                        qk[st.qn * QS + tid] = __float_as_uint(key);
-                        ++st.qn;
+                for (int jb = 0; jb < 16; jb += 4) {
+                    const float4 n4 = __ldg(N4 + (hb + jb) / 4);
+                    const float nn[4] = {n4.x, n4.y, n4.z, n4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float key = make_key(fmaf(-2.f, v[hb + jb + e], nn[e]),
+                                                   (uint32_t)(jbase + hb + jb + e), mask);
+                        if (key < st.thr) {
+                            *qp = __float_as_uint(key);
+                            qp += QS;
+                        }
                     }
                 }
-                if (__any_sync(0xffffffffu, st.qn > kQueue - 8))
+                st.qn = (int)((qp - (qk + tid)) / QS);
+                if (__any_sync(0xffffffffu, st.qn > kQueue - 16))
                     queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
             }
         };
@@ -386,6 +393,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
             ScanState st;
             st.qn = 0;
             st.thr = INFINITY;
+#pragma unroll 1
             for (int c = 0; c < nch; ++c, ++g) {
                 const int tb = (int)(g & 1);
                 const bool w = mbar_wait(&t_full[tb], (uint32_t)((g >> 1) & 1));
@@ -395,46 +403,48 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                 }
                 tc_fence_after();
                 const int base = c * kTcN;
-                const int cnt = a.L - base < kTcN ? a.L - base : kTcN;
                 const uint32_t col = my_lane_addr + (uint32_t)(tb * kTcN);
-                float v[32];
-                tmem_ld32(col, v);
-                if (c == 0) {
-                    // The first KF values go straight into the list (one
-                    // sorting network); any of them beyond KC are dropped,
-                    // which the certificate covers like any key pushed out.
-                    float kv[KF];
-#pragma unroll
-                    for (int t = 0; t < KF; ++t)
-                        kv[t] = t < cnt ? make_key(fmaf(-2.f, v[t], __ldg(a.norms + t)),
-                                                   (uint32_t)t, mask)
-                                        : INFINITY;
-                    key_sort<KF>(kv);
-#pragma unroll
-                    for (int t = 0; t < KC; ++t) keys[t] = t < KF ? kv[t] : INFINITY;
-                    st.thr = push_threshold(at<KC>(keys, a.k - 1), M, q);
-                    if (KF < 32) {
-                        // the rest of the first half
-#pragma unroll
-                        for (int t = 0; t < 32; ++t)
-                            if (t >= KF && t < cnt) {
-                                const float key = make_key(fmaf(-2.f, v[t], __ldg(a.norms + t)),
-                                                           (uint32_t)t, mask);
-                                if (key < st.thr) {
-                                    qk[st.qn * QS + tid] = __float_as_uint(key);
-                                    ++st.qn;
-                                }
-                            }
-                        queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    float v[32];
+                    tmem_ld32(col + (uint32_t)(32 * h), v);
+                    if (h == 1) {
+                        // both halves are in registers: release the buffer
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&t_empty[tb]);
                     }
-                } else {
-                    push32(v, base, 0, cnt, keys, st, M);
+                    if (c == 0 && h == 0) {
+                        // The first KF values go straight into the list (one
+                        // sorting network; padding columns sort last); any
+                        // beyond KC are dropped, which the certificate covers
+                        // like any key pushed out.  The rest of the half is
+                        // pushed.
+                        const int cnt = a.L < kTcN ? a.L : kTcN;
+                        float kv[KF];
+#pragma unroll
+                        for (int t = 0; t < KF; ++t)
+                            kv[t] = t < cnt ? make_key(fmaf(-2.f, v[t], __ldg(a.norms + t)),
+                                                       (uint32_t)t, mask)
+                                            : INFINITY;
+                        key_sort<KF>(kv);
+#pragma unroll
+                        for (int t = 0; t < KC; ++t) keys[t] = t < KF ? kv[t] : INFINITY;
+                        st.thr = push_threshold(at<KC>(keys, a.k - 1), M, q);
+#pragma unroll
+                        for (int t = KF; t < 32; ++t) {
+                            const float key = make_key(fmaf(-2.f, v[t], __ldg(a.norms + t)),
+                                                       (uint32_t)t, mask);
+                            if (key < st.thr) {
+                                qk[st.qn * QS + tid] = __float_as_uint(key);
+                                ++st.qn;
+                            }
+                        }
+                        queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
+                    } else {
+                        push32(v, base + 32 * h, keys, st, M);
+                    }
                 }
-                tmem_ld32(col + 32, v);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&t_empty[tb]);
-                push32(v, base, 32, cnt, keys, st, M);
             }
             if (!ok) break;
             // Every MMA of this tile has completed (its last chunk has been

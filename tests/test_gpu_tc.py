@@ -166,3 +166,36 @@ def test_side_stream_and_repeat(esom):
         c = P.project(X, w.boost, w.adjust)
         torch.cuda.synchronize()
     assert torch.equal(a, b) and torch.equal(a, c)
+
+
+@pytest.mark.parametrize("case", ["mixture30_d16", "mixture10_d8", "uniform_d32", "chunked",
+                                  "batch4"])
+def test_split_equals_fused(esom, case):
+    """FP32 screening as two kernels (k-NN, then projection from the
+    neighbours) gives the fused kernel's bits, also across pass boundaries
+    (n above 2^19) and with streamed landmark chunks."""
+    chunk = None
+    if case == "mixture30_d16":
+        w = workloads.mixture30_d16(n=600_000)
+    elif case == "mixture10_d8":
+        w = workloads.mixture10_d8()
+    elif case == "uniform_d32":
+        w = workloads.make("uniform_d32", n=50_000)
+    elif case == "chunked":
+        w = workloads.mixture30_d16(n=30_000)
+        chunk = 200
+    else:
+        p = workloads.batch64()[4]
+        w = workloads.batch_member(p, n=min(p["n"], 20_000))
+    X = torch.from_numpy(w.X).cuda()
+    outs = []
+    with esom.Projector(w.d, w.L, w.k) as P:
+        P.set_landmarks(torch.from_numpy(w.hi).cuda(), torch.from_numpy(w.lo).cuda())
+        if chunk:
+            P.set_landmark_chunk(chunk)
+        for split in (False, True):
+            P.set_split(split)
+            outs.append(P.project(X, w.boost, w.adjust).cpu().numpy())
+        torch.cuda.synchronize()
+        assert P.device_status() == 0
+    assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
