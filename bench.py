@@ -392,8 +392,9 @@ def run_esom(args, world, rank, local):
                                 other: other_stats["rescans"] / max(other_stats["points"], 1)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "algorithmic": "2 * n * (L*d + k^2*d) flops per launch",
+                         "algorithmic": "2 * n * (L*d + k^2*d) flops per step",
                          "peak_from": roof_note,
+                         "frac_of_fp32_alu_peak": achieved / alu_peak,
                          "frac_at_sampled_clock": (achieved / peak * max_mhz / clocks["sm_mhz"])
                          if clocks.get("sm_mhz") else None},
             "clocks": clocks,

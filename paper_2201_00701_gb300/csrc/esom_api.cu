@@ -203,21 +203,40 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
         // Split execution: the k-NN kernel (tensor-core or plain); for a
         // projection, in passes of kTcPass points through the handle's
         // neighbour scratch, each followed by the projection kernel.
+        // Points whose certificate fails go to the handle's fail list (the
+        // count lives in status word 3) and are resolved by the warp-per-point
+        // rescan kernel after the pass; a pass holds at most kTcPass points.
+        unsigned *fail_count = reinterpret_cast<unsigned *>(h->status) + 3;
         auto knn = [&](FusedArgs k, long long cnt) -> cudaError_t {
             k.mode = esom::kKnn;
+            k.fail_list = h->fail_list;
+            k.fail_count = fail_count;
+            cudaError_t r = cudaMemsetAsync(fail_count, 0, sizeof(unsigned), stream);
+            if (r != cudaSuccess) return r;
             if (h->screening) {
                 const long long tiles = (cnt + esom::kTcRows - 1) / esom::kTcRows;
                 long long grid = (long long)h->tc_blocks_per_sm * h->num_sms;
                 if (grid > tiles) grid = tiles;
-                return h->tc->launch(k, (int)grid, h->tc_smem, stream);
+                r = h->tc->launch(k, (int)grid, h->tc_smem, stream);
+            } else {
+                k.ntiles = (cnt + esom::kThreads - 1) / esom::kThreads;
+                long long grid = (long long)h->blocks_per_sm * h->num_sms;
+                if (grid > k.ntiles) grid = k.ntiles;
+                r = h->ops->launch(k, (int)grid, h->smem, stream);
             }
-            k.ntiles = (cnt + esom::kThreads - 1) / esom::kThreads;
-            long long grid = (long long)h->blocks_per_sm * h->num_sms;
-            if (grid > k.ntiles) grid = k.ntiles;
-            return h->ops->launch(k, (int)grid, h->smem, stream);
+            if (r != cudaSuccess) return r;
+            return h->ops->launch_rescan(k, 2 * h->num_sms, stream);
         };
         if (mode == esom::kKnn) {
-            e = knn(a, n);
+            for (long long off = 0; off < n && e == cudaSuccess; off += esom::kTcPass) {
+                const long long cnt = n - off < esom::kTcPass ? n - off : esom::kTcPass;
+                FusedArgs k = a;
+                k.X = points + off * h->d;
+                k.n = cnt;
+                k.idx = idx + off * h->k;
+                k.dist2 = dist2 ? dist2 + off * h->k : nullptr;
+                e = knn(k, cnt);
+            }
         } else {
             for (long long off = 0; off < n && e == cudaSuccess; off += esom::kTcPass) {
                 const long long cnt = n - off < esom::kTcPass ? n - off : esom::kTcPass;
@@ -527,11 +546,14 @@ esom_status prepare_split(esom_ctx *h) {
     if (!h->tc_idx) {
         e = cudaMalloc(&h->tc_idx, (size_t)esom::kTcPass * h->k * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&h->tc_d2, (size_t)esom::kTcPass * h->k * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&h->fail_list, (size_t)esom::kTcPass * sizeof(long long));
         if (e != cudaSuccess) {
             cudaFree(h->tc_idx);
             cudaFree(h->tc_d2);
+            cudaFree(h->fail_list);
             h->tc_idx = nullptr;
             h->tc_d2 = nullptr;
+            h->fail_list = nullptr;
             return fail(ESOM_ENOMEM, "device allocation of the neighbour scratch: %s",
                         cudaGetErrorString(e));
         }
@@ -631,6 +653,7 @@ esom_status esom_destroy(esom_handle h) {
     cudaFree(h->qtab);
     cudaFree(h->tc_idx);
     cudaFree(h->tc_d2);
+    cudaFree(h->fail_list);
     for (int b = 0; b < 2; ++b) {
         cudaFree(h->stage_x[b]);
         cudaFree(h->stage_out[b]);

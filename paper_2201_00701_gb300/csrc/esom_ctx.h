@@ -34,6 +34,7 @@ struct esom_ctx {
     // neighbours of one k-NN pass (kTcPass x k) for the projection kernel
     int *tc_idx = nullptr;
     float *tc_d2 = nullptr;
+    long long *fail_list = nullptr;  // rows whose certificate failed (kTcPass)
     int proj_blocks_per_sm = 0;
     size_t proj_smem = 0;
     // host-buffer pipeline state (created on first use)

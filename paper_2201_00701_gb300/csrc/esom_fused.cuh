@@ -1008,7 +1008,13 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
         float sd[KK];
         int si[KK];
         const bool cert = rerank<D, KC, KK>(xr, keys, Lg, mask, a.L, a.k, M, q, sd, si);
-        if (__builtin_expect(!cert, 0)) {
+        if (__builtin_expect(!cert, 0) && a.fail_list) {
+            // deferred to rescan_kernel
+            if (active) {
+                atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
+                a.fail_list[atomicAdd(a.fail_count, 1u)] = row0 + tid;
+            }
+        } else if (__builtin_expect(!cert, 0)) {
             if (active) atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
             float4 tx[D / 4];
             float tsd[KK];
@@ -1307,6 +1313,78 @@ cudaError_t launch_project(const FusedArgs &a, int grid, size_t smem, cudaStream
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Exact k-NN of the points whose screening certificate failed (deferred by
+// the k-NN kernels to keep their warps on the fast path), one warp per point:
+// FP32 difference-form distances to all L landmarks (dist2_row, the same
+// arithmetic as exact_rescan), each lane keeping the nearest KK of the
+// landmarks j = lane (mod 32), then KK rounds of a warp minimum over the
+// lanes' heads.  Keys are (distance bits << 32) | j: distances are >= 0, so
+// their bit patterns order like the values and ties go to the lower index,
+// as in exact_rescan.
+
+__device__ __forceinline__ unsigned long long umin64(unsigned long long x, unsigned long long y) {
+    return x < y ? x : y;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long x, unsigned long long y) {
+    return x < y ? y : x;
+}
+
+template <int D, int KC>
+__global__ void __launch_bounds__(256) rescan_kernel(const FusedArgs a) {
+    constexpr int KK = KC - 4;
+    const unsigned count = *reinterpret_cast<volatile const unsigned *>(a.fail_count);
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const float4 *Lg = reinterpret_cast<const float4 *>(a.hi);
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (long long)count;
+         w += nwarps) {
+        const long long row = a.fail_list[w];
+        const float4 *xp = reinterpret_cast<const float4 *>(a.X) + row * (D / 4);
+        float4 x[D / 4];
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) x[e] = __ldg(xp + e);
+        unsigned long long best[KK];
+#pragma unroll
+        for (int t = 0; t < KK; ++t) best[t] = ~0ull;
+        for (int j = lane; j < a.L; j += 32) {
+            const float d2 = dist2_row<D>(x, Lg, j);
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
+            if (key < best[KK - 1]) {
+                unsigned long long prev = best[0];
+                best[0] = umin64(key, best[0]);
+#pragma unroll
+                for (int t = 1; t < KK; ++t) {
+                    const unsigned long long cur = best[t];
+                    best[t] = umax64(prev, umin64(key, cur));
+                    prev = cur;
+                }
+            }
+        }
+        for (int r = 0; r < a.k; ++r) {
+            unsigned long long m = best[0];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) m = umin64(m, __shfl_xor_sync(0xffffffffu, m, off));
+            if (best[0] == m) {  // keys are unique: one lane pops its head
+#pragma unroll
+                for (int t = 0; t + 1 < KK; ++t) best[t] = best[t + 1];
+                best[KK - 1] = ~0ull;
+            }
+            if (lane == 0) {
+                a.idx[row * a.k + r] = (int)(unsigned)(m & 0xffffffffu);
+                if (a.dist2) a.dist2[row * a.k + r] = __uint_as_float((unsigned)(m >> 32));
+            }
+        }
+    }
+}
+
+template <int D, int KC>
+cudaError_t launch_rescan(const FusedArgs &a, int grid, cudaStream_t stream) {
+    rescan_kernel<D, KC><<<grid, 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
 // One thread per ordered pair (u, v): the squared distance table of the pair
 // loop, computed by the loop's own pair_q.
 template <int D>
@@ -1358,7 +1436,7 @@ const KernelOps Instance<D, KC>::ops = {
     reinterpret_cast<const void *>(&batch_kernel<D, KC, Instance<D, KC>::kMinBlocks>),
     &launch_batch<D, KC, Instance<D, KC>::kMinBlocks>, &launch_qtab<D>,
     reinterpret_cast<const void *>(&project_kernel<D, KC, Instance<D, KC>::kMinBlocks>),
-    &launch_project<D, KC, Instance<D, KC>::kMinBlocks>};
+    &launch_project<D, KC, Instance<D, KC>::kMinBlocks>, &launch_rescan<D, KC>};
 
 // Table of the list capacities instantiated for each D.
 #define ESOM_DEFINE_D(DV)                                            \

@@ -40,6 +40,11 @@ struct FusedArgs {
     const unsigned char *img;  // tensor-core screening: landmark chunk images
     int tc_chunks;        // ceil(L / kTcN) chunks in img
     const float *qtab;    // L x L squared landmark distances (pair_q values), or null
+    // k-NN mode: when set, a point whose screening certificate fails is not
+    // rescanned in line but appended (row index) to fail_list, counted in
+    // *fail_count; rescan_kernel then finds its neighbours exactly
+    long long *fail_list;
+    unsigned *fail_count;
 };
 
 // Many datasets of one (D, list capacity) in one launch: every block walks a
@@ -69,6 +74,9 @@ struct KernelOps {
     // when a.nchunks == 1 (project_smem_bytes).
     const void *proj_func;
     cudaError_t (*launch_proj)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
+    // Exact k-NN of the rows in a.fail_list (one warp per row), written to
+    // a.idx / a.dist2 like the k-NN kernels do.
+    cudaError_t (*launch_rescan)(const FusedArgs &, int grid, cudaStream_t);
 };
 
 // Returns the instantiation for dimension D and list capacity kc, or nullptr.

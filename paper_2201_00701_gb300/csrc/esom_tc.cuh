@@ -23,11 +23,13 @@
 // product's and the certificate almost never fails.
 //
 // Each selection thread owns one point (one TMEM lane), reads its 64 values
-// of a chunk with one tcgen05.ld, keys them like the plain kernel (value with
-// the landmark index in the low mantissa bits) and keeps the KC smallest.
-// The list is then re-ranked with exact FP32 difference-form distances, and
-// a bound on the TF32 screening error certifies that no landmark outside the
-// list can be among the k nearest; a point that fails is rescanned exactly.
+// of a chunk with two tcgen05.ld, keys them like the plain kernel (value
+// with the landmark index in the low mantissa bits) and keeps the KC
+// smallest.  The list is then re-ranked with exact FP32 difference-form
+// distances, and a bound on the screening error certifies that no landmark
+// outside the list can be among the k nearest; a point that fails is
+// appended to a list that rescan_kernel (one warp per point) then resolves
+// with an exact scan.
 // So the neighbours and their distances are the plain kernel's, bit for
 // bit (and so are the coordinates projected from them); the screening
 // precision only decides how often a point is rescanned.
@@ -462,19 +464,10 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
             float sd[KK];
             int si[KK];
             const bool cert = rerank<D, KC, KK>(xr, keys, Lg, mask, a.L, a.k, M, q, sd, si, xx);
-            if (__builtin_expect(!cert, 0)) {
-                if (active) atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
-                float4 tx[D / 4];
-                float tsd[KK];
-                int tsi[KK];
-#pragma unroll
-                for (int e = 0; e < D / 4; ++e) tx[e] = xr[e];
-                exact_rescan<D, KK>(tx, Lg, a.L, tsd, tsi);
-#pragma unroll
-                for (int t = 0; t < KK; ++t) {
-                    sd[t] = tsd[t];
-                    si[t] = tsi[t];
-                }
+            if (__builtin_expect(!cert, 0) && active) {
+                // deferred: rescan_kernel finds this point's neighbours exactly
+                atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
+                a.fail_list[atomicAdd(a.fail_count, 1u)] = row;
             }
             if (active) {
 #pragma unroll

@@ -58,8 +58,9 @@ def same_as_fp32(esom, w, label, max_rescans=0.02):
     return got
 
 
-@pytest.mark.parametrize("n", [1, 127, 128, 129, 20_000 + 77])
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 20_000 + 77, (1 << 19) + 1000])
 def test_mixture30_d16_equals_fp32(esom, n):
+    """Tile edges, a ragged tail, and two k-NN passes (n above 2^19)."""
     w = workloads.mixture30_d16(n=n)
     same_as_fp32(esom, w, f"mixture30_d16 n={n}")
 
@@ -169,7 +170,7 @@ def test_side_stream_and_repeat(esom):
 
 
 @pytest.mark.parametrize("case", ["mixture30_d16", "mixture10_d8", "uniform_d32", "chunked",
-                                  "batch4"])
+                                  "batch4", "shifted"])
 def test_split_equals_fused(esom, case):
     """FP32 screening as two kernels (k-NN, then projection from the
     neighbours) gives the fused kernel's bits, also across pass boundaries
@@ -184,6 +185,10 @@ def test_split_equals_fused(esom, case):
     elif case == "chunked":
         w = workloads.mixture30_d16(n=30_000)
         chunk = 200
+    elif case == "shifted":  # every point fails its certificate: deferred rescans
+        w = workloads.random_case(np.random.default_rng(11), 4000, 16, 512, 12)
+        w.X = (w.X + 200.0).astype(np.float32)
+        w.hi = (w.hi + 200.0).astype(np.float32)
     else:
         p = workloads.batch64()[4]
         w = workloads.batch_member(p, n=min(p["n"], 20_000))
