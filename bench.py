@@ -33,7 +33,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "mixture30_d16"
-PROFILE = os.path.join(ROOT, "profiles", "fused_kernel_mixture30_d16.txt")
+PROFILES = {"fp32": os.path.join(ROOT, "profiles", "fused_kernel_mixture30_d16.txt"),
+            "tf32": os.path.join(ROOT, "profiles", "tc_knn_kernel_mixture30_d16.txt")}
 
 
 def baseline_metric():
@@ -53,12 +54,13 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+def profile_traffic(screen: str):
+    """DRAM bytes of the dominant kernel in one step, from the committed ncu
+    summary of the screening mode, if it was taken on the current kernel
+    sources."""
     try:
         kv = {}
-        with open(PROFILE) as f:
+        with open(PROFILES[screen]) as f:
             for line in f:
                 if ":" in line and not line.startswith("#"):
                     key, val = line.split(":", 1)
@@ -361,7 +363,7 @@ def run_esom(args, world, rank, local):
             roof_note = (f"n*L*d on TF32 tensor cores at {tf32_peak:.0f} TFLOP/s (half the "
                          f"measured sustained BF16 rate) + n*k^2*d on the FP32 lanes at "
                          f"{alu_peak:.1f} TFLOP/s")
-        traffic = profile_traffic() if args.workload == WORKLOAD else None
+        traffic = profile_traffic(screen) if args.workload == WORKLOAD else None
         line = {
             "metric": baseline_metric(), "value": value, "unit": "points/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
