@@ -314,16 +314,14 @@ __device__ __forceinline__ void screen_block(const float4 (&x)[D / 4], float hxx
 // indices base + j; base is a multiple of 8).  Single landmarks up to the
 // next multiple of 8, then blocks of 8, then the tail; the queue is checked
 // after every block and after each single-step run (at most 7 pushes).
-// Branch-free push: the key is stored at the queue's end, which advances
-// only when the key passes the threshold.  The queue is checked at least
-// every kCheck keys and flushed above kQueue - kCheck, so the stores stay
-// inside it.
 template <int D, int KC>
 __device__ __forceinline__ void push_key(float v, int jg, uint32_t mask, ScanState &st,
                                          uint32_t *qk, int tid) {
     const float key = make_key(v, (uint32_t)jg, mask);
-    qk[st.qn * kThreads + tid] = __float_as_uint(key);
-    st.qn += key < st.thr ? 1 : 0;
+    if (key < st.thr) {
+        qk[st.qn * kThreads + tid] = __float_as_uint(key);
+        ++st.qn;
+    }
 }
 
 template <int D, int KC>

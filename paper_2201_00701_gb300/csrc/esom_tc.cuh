@@ -349,11 +349,9 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
 
         // Keys of 32 values of chunk base (columns h32 .. h32 + 31) into the
         // queue: one FMA for the screening value, the key, the threshold
-        // test and a branch-free push (every key is stored at the queue's
-        // end, which advances only when the key passes).  Padding columns
-        // (beyond L) have NaN norms, so they never pass.  The queue is
-        // flushed after every 16 values when a lane holds more than
-        // kQueue - 17 keys, so the 16 stores of the next run stay inside it.
+        // test and a predicated push.  Padding columns (beyond L) have NaN
+        // norms, so they never pass.  The queue is flushed after every 16
+        // values when a lane may not have room for 16 more.
         auto push32 = [&](const float (&v)[32], int jbase, float (&keys)[KC], ScanState &st,
                           float M) {
             const float4 *N4 = reinterpret_cast<const float4 *>(a.norms + jbase);
@@ -368,12 +366,14 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                     for (int e = 0; e < 4; ++e) {
                         const float key = make_key(fmaf(-2.f, v[hb + jb + e], nn[e]),
                                                    (uint32_t)(jbase + hb + jb + e), mask);
-                        *qp = __float_as_uint(key);
-                        qp += key < st.thr ? QS : 0;
+                        if (key < st.thr) {
+                            *qp = __float_as_uint(key);
+                            qp += QS;
+                        }
                     }
                 }
                 st.qn = (int)((qp - (qk + tid)) / QS);
-                if (__any_sync(0xffffffffu, st.qn > kQueue - 17))
+                if (__any_sync(0xffffffffu, st.qn > kQueue - 16))
                     queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
             }
         };
