@@ -26,8 +26,8 @@
 //     packed with the landmark index into one 32-bit key (index in the low
 //     mantissa bits), kept in a sorted register list of KC = k + spare
 //     entries; keys below the current threshold go to a per-thread queue in
-//     shared memory and are merged in warp-uniform flushes with a min/max
-//     insertion (two instructions a slot, no chain through the list);
+//     shared memory and are merged in warp-uniform flushes, in sorted blocks
+//     of 8 with a bitonic merge network;
 //   * exact re-rank: the listed candidates get their squared distance in the
 //     FP32 difference form, are ordered by (distance, index), and a bound on
 //     the screening error certifies that no landmark outside the list can
@@ -167,21 +167,6 @@ __device__ __forceinline__ float make_key(float value, uint32_t j, uint32_t mask
     return __uint_as_float((__float_as_uint(value) & ~mask) | j);
 }
 
-// Sorted key list: inserting v gives slot t the value
-// max(list[t-1], min(v, list[t])) -- shift when v is smaller than list[t-1],
-// v at its place, unchanged after.  Every slot uses only old values.
-template <int KC>
-__device__ __forceinline__ void key_insert(float (&keys)[KC], float v) {
-    float prev = keys[0];
-    keys[0] = fminf(v, keys[0]);
-#pragma unroll
-    for (int t = 1; t < KC; ++t) {
-        const float cur = keys[t];
-        keys[t] = fmaxf(prev, fminf(v, cur));
-        prev = cur;
-    }
-}
-
 // Batcher's odd-even merge sort network for any N, as a compile-time list of
 // compare-exchange pairs, so that the unrolled loop indexes registers only.
 template <int N>
@@ -275,13 +260,49 @@ struct ScanState {
     float thr;     // push threshold
 };
 
+__host__ __device__ constexpr int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p += p;
+    return p;
+}
+
+// keys (KC, ascending) <- the KC smallest of keys and q (8, ascending): the
+// sequence [keys, +inf padding, q reversed] is bitonic, so one bitonic merge
+// of its power-of-two length sorts it (compare-exchanges with the constant
+// padding and those feeding only positions >= KC fold away).
+template <int KC>
+__device__ __forceinline__ void merge8(float (&keys)[KC], const float (&q)[8]) {
+    constexpr int P = next_pow2(KC + 8);
+    float s[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) s[i] = i < KC ? keys[i] : (i >= P - 8 ? q[P - 1 - i] : INFINITY);
+#pragma unroll
+    for (int len = P / 2; len >= 1; len /= 2)
+#pragma unroll
+        for (int i = 0; i < P; ++i)
+            if ((i & len) == 0) {
+                const float a = s[i], b = s[i + len];
+                s[i] = fminf(a, b);
+                s[i + len] = fmaxf(a, b);
+            }
+#pragma unroll
+    for (int i = 0; i < KC; ++i) keys[i] = s[i];
+}
+
+// Merges every lane's queued keys into its list, in sorted blocks of 8 (a
+// sorting network, then merge8; about half the operations of inserting the
+// keys one by one), and recomputes the push threshold.
 template <int KC, int QS = kThreads>
 __device__ __forceinline__ void queue_flush(float (&keys)[KC], ScanState &st, const uint32_t *qk,
                                             int tid, int k, float M, float q) {
     const int mx = __reduce_max_sync(0xffffffffu, st.qn);
-    for (int i = 0; i < mx; ++i) {
-        const float v = i < st.qn ? __uint_as_float(qk[i * QS + tid]) : INFINITY;
-        key_insert<KC>(keys, v);
+    for (int b = 0; b < mx; b += 8) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            v[i] = b + i < st.qn ? __uint_as_float(qk[(b + i) * QS + tid]) : INFINITY;
+        key_sort<8>(v);
+        merge8<KC>(keys, v);
     }
     st.qn = 0;
     st.thr = push_threshold(at<KC>(keys, k - 1), M, q);
