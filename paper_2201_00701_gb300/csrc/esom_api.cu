@@ -311,7 +311,8 @@ esom_status esom_create(int d, int L, int k, esom_handle *out) {
         return cuda_fail(e, "device query");
     }
     e = cudaMalloc(&h->hi, (size_t)L * d * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&h->lo, (size_t)L * 2 * sizeof(float));
+    // 2-D positions padded to 16 bytes, so they can be bulk-copied whole
+    if (e == cudaSuccess) e = cudaMalloc(&h->lo, ((size_t)L * 2 * sizeof(float) + 15) & ~(size_t)15);
     if (e == cudaSuccess)
         e = cudaMalloc(&h->norms, (size_t)((L + esom::kTcN - 1) / esom::kTcN * esom::kTcN) *
                                       sizeof(float));

@@ -545,14 +545,15 @@ __device__ __forceinline__ PairTerm pair_term(const float4 (&lu)[D / 4], float2 
                                               const float *qrow) {
     const float qq = qrow ? __ldg(qrow + iv)
                           : pair_q<D>(lu, Lg + (size_t)iv * (D / 4), swz(D, iv));
-    const float2 lvt = __ldg(&lo2[iv]);
+    const float2 lvt = lo2[iv];
     const float hx = lvt.x - lut.x, hy = lvt.y - lut.y;
     const float r = fmaf(hx, hx, hy * hy);
     PairTerm t;
     t.ok = qq > 0.f && r > 0.f;
     const float ir = rcp_fast(r);
-    // r^-adjust by the SFU (relative error ~1e-6)
-    const float w = su * sv * exp2f_fast(-adjust * log2f_fast(r));
+    // r^-adjust: 1/r itself for the common adjust = 1, else by the SFU
+    // (relative error ~1e-6)
+    const float w = su * sv * (adjust == 1.f ? ir : exp2f_fast(-adjust * log2f_fast(r)));
     const float wr = w * ir;
     if (PASS == 0) {
         const float Duv = fmaf(0.5f * (du - dv), rcp_fast(qq), 0.5f);
@@ -602,7 +603,7 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
 #pragma unroll
         for (int e = 0; e < D / 4; ++e)
             lu[e] = qrow ? make_float4(0.f, 0.f, 0.f, 0.f) : Lu[e ^ fu];
-        const float2 lut = __ldg(&lo2[iu]);
+        const float2 lut = lo2[iu];
         const float lux = lut.x - l0.x, luy = lut.y - l0.y;  // l_u relative to l_0
 #pragma unroll
         for (int v0 = 1; v0 < KK; v0 += 2) {
@@ -775,12 +776,12 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
     }
 
     // 2-D coordinates relative to the nearest neighbour's.
-    const float2 l0 = __ldg(&lo2[nb_at<QS>(nb, 0)]);
+    const float2 l0 = lo2[nb_at<QS>(nb, 0)];
     float C0 = 0.f, C1 = 0.f, Ssum = 0.f, M0 = 0.f, M1 = 0.f;
 #pragma unroll
     for (int t = 0; t < KK; ++t)
         if (t < m) {
-            const float2 lt = __ldg(&lo2[nb_at<QS>(nb, t)]);
+            const float2 lt = lo2[nb_at<QS>(nb, t)];
             const float px = lt.x - l0.x, py = lt.y - l0.y;
             C0 = fmaf(ss[t], px, C0);
             C1 = fmaf(ss[t], py, C1);
@@ -1280,7 +1281,8 @@ __global__ void __launch_bounds__(kThreads, MINB) project_kernel(const FusedArgs
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     float *sL = reinterpret_cast<float *>(smem + kBarrierBytes);
     const bool resident = a.nchunks == 1;
-    uint32_t *qk = reinterpret_cast<uint32_t *>(sL + (resident ? (size_t)a.L * D : 0));
+    float2 *sLo = reinterpret_cast<float2 *>(sL + (resident ? (size_t)a.L * D : 0));
+    uint32_t *qk = reinterpret_cast<uint32_t *>(sLo + (resident ? (a.L + 1) & ~1 : 0));
     const int tid = threadIdx.x;
     const long long ntiles = (a.n + kThreads - 1) / kThreads;
     if ((long long)blockIdx.x >= ntiles) return;
@@ -1292,8 +1294,11 @@ __global__ void __launch_bounds__(kThreads, MINB) project_kernel(const FusedArgs
         __syncthreads();
         if (tid == 0) {
             const uint32_t bytes = (uint32_t)((size_t)a.L * D * sizeof(float));
-            mbar_expect_tx(bar, bytes);
+            // (the handle's 2-D position buffer is padded to 16 bytes)
+            const uint32_t lbytes = (uint32_t)(((size_t)a.L * 2 * sizeof(float) + 15) & ~(size_t)15);
+            mbar_expect_tx(bar, bytes + lbytes);
             copy_pieces(sL, a.hi, bytes, bar);
+            copy_pieces(sLo, a.lo, lbytes, bar);
         }
         const bool ok = mbar_wait(bar, 0);
         if (!__syncthreads_and(ok)) {
@@ -1307,18 +1312,40 @@ __global__ void __launch_bounds__(kThreads, MINB) project_kernel(const FusedArgs
     }
     const float4 *Lg = resident ? reinterpret_cast<const float4 *>(sL)
                                 : reinterpret_cast<const float4 *>(a.hi);
-    const float2 *lo2 = reinterpret_cast<const float2 *>(a.lo);
+    const float2 *lo2 = resident ? sLo : reinterpret_cast<const float2 *>(a.lo);
     uint32_t *nb = qk + tid;
+    const bool vec = (a.k & 3) == 0;  // rows of k entries are 16-byte aligned
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long row = tile * kThreads + tid;
         const bool active = row < a.n;
         float sd[KK];
         int si[KK];
+        if (vec) {
+            const int4 *ip = reinterpret_cast<const int4 *>(a.idx + (active ? row : 0) * a.k);
+            const float4 *dp = reinterpret_cast<const float4 *>(a.dist2 + (active ? row : 0) * a.k);
 #pragma unroll
-        for (int t = 0; t < KK; ++t) {
-            const bool have = active && t < a.k;
-            si[t] = have ? min(max(a.idx[row * a.k + t], 0), a.L - 1) : 0;
-            sd[t] = have ? a.dist2[row * a.k + t] : 0.f;
+            for (int t = 0; t < KK; t += 4) {
+                const bool have = active && t < a.k;
+                const int4 iv = have ? ip[t / 4] : make_int4(0, 0, 0, 0);
+                const float4 dv = have ? dp[t / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                si[t] = iv.x;
+                si[t + 1] = iv.y;
+                si[t + 2] = iv.z;
+                si[t + 3] = iv.w;
+                sd[t] = dv.x;
+                sd[t + 1] = dv.y;
+                sd[t + 2] = dv.z;
+                sd[t + 3] = dv.w;
+            }
+#pragma unroll
+            for (int t = 0; t < KK; ++t) si[t] = min(max(si[t], 0), a.L - 1);
+        } else {
+#pragma unroll
+            for (int t = 0; t < KK; ++t) {
+                const bool have = active && t < a.k;
+                si[t] = have ? min(max(a.idx[row * a.k + t], 0), a.L - 1) : 0;
+                sd[t] = have ? a.dist2[row * a.k + t] : 0.f;
+            }
         }
 #pragma unroll
         for (int t = 0; t < KK; t += 2)

@@ -70,8 +70,8 @@ struct KernelOps {
     // exactly the values the loop would compute.
     cudaError_t (*launch_qtab)(const float *hi, int L, float *qtab, cudaStream_t);
     // Projection from given neighbours (FusedArgs idx / dist2, k per point):
-    // steps 2-4 of the fused kernel, landmark rows resident in shared memory
-    // when a.nchunks == 1 (project_smem_bytes).
+    // steps 2-4 of the fused kernel, landmark rows and 2-D positions
+    // resident in shared memory when a.nchunks == 1 (project_smem_bytes).
     const void *proj_func;
     cudaError_t (*launch_proj)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
     // Exact k-NN of the rows in a.fail_list (one warp per row), written to
@@ -145,7 +145,8 @@ struct TcOps {
 
 
 inline size_t project_smem_bytes(int D, int L, bool resident) {
-    return kBarrierBytes + (resident ? (size_t)L * D * sizeof(float) : 0) +
+    return kBarrierBytes +
+           (resident ? (size_t)L * D * sizeof(float) + (size_t)((L + 1) & ~1) * 8 : 0) +
            (size_t)kQueue * kThreads * sizeof(unsigned);
 }
 
