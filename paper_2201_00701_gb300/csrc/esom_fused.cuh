@@ -1274,46 +1274,13 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchArgs B
 // memory once per block when they fit (a.nchunks == 1), else read from
 // global memory; the pair loop uses the distance table when a.qtab is set.
 
-template <int D, int KC, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) project_kernel(const FusedArgs a) {
-    constexpr int KK = KC - 4;
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    float *sL = reinterpret_cast<float *>(smem + kBarrierBytes);
-    const bool resident = a.nchunks == 1;
-    float2 *sLo = reinterpret_cast<float2 *>(sL + (resident ? (size_t)a.L * D : 0));
-    uint32_t *qk = reinterpret_cast<uint32_t *>(sLo + (resident ? (a.L + 1) & ~1 : 0));
-    const int tid = threadIdx.x;
+// The projection loop over this block's tiles.  Instantiated once with the
+// rows and 2-D positions in shared memory and once in global memory, so the
+// compiler knows each pointer's space (shared loads instead of generic ones).
+template <int D, int KK>
+__device__ __forceinline__ void project_tiles(const FusedArgs &a, const float4 *Lg,
+                                              const float2 *lo2, uint32_t *nb, int tid) {
     const long long ntiles = (a.n + kThreads - 1) / kThreads;
-    if ((long long)blockIdx.x >= ntiles) return;
-    if (resident) {
-        if (tid == 0) {
-            mbar_init(bar, 1);
-            fence_mbar_init();
-        }
-        __syncthreads();
-        if (tid == 0) {
-            const uint32_t bytes = (uint32_t)((size_t)a.L * D * sizeof(float));
-            // (the handle's 2-D position buffer is padded to 16 bytes)
-            const uint32_t lbytes = (uint32_t)(((size_t)a.L * 2 * sizeof(float) + 15) & ~(size_t)15);
-            mbar_expect_tx(bar, bytes + lbytes);
-            copy_pieces(sL, a.hi, bytes, bar);
-            copy_pieces(sLo, a.lo, lbytes, bar);
-        }
-        const bool ok = mbar_wait(bar, 0);
-        if (!__syncthreads_and(ok)) {
-            // the copy did not land in time: report, drain it (bounded), leave
-            if (tid == 0) {
-                atomicOr(a.status, kErrWaitTimeout);
-                mbar_wait(bar, 0);
-            }
-            return;
-        }
-    }
-    const float4 *Lg = resident ? reinterpret_cast<const float4 *>(sL)
-                                : reinterpret_cast<const float4 *>(a.hi);
-    const float2 *lo2 = resident ? sLo : reinterpret_cast<const float2 *>(a.lo);
-    uint32_t *nb = qk + tid;
     const bool vec = (a.k & 3) == 0;  // rows of k entries are 16-byte aligned
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const long long row = tile * kThreads + tid;
@@ -1352,6 +1319,48 @@ __global__ void __launch_bounds__(kThreads, MINB) project_kernel(const FusedArgs
             nb[(t >> 1) * kThreads] = (uint32_t)si[t] | ((uint32_t)si[t + 1] << 16);
         const float2 p = project_point<D, KK>(sd, nb, Lg, lo2, a);
         if (active) reinterpret_cast<float2 *>(a.out)[row] = p;
+    }
+}
+
+template <int D, int KC, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) project_kernel(const FusedArgs a) {
+    constexpr int KK = KC - 4;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    float *sL = reinterpret_cast<float *>(smem + kBarrierBytes);
+    const bool resident = a.nchunks == 1;
+    float2 *sLo = reinterpret_cast<float2 *>(sL + (resident ? (size_t)a.L * D : 0));
+    uint32_t *qk = reinterpret_cast<uint32_t *>(sLo + (resident ? (a.L + 1) & ~1 : 0));
+    const int tid = threadIdx.x;
+    const long long ntiles = (a.n + kThreads - 1) / kThreads;
+    if ((long long)blockIdx.x >= ntiles) return;
+    if (resident) {
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)((size_t)a.L * D * sizeof(float));
+            // (the handle's 2-D position buffer is padded to 16 bytes)
+            const uint32_t lbytes = (uint32_t)(((size_t)a.L * 2 * sizeof(float) + 15) & ~(size_t)15);
+            mbar_expect_tx(bar, bytes + lbytes);
+            copy_pieces(sL, a.hi, bytes, bar);
+            copy_pieces(sLo, a.lo, lbytes, bar);
+        }
+        const bool ok = mbar_wait(bar, 0);
+        if (!__syncthreads_and(ok)) {
+            // the copy did not land in time: report, drain it (bounded), leave
+            if (tid == 0) {
+                atomicOr(a.status, kErrWaitTimeout);
+                mbar_wait(bar, 0);
+            }
+            return;
+        }
+        project_tiles<D, KK>(a, reinterpret_cast<const float4 *>(sL), sLo, qk + tid, tid);
+    } else {
+        project_tiles<D, KK>(a, reinterpret_cast<const float4 *>(a.hi),
+                             reinterpret_cast<const float2 *>(a.lo), qk + tid, tid);
     }
 }
 
