@@ -155,7 +155,7 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_baseline(w, budget_s=10.0, chunk=2000, max_points=200_000):
+def cpu_baseline(w, budget_s=10.0, chunk=2000, max_points=1_000_000):
     """The oracle, as it stands, on the host cores: points/s over the first
     points of the workload, processed in chunks until the time budget."""
     import oracle
