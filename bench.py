@@ -228,35 +228,22 @@ def run_esom(args, world, rank, local):
     n, d, L, k = w.n, w.d, w.L, w.k
     P = binding.Projector(d, L, k)
     P.set_landmarks(torch.from_numpy(w.hi).to(dev), torch.from_numpy(w.lo).to(dev))
-    modes = {"fp32": binding.ESOM_SCREEN_FP32, "tf32": binding.ESOM_SCREEN_TF32}
     X = torch.from_numpy(w.X).to(dev)
     out = torch.empty((n, 2), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    screen = args.screen
+    plans = {"fused": binding.ESOM_PLAN_FUSED, "split": binding.ESOM_PLAN_SPLIT,
+             "tf32": binding.ESOM_PLAN_TF32}
+    screen = {"fp32": "fused", "tf32": "tf32"}.get(args.screen, args.screen)
     if screen == "auto":
-        # both modes give the same bits; keep the faster on this workload
-        best = None
-        for name in ("fp32", "tf32"):
-            P.set_screening(modes[name])
-            ts = []
-            for i in range(6):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                P.project(X, w.boost, w.adjust, out=out)
-                e1.record(stream)
-                e1.synchronize()
-                if i >= 2:
-                    ts.append(e0.elapsed_time(e1))
-            if best is None or min(ts) < best[1]:
-                best = (name, min(ts))
-        screen = best[0]
+        # the library's autotuner times the three plans (same bits) on these
+        # points and keeps the fastest
+        screen = binding.PLAN_NAMES[P.tune(X, w.boost, w.adjust)]
         if world > 1:  # every rank uses rank 0's choice
-            t = torch.tensor([1 if screen == "tf32" else 0], device=dev)
+            t = torch.tensor([plans[screen]], device=dev)
             dist.broadcast(t, 0)
-            screen = "tf32" if int(t[0]) else "fp32"
-    P.set_screening(modes[screen])
+            screen = binding.PLAN_NAMES[int(t[0])]
+    P.set_plan(plans[screen])
     cfg = P.config()
 
     for _ in range(args.warmup):
@@ -293,21 +280,22 @@ def run_esom(args, world, rank, local):
         raise RuntimeError("device status flag raised in the timed region")
     main_stats = P.stats(reset=True)
 
-    # the other screening mode on the same buffers (same results, bit for bit)
-    other = "fp32" if screen == "tf32" else "tf32"
-    P.set_screening(modes[other])
-    other_ms = []
-    for i in range(args.warmup + min(args.steps, 20)):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        P.project(X, w.boost, w.adjust, out=out)
-        e1.record(stream)
-        e1.synchronize()
-        if i >= args.warmup:
-            other_ms.append(e0.elapsed_time(e1))
-    other_stats = P.stats(reset=True)
-    P.set_screening(modes[screen])
+    # the other plans on the same buffers (same results, bit for bit)
+    others = {}
+    for other in [p for p in plans if p != screen]:
+        P.set_plan(plans[other])
+        other_ms = []
+        for i in range(args.warmup + min(args.steps, 20)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.project(X, w.boost, w.adjust, out=out)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= args.warmup:
+                other_ms.append(e0.elapsed_time(e1))
+        others[other] = (float(np.median(other_ms)), P.stats(reset=True))
+    P.set_plan(plans[screen])
 
     # the k-NN step alone (same kernel, no projection phase): splits the step
     # time into k-NN and scores + pair sums + solve
@@ -363,7 +351,8 @@ def run_esom(args, world, rank, local):
             roof_note = (f"n*L*d on TF32 tensor cores at {tf32_peak:.0f} TFLOP/s (half the "
                          f"measured sustained BF16 rate) + n*k^2*d on the FP32 lanes at "
                          f"{alu_peak:.1f} TFLOP/s")
-        traffic = profile_traffic(screen) if args.workload == WORKLOAD else None
+        traffic = (profile_traffic("tf32" if screen == "tf32" else "fp32")
+                   if args.workload == WORKLOAD and screen != "split" else None)
         line = {
             "metric": baseline_metric(), "value": value, "unit": "points/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -371,10 +360,13 @@ def run_esom(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "d": d, "L": L, "k": k,
                        "boost": w.boost, "adjust": w.adjust,
-                       "path": ("tensor-core (TF32) screened k-NN + exact FP32 re-rank, fused "
-                                "projection" if screen == "tf32" else
-                                "FP32 screened k-NN + exact re-rank, fused projection"),
-                       "screening": screen,
+                       "path": {"tf32": "tensor-core (split TF32) screened k-NN kernel, exact "
+                                        "FP32 re-rank, projection kernel",
+                                "split": "FP32 screened k-NN kernel, exact re-rank, projection "
+                                         "kernel",
+                                "fused": "one fused FP32 kernel: screened k-NN, exact re-rank, "
+                                         "projection"}[screen],
+                       "plan": screen,
                        "parallelism": f"dp{world} (points sharded, no collective)",
                        "l2": "flushed between steps by an untimed 256 MiB write",
                        "launch": {key: cfg[key] for key in ("threads_per_block",
@@ -388,10 +380,11 @@ def run_esom(args, world, rank, local):
                           "projection_share": 1.0 - float(np.median(knn_ms))
                           / float(np.median(step_ms))},
             "gpu_launches": args.steps,
-            "screening_paths_ms": {screen: float(np.median(step_ms)),
-                                   other: float(np.median(other_ms))},
+            "plans_ms": {screen: float(np.median(step_ms)),
+                         **{o: v[0] for o, v in others.items()}},
             "rescan_fraction": {screen: main_stats["rescans"] / max(main_stats["points"], 1),
-                                other: other_stats["rescans"] / max(other_stats["points"], 1)},
+                                **{o: v[1]["rescans"] / max(v[1]["points"], 1)
+                                   for o, v in others.items()}},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "algorithmic": "2 * n * (L*d + k^2*d) flops per step",
@@ -502,9 +495,9 @@ def run_serve(args):
     params = workloads.serve8(n_scale=args.serve_scale)
     srv = binding.Server(int(args.serve_budget_gb * (1 << 30)), args.serve_inflight)
     srv.set_coalescing(args.serve_coalesce)
-    screen = "tf32" if args.screen == "auto" else args.screen
-    srv.set_screening({"fp32": binding.ESOM_SCREEN_FP32,
-                       "tf32": binding.ESOM_SCREEN_TF32}[screen])
+    screen = {"fused": "fp32", "split": "fp32"}.get(args.screen, args.screen)
+    srv.set_screening({"fp32": binding.ESOM_SCREEN_FP32, "tf32": binding.ESOM_SCREEN_TF32,
+                       "auto": binding.ESOM_SCREEN_AUTO}[screen])
     sids, sizes = [], {}
     for p in params:
         w = workloads.serve_member(p)
@@ -592,7 +585,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="esom", choices=["esom", "reference"])
     ap.add_argument("--n", type=int, default=0, help="points (default: the workload's n)")
-    ap.add_argument("--screen", default="auto", choices=["auto", "fp32", "tf32"])
+    ap.add_argument("--screen", default="auto",
+                    choices=["auto", "fp32", "tf32", "fused", "split"],
+                    help="execution plan: auto (library autotuner), fused (= fp32), split, tf32")
     ap.add_argument("--ref-points", type=int, default=4000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -147,6 +147,7 @@ typedef struct {
     int screening;              /* ESOM_SCREEN_* in effect (the other fields then
                                    describe the tensor-core launch: 160 threads,
                                    128 points a tile, 64-landmark chunks) */
+    int plan;                   /* ESOM_PLAN_* of esom_project */
 } esom_config;
 
 esom_status esom_get_config(esom_handle h, esom_config *cfg);
@@ -190,6 +191,22 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream);
  * scratch is shared).  Tensor-core screening always runs split.
  * Errors: ESOM_ENOMEM, ESOM_EUNSUPPORTED, ESOM_ECUDA. */
 esom_status esom_set_split(esom_handle h, int on);
+
+/* Execution plans of esom_project: one fused FP32 kernel, FP32 k-NN kernel +
+ * projection kernel, tensor-core k-NN + projection kernel.  All give the
+ * same bits; which is fastest depends on d, L and k (tensor cores pay at
+ * large L, the split at small L). */
+#define ESOM_PLAN_FUSED 0
+#define ESOM_PLAN_SPLIT 1
+#define ESOM_PLAN_TF32 2
+/* Autotuner: times each plan on the first min(n, 2^19) of `points` (device,
+ * n x d) three times on `stream`, writing their coordinates to `out`
+ * (n x 2 device), keeps the fastest for the handle (as if set with
+ * esom_set_screening / esom_set_split) and stores it in *plan (nullable).
+ * Synchronises the stream.  Plans that cannot run here are skipped.
+ * Errors: those of esom_project; ESOM_ECUDA if no plan ran. */
+esom_status esom_tune(esom_handle h, const float *points, int64_t n, float *out, float boost,
+                      float adjust, esom_stream_t stream, int *plan);
 
 /* ---------------------------------------------------------------------------
  * Batched projection: many datasets of uneven n, d and L through one plan.
@@ -315,10 +332,13 @@ esom_status esom_server_submit(esom_server s, int session, double arrival);
  * (an interactive view shows the newest one).  Keeps latency bounded when
  * frames arrive faster than the GPU projects them. */
 esom_status esom_server_set_coalescing(esom_server s, int on);
-/* Screening mode (ESOM_SCREEN_*) of the handles of sessions added from now
- * on; only before the first esom_server_add_session (ESOM_EINVAL after).
- * Results are the same in either mode; TF32 adds the landmark images to each
- * session's footprint. */
+/* Screening of the handles of sessions added from now on: ESOM_SCREEN_FP32,
+ * ESOM_SCREEN_TF32, or ESOM_SCREEN_AUTO (each session's handle is tuned with
+ * esom_tune on its own points when it is admitted); only before the first
+ * esom_server_add_session (ESOM_EINVAL after).  Results are the same in any
+ * mode; TF32 and AUTO add the landmark images and the neighbour scratch to
+ * each session's footprint. */
+#define ESOM_SCREEN_AUTO 2
 esom_status esom_server_set_screening(esom_server s, int mode);
 /* Collects finished frames (up to max) and starts queued ones in free
  * slots; wait_all != 0 blocks until every queued frame has finished (or

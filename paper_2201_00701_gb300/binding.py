@@ -26,6 +26,11 @@ ESOM_EUNSUPPORTED = -6
 ESOM_EDEVICE = -7
 ESOM_SCREEN_FP32 = 0
 ESOM_SCREEN_TF32 = 1
+ESOM_SCREEN_AUTO = 2
+ESOM_PLAN_FUSED = 0
+ESOM_PLAN_SPLIT = 1
+ESOM_PLAN_TF32 = 2
+PLAN_NAMES = {ESOM_PLAN_FUSED: "fused", ESOM_PLAN_SPLIT: "split", ESOM_PLAN_TF32: "tf32"}
 
 HEADER = os.path.join(_build.INCLUDE, "esom.h")
 
@@ -61,7 +66,7 @@ class FrameDone(ctypes.Structure):
 class _Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("d", "L", "k", "kc", "threads_per_block", "blocks_per_sm", "num_sms",
-                 "landmark_chunk", "landmark_chunks", "shared_bytes", "screening")]
+                 "landmark_chunk", "landmark_chunks", "shared_bytes", "screening", "plan")]
 
 
 _lib = None
@@ -98,6 +103,7 @@ def load(build_if_missing: bool = False):
         "esom_get_stats": ([P, P, ctypes.POINTER(_Stats), I], I),
         "esom_set_screening": ([P, I, P], I),
         "esom_set_split": ([P, I], I),
+        "esom_tune": ([P, P, I64, P, F, F, P, ctypes.POINTER(I)], I),
         "esom_batch_create": ([ctypes.POINTER(BatchItem), I, I, ctypes.POINTER(P)], I),
         "esom_batch_run": ([P, P], I),
         "esom_batch_run_graph": ([P, P], I),
@@ -197,6 +203,14 @@ def esom_set_screening(h, mode: int, stream: int = 0) -> int:
 def esom_set_split(h, on: bool) -> int:
     """Two kernels (k-NN, then projection from neighbours) instead of one."""
     return load().esom_set_split(h, int(on))
+
+
+def esom_tune(h, points_ptr: int, n: int, out_ptr: int, boost: float, adjust: float,
+              stream: int = 0):
+    """Returns (status, plan): ESOM_PLAN_FUSED / _SPLIT / _TF32, now set."""
+    plan = ctypes.c_int(-1)
+    st = load().esom_tune(h, points_ptr, n, out_ptr, boost, adjust, stream, ctypes.byref(plan))
+    return st, plan.value
 
 
 def esom_project_noalloc(points_ptr: int, n: int, hi_ptr: int, lo_ptr: int, d: int, L: int,
@@ -403,6 +417,21 @@ class Projector:
 
     def set_split(self, on: bool):
         check(esom_set_split(self.h, on))
+
+    def set_plan(self, plan: int):
+        """ESOM_PLAN_FUSED, ESOM_PLAN_SPLIT or ESOM_PLAN_TF32."""
+        self.set_screening(ESOM_SCREEN_TF32 if plan == ESOM_PLAN_TF32 else ESOM_SCREEN_FP32)
+        self.set_split(plan == ESOM_PLAN_SPLIT)
+
+    def tune(self, X, boost: float = 1.0, adjust: float = 1.0) -> int:
+        """Times the execution plans on X and keeps the fastest; returns it."""
+        X = self._points(X)
+        import torch
+        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=X.device)
+        st, plan = esom_tune(self.h, X.data_ptr(), X.shape[0], out.data_ptr(), boost, adjust,
+                             self._stream())
+        check(st)
+        return plan
 
     def set_landmark_chunk(self, chunk: int):
         check(esom_set_landmark_chunk(self.h, chunk))

@@ -518,6 +518,7 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg) {
     cfg->landmark_chunks = h->nchunks;
     cfg->shared_bytes = (int)h->smem;
     cfg->screening = h->screening;
+    cfg->plan = h->screening ? ESOM_PLAN_TF32 : (h->split ? ESOM_PLAN_SPLIT : ESOM_PLAN_FUSED);
     if (h->screening) {
         // the tensor-core k-NN kernel (the projection kernel that follows it
         // uses 256 threads and the landmark rows of the plain kernel)
@@ -578,6 +579,57 @@ esom_status esom_set_split(esom_handle h, int on) {
     }
     h->split = on ? 1 : 0;
     return ESOM_OK;
+}
+
+esom_status esom_tune(esom_handle h, const float *points, int64_t n, float *out, float boost,
+                      float adjust, esom_stream_t stream, int *plan) {
+    esom_status s = check_common(h, points, n);
+    if (s != ESOM_OK) return s;
+    if (n < 1 || !out) return fail(ESOM_EINVAL, "esom_tune needs n >= 1 points and an output");
+    const long long m = n < esom::kTcPass ? n : esom::kTcPass;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    const int old_screening = h->screening, old_split = h->split;
+    int best = -1;
+    float best_ms = 0.f;
+    for (int p = ESOM_PLAN_FUSED; p <= ESOM_PLAN_TF32; ++p) {
+        s = p == ESOM_PLAN_TF32 ? esom_set_screening(h, ESOM_SCREEN_TF32, stream)
+                                : esom_set_screening(h, ESOM_SCREEN_FP32, stream);
+        if (s == ESOM_OK) s = esom_set_split(h, p == ESOM_PLAN_SPLIT);
+        if (s != ESOM_OK) continue;  // plan unavailable here (e.g. no tensor-core kernel)
+        float total = 0.f;
+        for (int r = 0; r < 3 && s == ESOM_OK; ++r) {
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) s = esom_project(h, points, m, out, boost, adjust, stream);
+            if (s == ESOM_OK && e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (s == ESOM_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (s == ESOM_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) s = cuda_fail(e, "tuning run");
+            if (r > 0) total += ms;  // the first run warms up
+        }
+        if (s == ESOM_OK && (best < 0 || total < best_ms)) {
+            best = p;
+            best_ms = total;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best < 0) {
+        esom_set_screening(h, old_screening, stream);
+        esom_set_split(h, old_split);
+        return fail(ESOM_ECUDA, "no execution plan ran");
+    }
+    s = esom_set_screening(h, best == ESOM_PLAN_TF32 ? ESOM_SCREEN_TF32 : ESOM_SCREEN_FP32, stream);
+    if (s == ESOM_OK) s = esom_set_split(h, best == ESOM_PLAN_SPLIT);
+    if (s == ESOM_OK && plan) *plan = best;
+    return s;
 }
 
 esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {

@@ -138,6 +138,7 @@ struct Session {
     std::deque<Frame> queue;
     bool inflight = false;
     std::vector<Frame> current;  // frames the work in flight completes
+    int plan = -1;               // ESOM_PLAN_* chosen by esom_tune (automatic screening)
     std::deque<esom_frame_done> finished;  // completed, not yet reported
     uint64_t submitted = 0, completed = 0;
 };
@@ -280,7 +281,7 @@ double esom_server_now(esom_server s) { return s ? host_now(s) : 0.0; }
 
 esom_status esom_server_set_screening(esom_server s, int mode) {
     if (!s) return sfail(ESOM_EINVAL, "null server");
-    if (mode != ESOM_SCREEN_FP32 && mode != ESOM_SCREEN_TF32)
+    if (mode != ESOM_SCREEN_FP32 && mode != ESOM_SCREEN_TF32 && mode != ESOM_SCREEN_AUTO)
         return sfail(ESOM_EINVAL, "unknown screening mode");
     std::lock_guard<std::mutex> lock(s->mu);
     if (!s->sessions.empty()) return sfail(ESOM_EINVAL, "set the screening mode before adding sessions");
@@ -309,7 +310,7 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
     // minibatch k-NN indices
     const size_t qtab = d.L <= esom::kQtabMaxL ? (size_t)d.L * d.L * 4 : 0;
     // tensor-core screening: landmark images and the neighbour scratch
-    const size_t img = s->screening == ESOM_SCREEN_TF32
+    const size_t img = s->screening != ESOM_SCREEN_FP32
                            ? (size_t)((d.L + esom::kTcN - 1) / esom::kTcN) * esom::tc_chunk_bytes(d.d) +
                                  (size_t)esom::kTcPass * d.k * 8
                            : 0;
@@ -323,8 +324,8 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
     ss->desc = d;
     ss->bytes = bytes;
     esom_status r = esom_create(d.d, d.L, d.k, &ss->h);
-    if (r == ESOM_OK && s->screening != ESOM_SCREEN_FP32)
-        r = esom_set_screening(ss->h, s->screening, nullptr);
+    if (r == ESOM_OK && s->screening == ESOM_SCREEN_TF32)
+        r = esom_set_screening(ss->h, ESOM_SCREEN_TF32, nullptr);
     cudaError_t e = cudaSuccess;
     if (r == ESOM_OK) {
         e = cudaMalloc(&ss->points, (size_t)d.n * d.d * 4);
@@ -344,6 +345,9 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
             r = esom_set_landmarks(ss->h, ss->hi, ss->lo, reinterpret_cast<esom_stream_t>(ss->stream));
         }
         if (e == cudaSuccess && r == ESOM_OK) e = cudaStreamSynchronize(ss->stream);
+        if (e == cudaSuccess && r == ESOM_OK && s->screening == ESOM_SCREEN_AUTO)
+            r = esom_tune(ss->h, ss->points, d.n, ss->out, d.boost, d.adjust,
+                          reinterpret_cast<esom_stream_t>(ss->stream), &ss->plan);
     }
     if (r != ESOM_OK || e != cudaSuccess) {
         free_session(ss);

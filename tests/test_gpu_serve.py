@@ -317,3 +317,24 @@ def test_server_tf32_sessions_equal_fp32(esom):
             with pytest.raises(esom.EsomError):
                 srv.set_screening(esom.ESOM_SCREEN_FP32)  # sessions exist already
     assert torch.equal(outs[0], outs[1])
+
+
+def test_server_auto_screening_equals_fp32(esom):
+    """Sessions tuned automatically at admission give the FP32 sessions' bits."""
+    ps = workloads.serve8(n_scale=0.01)[:2]
+    outs = []
+    for mode in (esom.ESOM_SCREEN_FP32, esom.ESOM_SCREEN_AUTO):
+        with esom.Server(1 << 30, 2) as srv:
+            srv.set_screening(mode)
+            sids = []
+            for p in ps:
+                w, X, h, l = _session_arrays(p)
+                sids.append(srv.add_session(X, h, l, w.k, w.boost, w.adjust, p["alpha"],
+                                            p["sigma"], minibatch=p["minibatch"], seed=p["seed"]))
+            for _ in range(2):
+                for s in sids:
+                    srv.submit(s)
+            srv.poll(wait_all=True)
+            outs.append([srv.output(s)[0] for s in sids])
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)

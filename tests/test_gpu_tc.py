@@ -204,3 +204,24 @@ def test_split_equals_fused(esom, case):
         torch.cuda.synchronize()
         assert P.device_status() == 0
     assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
+
+
+@pytest.mark.parametrize("name", ["mixture30_d16", "uniform_d16"])
+def test_tune_picks_a_plan_with_the_same_bits(esom, name):
+    """esom_tune times the fused, split and tensor-core plans on the points,
+    keeps the fastest, and every plan gives the same coordinates."""
+    w = workloads.make(name, n=200_000)
+    X = torch.from_numpy(w.X).cuda()
+    with esom.Projector(w.d, w.L, w.k) as P:
+        P.set_landmarks(torch.from_numpy(w.hi).cuda(), torch.from_numpy(w.lo).cuda())
+        outs = {}
+        for plan in (esom.ESOM_PLAN_FUSED, esom.ESOM_PLAN_SPLIT, esom.ESOM_PLAN_TF32):
+            P.set_plan(plan)
+            assert P.config()["plan"] == plan
+            outs[plan] = P.project(X, w.boost, w.adjust).cpu().numpy()
+        chosen = P.tune(X, w.boost, w.adjust)
+        assert chosen in outs and P.config()["plan"] == chosen
+        got = P.project(X, w.boost, w.adjust).cpu().numpy()
+        print("TUNE", name, esom.PLAN_NAMES[chosen])
+    for o in outs.values():
+        assert np.array_equal(o.view(np.uint32), got.view(np.uint32))
