@@ -535,16 +535,12 @@ __device__ __forceinline__ float pair_q(const float4 (&lu)[D / 4], const float4 
     return (q0 + q1) + (q2 + q3);
 }
 
-// qrow: row u of the squared-distance table, or null (then q is computed
-// from the rows).
+// qq = |L_v - L_u|^2 (from the distance table or pair_q).
 template <int D, int PASS>
-__device__ __forceinline__ PairTerm pair_term(const float4 (&lu)[D / 4], float2 lut, float lux,
-                                              float luy, float su, float du, int iv, float sv,
-                                              float dv, const float4 *Lg, const float2 *lo2,
-                                              float adjust, float nx, float ny,
-                                              const float *qrow) {
-    const float qq = qrow ? __ldg(qrow + iv)
-                          : pair_q<D>(lu, Lg + (size_t)iv * (D / 4), swz(D, iv));
+__device__ __forceinline__ PairTerm pair_term(float2 lut, float lux, float luy, float su,
+                                              float du, int iv, float sv, float dv, float qq,
+                                              const float2 *lo2, float adjust, float nx,
+                                              float ny) {
     const float2 lvt = lo2[iv];
     const float hx = lvt.x - lut.x, hy = lvt.y - lut.y;
     const float r = fmaf(hx, hx, hy * hy);
@@ -580,7 +576,10 @@ __device__ __forceinline__ PairTerm pair_term(const float4 (&lu)[D / 4], float2 
 // <X - L_u, L_v - L_u> = (|X - L_u|^2 + |L_v - L_u|^2 - |X - L_v|^2) / 2.
 // The v loop runs in groups of two pairs with independent chains; pairs
 // outside u < v < m inside a group are masked by selects.
-template <int D, int KK, int PASS, int QS = kThreads>
+// PF: gather this u's table entries up front (the projection kernel, which
+// always has the table); else each pair reads its entry, or computes it
+// from the rows when there is no table.
+template <int D, int KK, int PASS, int QS = kThreads, bool PF = false>
 __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t *nb,
                                           const float (&ss)[KK], int m, const float4 *Lg,
                                           const float2 *lo2, float2 l0, const FusedArgs &a,
@@ -605,12 +604,22 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
             lu[e] = qrow ? make_float4(0.f, 0.f, 0.f, 0.f) : Lu[e ^ fu];
         const float2 lut = lo2[iu];
         const float lux = lut.x - l0.x, luy = lut.y - l0.y;  // l_u relative to l_0
+        // With PF, this u's distances are gathered up front (predicated,
+        // independent loads) so their L2 latencies overlap.
+        float qv[PF ? KK : 1];
+#pragma unroll
+        for (int v = 0; v < (PF ? KK : 1); ++v)
+            qv[v] = (PF && v > u && v < m) ? __ldg(qrow + nb_at<QS>(nb, v)) : 1.f;
+        auto qof = [&](int v, int iv) -> float {
+            if (PF) return qv[v < (PF ? KK : 1) ? v : 0];
+            return qrow ? __ldg(qrow + iv) : pair_q<D>(lu, Lg + (size_t)iv * (D / 4), swz(D, iv));
+        };
 #pragma unroll
         for (int v0 = 1; v0 < KK; v0 += 2) {
             if (v0 + 1 > u && v0 < m) {
-                const PairTerm c0 =
-                    pair_term<D, PASS>(lu, lut, lux, luy, su, du, nb_at<QS>(nb, v0), ss[v0],
-                                       sd[v0], Lg, lo2, a.adjust, nx, ny, qrow);
+                const int iv0 = nb_at<QS>(nb, v0);
+                const PairTerm c0 = pair_term<D, PASS>(lut, lux, luy, su, du, iv0, ss[v0], sd[v0],
+                                                       qof(v0, iv0), lo2, a.adjust, nx, ny);
                 const bool k0 = c0.ok && v0 > u;
                 A00 = k0 ? A00 + c0.a00 : A00;
                 A01 = k0 ? A01 + c0.a01 : A01;
@@ -620,9 +629,10 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
                 rho = k0 ? rho + c0.rho : rho;
                 if (v0 + 1 < KK) {
                     const int v1 = v0 + 1 < KK ? v0 + 1 : v0;
+                    const int iv1 = nb_at<QS>(nb, v1);
                     const PairTerm c1 =
-                        pair_term<D, PASS>(lu, lut, lux, luy, su, du, nb_at<QS>(nb, v1), ss[v1],
-                                           sd[v1], Lg, lo2, a.adjust, nx, ny, qrow);
+                        pair_term<D, PASS>(lut, lux, luy, su, du, iv1, ss[v1], sd[v1],
+                                           qof(v1, iv1), lo2, a.adjust, nx, ny);
                     const bool k1 = c1.ok && v1 < m;
                     A00 = k1 ? A00 + c1.a00 : A00;
                     A01 = k1 ? A01 + c1.a01 : A01;
@@ -721,7 +731,7 @@ __device__ __noinline__ double2 solve_slow(const SlowSolve in, const float *sdp,
 // exact squared distances of the k nearest; their landmark indices are in
 // this thread's column of shared memory (nb_at(nb, t) for rank t).
 
-template <int D, int KK, int QS = kThreads>
+template <int D, int KK, int QS = kThreads, bool PF = false>
 __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uint32_t *nb,
                                                 const float4 *Lg, const float2 *lo2,
                                                 const FusedArgs &a) {
@@ -792,7 +802,8 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
 
     // Step 3: pair terms, u < v < m.
     float A00 = 0.f, A01 = 0.f, A11 = 0.f, B0 = 0.f, B1 = 0.f, rho = 0.f;
-    pair_sums<D, KK, 0, QS>(sd, nb, ss, m, Lg, lo2, l0, a, 0.f, 0.f, A00, A01, A11, B0, B1, rho);
+    pair_sums<D, KK, 0, QS, PF>(sd, nb, ss, m, Lg, lo2, l0, a, 0.f, 0.f, A00, A01, A11, B0, B1,
+                                rho);
 
     // Step 4: FP64 solve; near-singular systems go to the out-of-line path.
     const double a00 = A00, a01 = A01, a11 = A11, b0 = B0, b1 = B1;
@@ -1277,7 +1288,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchArgs B
 // The projection loop over this block's tiles.  Instantiated once with the
 // rows and 2-D positions in shared memory and once in global memory, so the
 // compiler knows each pointer's space (shared loads instead of generic ones).
-template <int D, int KK>
+template <int D, int KK, bool TAB>
 __device__ __forceinline__ void project_tiles(const FusedArgs &a, const float4 *Lg,
                                               const float2 *lo2, uint32_t *nb, int tid) {
     const long long ntiles = (a.n + kThreads - 1) / kThreads;
@@ -1317,7 +1328,8 @@ __device__ __forceinline__ void project_tiles(const FusedArgs &a, const float4 *
 #pragma unroll
         for (int t = 0; t < KK; t += 2)
             nb[(t >> 1) * kThreads] = (uint32_t)si[t] | ((uint32_t)si[t + 1] << 16);
-        const float2 p = project_point<D, KK>(sd, nb, Lg, lo2, a);
+        const float2 p = TAB ? project_point<D, KK, kThreads, true>(sd, nb, Lg, lo2, a)
+                             : project_point<D, KK>(sd, nb, Lg, lo2, a);
         if (active) reinterpret_cast<float2 *>(a.out)[row] = p;
     }
 }
@@ -1357,10 +1369,14 @@ __global__ void __launch_bounds__(kThreads, MINB) project_kernel(const FusedArgs
             }
             return;
         }
-        project_tiles<D, KK>(a, reinterpret_cast<const float4 *>(sL), sLo, qk + tid, tid);
+        if (a.qtab)
+            project_tiles<D, KK, true>(a, reinterpret_cast<const float4 *>(sL), sLo, qk + tid, tid);
+        else
+            project_tiles<D, KK, false>(a, reinterpret_cast<const float4 *>(sL), sLo, qk + tid,
+                                        tid);
     } else {
-        project_tiles<D, KK>(a, reinterpret_cast<const float4 *>(a.hi),
-                             reinterpret_cast<const float2 *>(a.lo), qk + tid, tid);
+        project_tiles<D, KK, false>(a, reinterpret_cast<const float4 *>(a.hi),
+                                    reinterpret_cast<const float2 *>(a.lo), qk + tid, tid);
     }
 }
 
