@@ -149,10 +149,8 @@ def tensor_peak_tflops() -> float:
 
 
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2201_00701_gb300 import sharding
+    return sharding.env_ranks()
 
 
 def cpu_baseline(w, budget_s=10.0, chunk=2000, max_points=1_000_000):
@@ -213,7 +211,7 @@ def run_esom(args, world, rank, local):
     import torch
     import torch.distributed as dist
 
-    from paper_2201_00701_gb300 import binding, workloads
+    from paper_2201_00701_gb300 import binding, sharding, workloads
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -239,10 +237,8 @@ def run_esom(args, world, rank, local):
         # the library's autotuner times the three plans (same bits) on these
         # points and keeps the fastest
         screen = binding.PLAN_NAMES[P.tune(X, w.boost, w.adjust)]
-        if world > 1:  # every rank uses rank 0's choice
-            t = torch.tensor([plans[screen]], device=dev)
-            dist.broadcast(t, 0)
-            screen = binding.PLAN_NAMES[int(t[0])]
+        # every rank uses rank 0's choice
+        screen = binding.PLAN_NAMES[sharding.broadcast_choice(plans[screen], device=dev)]
     P.set_plan(plans[screen])
     cfg = P.config()
 
@@ -327,13 +323,10 @@ def run_esom(args, world, rank, local):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_s = float(np.sum(e2e_ms)) / 1e3
 
-    if world > 1:
-        t = torch.tensor([total_s, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s, e2e_s = float(t[0]), float(t[1])
+    total_s, e2e_s = sharding.max_over_ranks([total_s, e2e_s], device=dev)
 
     if rank == 0:
-        value = world * n * args.steps / total_s
+        value = sharding.job_throughput(n, world, args.steps, total_s)
         fmas = n * (L * d + k * k * d)              # algorithmic FMAs per launch
         t_launch = float(np.mean(step_ms)) / 1e3
         achieved = 2.0 * fmas / t_launch / 1e12     # TFLOP/s (FMA = 2 flops)
@@ -393,7 +386,8 @@ def run_esom(args, world, rank, local):
                          "frac_at_sampled_clock": (achieved / peak * max_mhz / clocks["sm_mhz"])
                          if clocks.get("sm_mhz") else None},
             "clocks": clocks,
-            "e2e": {"value": world * n * args.steps / e2e_s, "unit": "points/s",
+            "e2e": {"value": sharding.job_throughput(n, world, args.steps, e2e_s),
+                    "unit": "points/s",
                     "h2d_bytes_per_step": n * d * 4, "d2h_bytes_per_step": n * 2 * 4,
                     "api": "esom_project_host (pinned host buffers)"},
         }

@@ -1374,6 +1374,9 @@ __global__ void __launch_bounds__(kThreads, MINB) project_kernel(const FusedArgs
         else
             project_tiles<D, KK, false>(a, reinterpret_cast<const float4 *>(sL), sLo, qk + tid,
                                         tid);
+    } else if (a.qtab) {
+        project_tiles<D, KK, true>(a, reinterpret_cast<const float4 *>(a.hi),
+                                   reinterpret_cast<const float2 *>(a.lo), qk + tid, tid);
     } else {
         project_tiles<D, KK, false>(a, reinterpret_cast<const float4 *>(a.hi),
                                     reinterpret_cast<const float2 *>(a.lo), qk + tid, tid);
