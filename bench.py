@@ -410,7 +410,7 @@ def run_batch64(args):
     torch.cuda.set_device(0)
     binding.load()
     params = workloads.batch64(n_max=args.batch_n_max)
-    handles, items, bufs, ws = [], [], [], []
+    handles, items, bufs, ws, plans = [], [], [], [], []
     for p in params:
         w = workloads.batch_member(p)
         P = binding.Projector(w.d, w.L, w.k)
@@ -418,6 +418,7 @@ def run_batch64(args):
         P.set_landmarks(hi, lo)
         X = torch.from_numpy(w.X).cuda()
         out = torch.empty((w.n, 2), device="cuda")
+        plans.append(binding.PLAN_NAMES[P.tune(X, w.boost, w.adjust)])
         items.append(binding.BatchItem(P.h, X.data_ptr(), w.n, out.data_ptr(), w.boost, w.adjust))
         handles.append(P)
         bufs.append((X, hi, lo, out))
@@ -461,6 +462,7 @@ def run_batch64(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "batch64", "datasets": len(ws), "points": total,
+                   "handle_plans": {p: plans.count(p) for p in sorted(set(plans))},
                    "l2": "flushed between steps by an untimed 256 MiB write",
                    "plan": json.loads(binding.esom_batch_plan(b))},
         "batch": {"separate_launches_ms": t_sep, "batch_run_ms": t_batch,

@@ -232,9 +232,11 @@ typedef struct {
  * candidate launch shapes of every group on the batch itself (running it a
  * few times, so the outputs are written) and keeps the fastest: landmark
  * chunking (each dataset's own, or forced chunks of 512 or 256), blocks per
- * SM (occupancy limit or 1), or one single-dataset launch per dataset (for
- * large datasets the persistent group launch may not pay).  Handles are used
- * with FP32 screening and the fused kernel whatever their own settings. */
+ * SM (occupancy limit or 1), or one esom_project per dataset through its
+ * handle's own execution plan (for large datasets, and for handles tuned to
+ * the tensor-core plan, the persistent group launch may not pay).  The
+ * persistent group launch screens in FP32 with the fused kernel whatever
+ * the handles' settings; all shapes give the same bits. */
 esom_status esom_batch_create(const esom_batch_item *items, int count, int autotune,
                               esom_batch *out);
 

@@ -156,14 +156,14 @@ esom_status apply_shape(esom_batch_ctx *b, Group &g, const Shape &sh) {
 esom_status launch_group(esom_batch_ctx *b, const Group &g, cudaStream_t st) {
     if (g.tiles == 0) return ESOM_OK;
     if (g.shape.separate) {
+        // each dataset through its handle's own execution plan (fused,
+        // split or tensor-core, as set on the handle or chosen by esom_tune)
         for (size_t i = 0; i < g.items.size(); ++i) {
-            const esom_ctx *h = b->items[g.items[i]].landmarks;
-            const FusedArgs &a = g.args[i];
-            if (a.n == 0) continue;
-            long long grid = (long long)h->blocks_per_sm * h->num_sms;
-            if (grid > a.ntiles) grid = a.ntiles;
-            const cudaError_t e = h->ops->launch(a, (int)grid, h->smem, st);
-            if (e != cudaSuccess) return bcuda(e, "batch launch (separate)");
+            const esom_batch_item &it = b->items[g.items[i]];
+            if (it.n == 0) continue;
+            const esom_status s = esom_project(it.landmarks, it.points, it.n, it.out, it.boost,
+                                               it.adjust, reinterpret_cast<esom_stream_t>(st));
+            if (s != ESOM_OK) return s;
         }
         return ESOM_OK;
     }
