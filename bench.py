@@ -372,7 +372,10 @@ def run_esom(args, world, rank, local):
             "phases_ms": {"knn_only": float(np.median(knn_ms)),
                           "projection_share": 1.0 - float(np.median(knn_ms))
                           / float(np.median(step_ms))},
-            "gpu_launches": args.steps,
+            # this library's kernels per step: one fused launch, or per pass
+            # of 2^19 points a k-NN, a rescan and a projection launch
+            "gpu_launches": args.steps * (1 if screen == "fused" else
+                                          3 * ((n + (1 << 19) - 1) >> 19)),
             "plans_ms": {screen: float(np.median(step_ms)),
                          **{o: v[0] for o, v in others.items()}},
             "rescan_fraction": {screen: main_stats["rescans"] / max(main_stats["points"], 1),
