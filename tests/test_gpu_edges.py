@@ -142,14 +142,17 @@ def test_n_zero_and_errors(esom):
         assert (out == 0).all()      # nothing was launched
 
 
-def test_nan_input_no_fault(esom):
-    """NaN/Inf points give unspecified values but no fault; the context and
-    later calls stay healthy."""
+@pytest.mark.parametrize("plan", [0, 1, 2])
+def test_nan_input_no_fault(esom, plan):
+    """NaN/Inf points give unspecified values but no fault, in every
+    execution plan (fused, split, tensor-core); the context and later calls
+    stay healthy."""
     w = workloads.mixture10_d8(n=3000)
     w.X[5] = np.nan
     w.X[6, 3] = np.inf
     with esom.Projector(w.d, w.L, w.k) as P:
         P.set_landmarks(torch.from_numpy(w.hi).cuda(), torch.from_numpy(w.lo).cuda())
+        P.set_plan(plan)
         X = torch.from_numpy(w.X).cuda()
         P.project(X, 1.0, 1.0)
         P.knn(X)
