@@ -231,7 +231,7 @@ def run_esom(args, world, rank, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     plans = {"fused": binding.ESOM_PLAN_FUSED, "split": binding.ESOM_PLAN_SPLIT,
-             "tf32": binding.ESOM_PLAN_TF32}
+             "tf32": binding.ESOM_PLAN_TF32, "bf16": binding.ESOM_PLAN_BF16}
     screen = {"fp32": "fused", "tf32": "tf32"}.get(args.screen, args.screen)
     if screen == "auto":
         # the library's autotuner times the three plans (same bits) on these
@@ -335,17 +335,17 @@ def run_esom(args, world, rank, local):
         alu_peak = 2.0 * 128 * props.multi_processor_count * max_mhz * 1e6 / 1e12
         peak = alu_peak
         roof_note = f"128 FP32 lanes x {props.multi_processor_count} SMs x {max_mhz} MHz x 2"
-        if screen == "tf32":
+        if screen in ("tf32", "bf16"):
             # L*d on the tensor pipe (TF32 = half the measured sustained BF16
             # rate), k^2*d on the FP32 lanes: the effective peak of the mix
-            tf32_peak = tensor_peak_tflops() / 2.0
+            tf32_peak = tensor_peak_tflops() / (2.0 if screen == "tf32" else 1.0)
             t_roof = 2.0 * n * L * d / (tf32_peak * 1e12) + 2.0 * n * k * k * d / (alu_peak * 1e12)
             peak = 2.0 * fmas / t_roof / 1e12
-            roof_note = (f"n*L*d on TF32 tensor cores at {tf32_peak:.0f} TFLOP/s (half the "
-                         f"measured sustained BF16 rate) + n*k^2*d on the FP32 lanes at "
-                         f"{alu_peak:.1f} TFLOP/s")
+            roof_note = (f"n*L*d on {screen.upper()} tensor cores at {tf32_peak:.0f} TFLOP/s "
+                         f"(the measured sustained BF16 rate{', halved' if screen == 'tf32' else ''}"
+                         f") + n*k^2*d on the FP32 lanes at {alu_peak:.1f} TFLOP/s")
         traffic = (profile_traffic("tf32" if screen == "tf32" else "fp32")
-                   if args.workload == WORKLOAD and screen != "split" else None)
+                   if args.workload == WORKLOAD and screen in ("tf32", "fused") else None)
         line = {
             "metric": baseline_metric(), "value": value, "unit": "points/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -354,6 +354,8 @@ def run_esom(args, world, rank, local):
             "config": {"workload": args.workload, "n": n, "d": d, "L": L, "k": k,
                        "boost": w.boost, "adjust": w.adjust,
                        "path": {"tf32": "tensor-core (split TF32) screened k-NN kernel, exact "
+                                        "FP32 re-rank, projection kernel",
+                                "bf16": "tensor-core (split BF16) screened k-NN kernel, exact "
                                         "FP32 re-rank, projection kernel",
                                 "split": "FP32 screened k-NN kernel, exact re-rank, projection "
                                          "kernel",
@@ -496,7 +498,7 @@ def run_serve(args):
     srv.set_coalescing(args.serve_coalesce)
     screen = {"fused": "fp32", "split": "fp32"}.get(args.screen, args.screen)
     srv.set_screening({"fp32": binding.ESOM_SCREEN_FP32, "tf32": binding.ESOM_SCREEN_TF32,
-                       "auto": binding.ESOM_SCREEN_AUTO}[screen])
+                       "bf16": binding.ESOM_SCREEN_BF16, "auto": binding.ESOM_SCREEN_AUTO}[screen])
     sids, sizes = [], {}
     for p in params:
         w = workloads.serve_member(p)
@@ -585,8 +587,9 @@ def main():
     ap.add_argument("--impl", default="esom", choices=["esom", "reference"])
     ap.add_argument("--n", type=int, default=0, help="points (default: the workload's n)")
     ap.add_argument("--screen", default="auto",
-                    choices=["auto", "fp32", "tf32", "fused", "split"],
-                    help="execution plan: auto (library autotuner), fused (= fp32), split, tf32")
+                    choices=["auto", "fp32", "tf32", "bf16", "fused", "split"],
+                    help="execution plan: auto (library autotuner), fused (= fp32), split, tf32, "
+                         "bf16")
     ap.add_argument("--ref-points", type=int, default=4000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -162,6 +162,9 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg);
  *                     split into two TF32 parts, x = x_hi + x_lo, and the
  *                     three products x_hi l_hi + x_lo l_hi + x_hi l_lo
  *                     (screening error ~2^-21 relative, like FP32's).
+ *   ESOM_SCREEN_BF16  the same with BF16 parts (kind::f16; half the operand
+ *                     bytes, screening error ~2^-14 relative: more points
+ *                     fail the certificate and are rescanned).
  * Either way the listed candidates are re-ranked with exact FP32 distances
  * and a bound on the screening error certifies that no other landmark can be
  * among the k nearest (a point that fails is rescanned exactly; see
@@ -180,6 +183,7 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg);
  * esom_batch_* and esom_project_noalloc always screen in FP32. */
 #define ESOM_SCREEN_FP32 0
 #define ESOM_SCREEN_TF32 1
+#define ESOM_SCREEN_BF16 2
 esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream);
 
 /* on != 0: esom_project with FP32 screening runs as two kernels, as the
@@ -193,12 +197,13 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream);
 esom_status esom_set_split(esom_handle h, int on);
 
 /* Execution plans of esom_project: one fused FP32 kernel, FP32 k-NN kernel +
- * projection kernel, tensor-core k-NN + projection kernel.  All give the
+ * projection kernel, tensor-core k-NN (TF32 or BF16) + projection kernel.  All give the
  * same bits; which is fastest depends on d, L and k (tensor cores pay at
  * large L, the split at small L). */
 #define ESOM_PLAN_FUSED 0
 #define ESOM_PLAN_SPLIT 1
 #define ESOM_PLAN_TF32 2
+#define ESOM_PLAN_BF16 3
 /* Autotuner: times each plan on the first min(n, 2^19) of `points` (device,
  * n x d) three times on `stream`, writing their coordinates to `out`
  * (n x 2 device), keeps the fastest for the handle (as if set with
@@ -335,12 +340,13 @@ esom_status esom_server_submit(esom_server s, int session, double arrival);
  * frames arrive faster than the GPU projects them. */
 esom_status esom_server_set_coalescing(esom_server s, int on);
 /* Screening of the handles of sessions added from now on: ESOM_SCREEN_FP32,
- * ESOM_SCREEN_TF32, or ESOM_SCREEN_AUTO (each session's handle is tuned with
- * esom_tune on its own points when it is admitted); only before the first
+ * ESOM_SCREEN_TF32, ESOM_SCREEN_BF16, or ESOM_SCREEN_AUTO (each session's
+ * handle is tuned with esom_tune on its own points when it is admitted);
+ * only before the first
  * esom_server_add_session (ESOM_EINVAL after).  Results are the same in any
  * mode; TF32 and AUTO add the landmark images and the neighbour scratch to
  * each session's footprint. */
-#define ESOM_SCREEN_AUTO 2
+#define ESOM_SCREEN_AUTO 3
 esom_status esom_server_set_screening(esom_server s, int mode);
 /* Collects finished frames (up to max) and starts queued ones in free
  * slots; wait_all != 0 blocks until every queued frame has finished (or

@@ -26,11 +26,14 @@ ESOM_EUNSUPPORTED = -6
 ESOM_EDEVICE = -7
 ESOM_SCREEN_FP32 = 0
 ESOM_SCREEN_TF32 = 1
-ESOM_SCREEN_AUTO = 2
+ESOM_SCREEN_BF16 = 2
+ESOM_SCREEN_AUTO = 3
 ESOM_PLAN_FUSED = 0
 ESOM_PLAN_SPLIT = 1
 ESOM_PLAN_TF32 = 2
-PLAN_NAMES = {ESOM_PLAN_FUSED: "fused", ESOM_PLAN_SPLIT: "split", ESOM_PLAN_TF32: "tf32"}
+ESOM_PLAN_BF16 = 3
+PLAN_NAMES = {ESOM_PLAN_FUSED: "fused", ESOM_PLAN_SPLIT: "split", ESOM_PLAN_TF32: "tf32",
+              ESOM_PLAN_BF16: "bf16"}
 
 HEADER = os.path.join(_build.INCLUDE, "esom.h")
 
@@ -196,7 +199,7 @@ def esom_get_stats(h, stream: int = 0, reset: bool = False):
 
 
 def esom_set_screening(h, mode: int, stream: int = 0) -> int:
-    """ESOM_SCREEN_FP32 (0) or ESOM_SCREEN_TF32 (1, tensor cores)."""
+    """ESOM_SCREEN_FP32 (0), ESOM_SCREEN_TF32 (1) or ESOM_SCREEN_BF16 (2)."""
     return load().esom_set_screening(h, mode, stream)
 
 
@@ -419,8 +422,9 @@ class Projector:
         check(esom_set_split(self.h, on))
 
     def set_plan(self, plan: int):
-        """ESOM_PLAN_FUSED, ESOM_PLAN_SPLIT or ESOM_PLAN_TF32."""
-        self.set_screening(ESOM_SCREEN_TF32 if plan == ESOM_PLAN_TF32 else ESOM_SCREEN_FP32)
+        """ESOM_PLAN_FUSED, _SPLIT, _TF32 or _BF16."""
+        self.set_screening({ESOM_PLAN_TF32: ESOM_SCREEN_TF32,
+                            ESOM_PLAN_BF16: ESOM_SCREEN_BF16}.get(plan, ESOM_SCREEN_FP32))
         self.set_split(plan == ESOM_PLAN_SPLIT)
 
     def tune(self, X, boost: float = 1.0, adjust: float = 1.0) -> int:

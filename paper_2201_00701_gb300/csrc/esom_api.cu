@@ -33,6 +33,9 @@ esom_status cuda_fail(cudaError_t e, const char *what) {
 // Points per chunk of the host-buffer pipeline.
 constexpr long long kHostChunk = 1 << 20;
 
+// Operand precision of a tensor-core screening mode.
+int tc_prec(int screening) { return screening == ESOM_SCREEN_BF16 ? esom::kTcBf16 : esom::kTcTf32; }
+
 }  // namespace
 
 namespace esom {
@@ -109,44 +112,76 @@ cudaError_t launch_landmark_prep(float *hi, int L, int D, float *norms, float *l
 }
 
 // One thread per 16-byte piece of a chunk image: piece c of column block blk
-// of landmark j holds values 4e..4e+3 (e = blk * pieces + c) of the row
-// split into TF32 parts -- hi = tf32(v) in the first half of the image,
-// lo = tf32(v - hi) in the second (nearest, ties away) -- zero beyond d and
-// for rows beyond L.  The rows of hi are chunk-swizzled (logical chunk e at
-// e ^ swz(D, j)).
+// of landmark j holds row bytes blk * row_bytes + 16 c .. + 15 of the split
+// row -- high parts (the rounding of each value to TF32 or BF16, nearest) in
+// the first half of the image, low parts (the rounding of the remainder) in
+// the second -- zero beyond d and for rows beyond L.  The rows of hi are
+// chunk-swizzled (logical chunk e at e ^ swz(D, j)).
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
 }
 
+__device__ __forceinline__ uint32_t bf16_rn(float x) {
+    unsigned short r;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(r) : "f"(x));
+    return r;
+}
+
 __global__ void tc_image_kernel(const float *__restrict__ hi, int L, int D,
-                                unsigned char *__restrict__ img, int Lpad) {
-    const int nb = tc_nblk(D), ppb = tc_row_bytes(D) / 16;
+                                unsigned char *__restrict__ img, int Lpad, int prec) {
+    const int eb = tc_elem_bytes(prec);
+    const int rb = tc_row_bytes(D, prec), nb = tc_nblk(D, prec), ppb = rb / 16;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)Lpad * nb * ppb) return;
     const int c = (int)(t % ppb);
     const int blk = (int)((t / ppb) % nb);
     const int j = (int)(t / ppb / nb);
-    const int e = blk * ppb + c;
-    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-    if (j < L && e < D / 4) {
-        const float4 v = reinterpret_cast<const float4 *>(hi + (size_t)j * D)[e ^ swz(D, j)];
-        h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-        l = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z),
-                        tf32_rna(v.w - h.w));
+    const int b0 = blk * rb + 16 * c;  // first byte of the piece in the split row
+    uint4 h = make_uint4(0u, 0u, 0u, 0u), l = h;
+    for (int q = 0; q < 4 / eb; ++q) {
+        const int e = b0 / (4 * eb) + q;  // float4 index of the row
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < L && e < D / 4) v = reinterpret_cast<const float4 *>(hi + (size_t)j * D)[e ^ swz(D, j)];
+        const float a[4] = {v.x, v.y, v.z, v.w};
+        uint32_t hw[4], lw[4];
+        for (int i = 0; i < 4; ++i) {
+            if (prec == kTcBf16) {
+                hw[i] = bf16_rn(a[i]);
+                lw[i] = bf16_rn(a[i] - __uint_as_float(hw[i] << 16));
+            } else {
+                const float hf = tf32_rna(a[i]);
+                hw[i] = __float_as_uint(hf);
+                lw[i] = __float_as_uint(tf32_rna(a[i] - hf));
+            }
+        }
+        if (prec == kTcBf16) {
+            const uint32_t h0 = hw[0] | (hw[1] << 16), h1 = hw[2] | (hw[3] << 16);
+            const uint32_t l0 = lw[0] | (lw[1] << 16), l1 = lw[2] | (lw[3] << 16);
+            if (q == 0) {
+                h.x = h0; h.y = h1; l.x = l0; l.y = l1;
+            } else {
+                h.z = h0; h.w = h1; l.z = l0; l.w = l1;
+            }
+        } else {
+            h = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            l = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
     }
-    unsigned char *chunk = img + (size_t)(j / kTcN) * tc_chunk_bytes(D);
-    const unsigned off = tc_image_offset(D, kTcN, j % kTcN, blk, c);
-    *reinterpret_cast<float4 *>(chunk + off) = h;
-    *reinterpret_cast<float4 *>(chunk + tc_chunk_bytes(D) / 2 + off) = l;
+    unsigned char *chunk = img + (size_t)(j / kTcN) * tc_chunk_bytes(D, prec);
+    const unsigned off = tc_image_offset(D, kTcN, j % kTcN, blk, c, prec);
+    *reinterpret_cast<uint4 *>(chunk + off) = h;
+    *reinterpret_cast<uint4 *>(chunk + tc_chunk_bytes(D, prec) / 2 + off) = l;
 }
 
-cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img,
+cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img, int prec,
                             cudaStream_t stream) {
     const int Lpad = (L + kTcN - 1) / kTcN * kTcN;
-    const long long threads = (long long)Lpad * tc_nblk(D) * (tc_row_bytes(D) / 16);
-    tc_image_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(hi, L, D, img, Lpad);
+    const long long threads =
+        (long long)Lpad * tc_nblk(D, prec) * (tc_row_bytes(D, prec) / 16);
+    tc_image_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(hi, L, D, img, Lpad,
+                                                                           prec);
     return cudaGetLastError();
 }
 }  // namespace esom
@@ -352,7 +387,8 @@ esom_status esom_set_landmarks(esom_handle h, const float *hi, const float *lo,
                                                          reinterpret_cast<float *>(h->status + 1), st,
                                                          esom::kTcN);
     if (e == cudaSuccess && h->qtab) e = h->ops->launch_qtab(h->hi, h->L, h->qtab, st);
-    if (e == cudaSuccess && h->screening) e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, st);
+    if (e == cudaSuccess && h->screening)
+        e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, tc_prec(h->screening), st);
     if (e != cudaSuccess) return cuda_fail(e, "landmark copy");
     ++h->version;
     return ESOM_OK;
@@ -518,7 +554,10 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg) {
     cfg->landmark_chunks = h->nchunks;
     cfg->shared_bytes = (int)h->smem;
     cfg->screening = h->screening;
-    cfg->plan = h->screening ? ESOM_PLAN_TF32 : (h->split ? ESOM_PLAN_SPLIT : ESOM_PLAN_FUSED);
+    cfg->plan = h->screening == ESOM_SCREEN_BF16   ? ESOM_PLAN_BF16
+                : h->screening == ESOM_SCREEN_TF32 ? ESOM_PLAN_TF32
+                : h->split                          ? ESOM_PLAN_SPLIT
+                                                    : ESOM_PLAN_FUSED;
     if (h->screening) {
         // the tensor-core k-NN kernel (the projection kernel that follows it
         // uses 256 threads and the landmark rows of the plain kernel)
@@ -598,9 +637,10 @@ esom_status esom_tune(esom_handle h, const float *points, int64_t n, float *out,
     const int old_screening = h->screening, old_split = h->split;
     int best = -1;
     float best_ms = 0.f;
-    for (int p = ESOM_PLAN_FUSED; p <= ESOM_PLAN_TF32; ++p) {
-        s = p == ESOM_PLAN_TF32 ? esom_set_screening(h, ESOM_SCREEN_TF32, stream)
-                                : esom_set_screening(h, ESOM_SCREEN_FP32, stream);
+    for (int p = ESOM_PLAN_FUSED; p <= ESOM_PLAN_BF16; ++p) {
+        s = esom_set_screening(h, p == ESOM_PLAN_TF32 ? ESOM_SCREEN_TF32
+                                  : p == ESOM_PLAN_BF16 ? ESOM_SCREEN_BF16 : ESOM_SCREEN_FP32,
+                               stream);
         if (s == ESOM_OK) s = esom_set_split(h, p == ESOM_PLAN_SPLIT);
         if (s != ESOM_OK) continue;  // plan unavailable here (e.g. no tensor-core kernel)
         float total = 0.f;
@@ -626,7 +666,9 @@ esom_status esom_tune(esom_handle h, const float *points, int64_t n, float *out,
         esom_set_split(h, old_split);
         return fail(ESOM_ECUDA, "no execution plan ran");
     }
-    s = esom_set_screening(h, best == ESOM_PLAN_TF32 ? ESOM_SCREEN_TF32 : ESOM_SCREEN_FP32, stream);
+    s = esom_set_screening(h, best == ESOM_PLAN_TF32 ? ESOM_SCREEN_TF32
+                              : best == ESOM_PLAN_BF16 ? ESOM_SCREEN_BF16 : ESOM_SCREEN_FP32,
+                           stream);
     if (s == ESOM_OK) s = esom_set_split(h, best == ESOM_PLAN_SPLIT);
     if (s == ESOM_OK && plan) *plan = best;
     return s;
@@ -634,7 +676,7 @@ esom_status esom_tune(esom_handle h, const float *points, int64_t n, float *out,
 
 esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
     if (!h) return fail(ESOM_EINVAL, "null handle");
-    if (mode != ESOM_SCREEN_FP32 && mode != ESOM_SCREEN_TF32)
+    if (mode != ESOM_SCREEN_FP32 && mode != ESOM_SCREEN_TF32 && mode != ESOM_SCREEN_BF16)
         return fail(ESOM_EINVAL, "unknown screening mode %d", mode);
     esom_status s = check_device(h);
     if (s != ESOM_OK) return s;
@@ -642,7 +684,8 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
         h->screening = 0;
         return ESOM_OK;
     }
-    const esom::TcOps *tc = esom::tc_ops(h->d, h->kc);
+    const int prec = tc_prec(mode);
+    const esom::TcOps *tc = esom::tc_ops(h->d, h->kc, prec);
     if (!tc) return fail(ESOM_EUNSUPPORTED, "no tensor-core kernel for d = %d, k = %d", h->d, h->k);
     int major = 0, minor = 0;
     cudaError_t e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->dev);
@@ -651,7 +694,7 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
     if (major != 10 || minor != 3)
         return fail(ESOM_EUNSUPPORTED, "tensor-core screening needs sm_103 (device is sm_%d%d)",
                     major, minor);
-    const size_t smem = esom::tc_smem_bytes(h->d);
+    const size_t smem = esom::tc_smem_bytes(h->d, prec);
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(shared memory opt-in)");
@@ -680,7 +723,9 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
     s = prepare_split(h);
     if (s != ESOM_OK) return s;
     if (!h->img) {
-        const size_t bytes = (size_t)((h->L + esom::kTcN - 1) / esom::kTcN) * esom::tc_chunk_bytes(h->d);
+        // sized for TF32, the larger of the two image formats
+        const size_t bytes = (size_t)((h->L + esom::kTcN - 1) / esom::kTcN) *
+                             esom::tc_chunk_bytes(h->d, esom::kTcTf32);
         e = cudaMalloc(&h->img, bytes);
         if (e != cudaSuccess) {
             h->img = nullptr;
@@ -689,7 +734,8 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
         }
     }
     if (h->version > 0) {
-        e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, reinterpret_cast<cudaStream_t>(stream));
+        e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, prec,
+                                  reinterpret_cast<cudaStream_t>(stream));
         if (e != cudaSuccess) return cuda_fail(e, "landmark image build");
     }
     h->tc = tc;

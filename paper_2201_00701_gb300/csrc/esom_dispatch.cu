@@ -31,30 +31,30 @@ const KernelOps *kernel_ops(int D, int kc) {
     }
 }
 
-#define ESOM_DECLARE_TC_D(DV) const TcOps *tc_ops_d##DV(int kc);
+#define ESOM_DECLARE_TC_D(DV) const TcOps *tc_ops_d##DV(int kc, int prec);
 ESOM_DECLARE_TC_D(4) ESOM_DECLARE_TC_D(8) ESOM_DECLARE_TC_D(12) ESOM_DECLARE_TC_D(16)
 ESOM_DECLARE_TC_D(20) ESOM_DECLARE_TC_D(24) ESOM_DECLARE_TC_D(28) ESOM_DECLARE_TC_D(32)
 ESOM_DECLARE_TC_D(36) ESOM_DECLARE_TC_D(40) ESOM_DECLARE_TC_D(44) ESOM_DECLARE_TC_D(48)
 ESOM_DECLARE_TC_D(52) ESOM_DECLARE_TC_D(56) ESOM_DECLARE_TC_D(60) ESOM_DECLARE_TC_D(64)
 
-const TcOps *tc_ops(int D, int kc) {
+const TcOps *tc_ops(int D, int kc, int prec) {
     switch (D) {
-        case 4: return tc_ops_d4(kc);
-        case 8: return tc_ops_d8(kc);
-        case 12: return tc_ops_d12(kc);
-        case 16: return tc_ops_d16(kc);
-        case 20: return tc_ops_d20(kc);
-        case 24: return tc_ops_d24(kc);
-        case 28: return tc_ops_d28(kc);
-        case 32: return tc_ops_d32(kc);
-        case 36: return tc_ops_d36(kc);
-        case 40: return tc_ops_d40(kc);
-        case 44: return tc_ops_d44(kc);
-        case 48: return tc_ops_d48(kc);
-        case 52: return tc_ops_d52(kc);
-        case 56: return tc_ops_d56(kc);
-        case 60: return tc_ops_d60(kc);
-        case 64: return tc_ops_d64(kc);
+        case 4: return tc_ops_d4(kc, prec);
+        case 8: return tc_ops_d8(kc, prec);
+        case 12: return tc_ops_d12(kc, prec);
+        case 16: return tc_ops_d16(kc, prec);
+        case 20: return tc_ops_d20(kc, prec);
+        case 24: return tc_ops_d24(kc, prec);
+        case 28: return tc_ops_d28(kc, prec);
+        case 32: return tc_ops_d32(kc, prec);
+        case 36: return tc_ops_d36(kc, prec);
+        case 40: return tc_ops_d40(kc, prec);
+        case 44: return tc_ops_d44(kc, prec);
+        case 48: return tc_ops_d48(kc, prec);
+        case 52: return tc_ops_d52(kc, prec);
+        case 56: return tc_ops_d56(kc, prec);
+        case 60: return tc_ops_d60(kc, prec);
+        case 64: return tc_ops_d64(kc, prec);
         default: return nullptr;
     }
 }

@@ -98,36 +98,49 @@ constexpr int kTcN = 64;
 constexpr int kTcThreads = 160;
 constexpr int kTcCols = 2 * kTcN;  // TMEM columns: two accumulator buffers
 
-// Operand layout: rows of tc_row_bytes per column block (64 bytes = 16 TF32
-// values with the 64-byte swizzle for d <= 16, else 128 bytes = 32 values
-// with the 128-byte swizzle), tc_nblk column blocks; pipeline stages of the
-// landmark ring; resident blocks per SM the launch aims for.
-__host__ __device__ constexpr int tc_row_bytes(int D) { return D <= 16 ? 64 : 128; }
-__host__ __device__ constexpr int tc_nblk(int D) { return D <= 16 ? 1 : (D + 31) / 32; }
-__host__ __device__ constexpr int tc_stages(int D) { return D <= 32 ? 3 : 2; }
+// Operand precision of the tensor-core screening: split TF32 (4-byte
+// elements, kind::tf32) or split BF16 (2-byte elements, kind::f16).
+enum TcPrec : int { kTcTf32 = 0, kTcBf16 = 1 };
+__host__ __device__ constexpr int tc_elem_bytes(int prec) { return prec == kTcBf16 ? 2 : 4; }
+
+// Operand layout: rows of tc_row_bytes per column block (64 bytes with the
+// 64-byte swizzle when a row's d elements fit, else 128 bytes with the
+// 128-byte swizzle), tc_nblk column blocks; pipeline stages of the landmark
+// ring; resident blocks per SM the launch aims for.  One MMA K step reads 32
+// bytes of a row (8 TF32 or 16 BF16 values).
+__host__ __device__ constexpr int tc_row_bytes(int D, int prec = kTcTf32) {
+    return D * tc_elem_bytes(prec) <= 64 ? 64 : 128;
+}
+__host__ __device__ constexpr int tc_nblk(int D, int prec = kTcTf32) {
+    return D * tc_elem_bytes(prec) <= 64 ? 1 : (D * tc_elem_bytes(prec) + 127) / 128;
+}
+__host__ __device__ constexpr int tc_stages(int D, int prec = kTcTf32) {
+    return D * tc_elem_bytes(prec) <= 128 ? 3 : 2;
+}
 __host__ __device__ constexpr int tc_minb(int D, int KC) { return D <= 16 ? (KC <= 16 ? 4 : 3) : 2; }
 
-// Bytes of one chunk image: the high TF32 parts of kTcN rows, then the low
+// Bytes of one chunk image: the high parts of kTcN rows, then the low
 // parts, in the swizzled K-major order the MMA reads (see tc_image_offset).
-__host__ __device__ inline size_t tc_chunk_bytes(int D) {
-    return (size_t)2 * kTcN * tc_row_bytes(D) * tc_nblk(D);
+__host__ __device__ inline size_t tc_chunk_bytes(int D, int prec = kTcTf32) {
+    return (size_t)2 * kTcN * tc_row_bytes(D, prec) * tc_nblk(D, prec);
 }
 
 // Byte offset of 16-byte piece c of column block blk of row r inside an
 // operand of `rows` rows (base aligned to 1024 bytes): 8-row groups of
 // 8 * row_bytes, piece c of row r at slot c ^ (r mod 8) (128-byte swizzle)
 // or c ^ ((r / 2) mod 4) (64-byte swizzle).
-__host__ __device__ inline unsigned tc_image_offset(int D, int rows, int r, int blk, int c) {
-    const int rb = tc_row_bytes(D);
+__host__ __device__ inline unsigned tc_image_offset(int D, int rows, int r, int blk, int c,
+                                                    int prec = kTcTf32) {
+    const int rb = tc_row_bytes(D, prec);
     const int sw = rb == 64 ? ((r >> 1) & 3) : (r & 7);
     return (unsigned)(blk * rows * rb + (r >> 3) * 8 * rb + (r & 7) * rb + ((c ^ sw) << 4));
 }
 
-inline size_t tc_smem_bytes(int D) {
-    const size_t rb = (size_t)tc_row_bytes(D) * tc_nblk(D);
+inline size_t tc_smem_bytes(int D, int prec = kTcTf32) {
+    const size_t rb = (size_t)tc_row_bytes(D, prec) * tc_nblk(D, prec);
     return 1024                                  // alignment slack
            + 2 * (size_t)kTcRows * rb            // point tile (high and low parts)
-           + (size_t)tc_stages(D) * tc_chunk_bytes(D)  // landmark chunk ring
+           + (size_t)tc_stages(D, prec) * tc_chunk_bytes(D, prec)  // landmark chunk ring
            + (size_t)kQueue * kTcRows * 4        // candidate queue
            + 256;                                // barriers, TMEM address, flags
 }
@@ -150,12 +163,14 @@ inline size_t project_smem_bytes(int D, int L, bool resident) {
            (size_t)kQueue * kThreads * sizeof(unsigned);
 }
 
-// Tensor-core instantiation for D and list capacity kc, or nullptr.
-const TcOps *tc_ops(int D, int kc);
+// Tensor-core instantiation for D, list capacity kc and precision, or
+// nullptr.
+const TcOps *tc_ops(int D, int kc, int prec);
 
-// Builds the TF32 chunk images of the landmarks from the (chunk-swizzled)
-// rows of hi: ceil(L / kTcN) images of tc_chunk_bytes(D), rows beyond L zero.
-cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img,
+// Builds the split chunk images of the landmarks (precision prec) from the
+// (chunk-swizzled) rows of hi: ceil(L / kTcN) images of tc_chunk_bytes(D,
+// prec), rows beyond L zero.
+cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img, int prec,
                             cudaStream_t stream);
 
 // Records `msg` as this host thread's last error message; returns s.

@@ -281,7 +281,8 @@ double esom_server_now(esom_server s) { return s ? host_now(s) : 0.0; }
 
 esom_status esom_server_set_screening(esom_server s, int mode) {
     if (!s) return sfail(ESOM_EINVAL, "null server");
-    if (mode != ESOM_SCREEN_FP32 && mode != ESOM_SCREEN_TF32 && mode != ESOM_SCREEN_AUTO)
+    if (mode != ESOM_SCREEN_FP32 && mode != ESOM_SCREEN_TF32 && mode != ESOM_SCREEN_BF16 &&
+        mode != ESOM_SCREEN_AUTO)
         return sfail(ESOM_EINVAL, "unknown screening mode");
     std::lock_guard<std::mutex> lock(s->mu);
     if (!s->sessions.empty()) return sfail(ESOM_EINVAL, "set the screening mode before adding sessions");
@@ -311,7 +312,8 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
     const size_t qtab = d.L <= esom::kQtabMaxL ? (size_t)d.L * d.L * 4 : 0;
     // tensor-core screening: landmark images and the neighbour scratch
     const size_t img = s->screening != ESOM_SCREEN_FP32
-                           ? (size_t)((d.L + esom::kTcN - 1) / esom::kTcN) * esom::tc_chunk_bytes(d.d) +
+                           ? (size_t)((d.L + esom::kTcN - 1) / esom::kTcN) *
+                                     esom::tc_chunk_bytes(d.d, esom::kTcTf32) +
                                  (size_t)esom::kTcPass * d.k * 8
                            : 0;
     const size_t bytes = (size_t)d.n * d.d * 4 + (size_t)d.n * 8 + (size_t)d.L * (d.d + 2) * 4 * 2 +
@@ -324,8 +326,8 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
     ss->desc = d;
     ss->bytes = bytes;
     esom_status r = esom_create(d.d, d.L, d.k, &ss->h);
-    if (r == ESOM_OK && s->screening == ESOM_SCREEN_TF32)
-        r = esom_set_screening(ss->h, ESOM_SCREEN_TF32, nullptr);
+    if (r == ESOM_OK && (s->screening == ESOM_SCREEN_TF32 || s->screening == ESOM_SCREEN_BF16))
+        r = esom_set_screening(ss->h, s->screening, nullptr);
     cudaError_t e = cudaSuccess;
     if (r == ESOM_OK) {
         e = cudaMalloc(&ss->points, (size_t)d.n * d.d * 4);

@@ -98,22 +98,55 @@ __device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
            ((uint64_t)((8 * ROWB) >> 4) << 32) | ((uint64_t)1 << 46) | (kLayout << 61);
 }
 
-// Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A and B TF32
-// (bits 7-9 and 10-12 = 2), both K-major, N / 8 at bits 17-22, M / 16 at
-// bits 24-28.
+// Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A and B both
+// TF32 (bits 7-9 and 10-12 = 2, kind::tf32) or both BF16 (= 1, kind::f16),
+// both K-major, N / 8 at bits 17-22, M / 16 at bits 24-28.
+template <int PREC>
 __host__ __device__ constexpr uint32_t tc_idesc() {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-           ((uint32_t)(kTcRows >> 4) << 24);
+    return (1u << 4) | ((PREC == kTcBf16 ? 1u : 2u) << 7) | ((PREC == kTcBf16 ? 1u : 2u) << 10) |
+           ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
+template <int PREC>
+__device__ __forceinline__ void mma_split(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    if (PREC == kTcBf16)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+}
+
+// FP32 -> BF16, round to nearest even; and back (exact).
+__device__ __forceinline__ uint32_t to_bf16_bits(float x) {
+    unsigned short r;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float bf16_bits_to_f32(uint32_t b) { return __uint_as_float(b << 16); }
+
+// Splits four values into BF16 high and low parts, packed two a word
+// (element 2w in the low half of word w, as the MMA reads K-contiguous
+// 16-bit elements).
+__device__ __forceinline__ void split_bf16x4(float4 v, uint2 &hi, uint2 &lo) {
+    const float a[4] = {v.x, v.y, v.z, v.w};
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        h[i] = to_bf16_bits(a[i]);
+        l[i] = to_bf16_bits(a[i] - bf16_bits_to_f32(h[i]));
+    }
+    hi = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+    lo = make_uint2(l[0] | (l[1] << 16), l[2] | (l[3] << 16));
 }
 
 // Arrives on `bar` once every MMA issued so far by this thread has completed.
@@ -154,34 +187,37 @@ __device__ __forceinline__ float to_tf32(float x) {
 }
 
 // Bound on the tensor-core part of the screening error per unit |X| max|L|.
-// With x_hi = tf32(x), x_lo = tf32(x - x_hi): |x - x_hi| <= 2^-11 |x| and
-// |x - x_hi - x_lo| <= 2^-22 |x|, so the dropped terms x_lo l_lo and the two
-// remainders are <= 3 2^-22 |x_i||l_i| per coordinate; the 3D products are
+// With x_hi the rounding of x to p significant bits (p = 11 for TF32, 8 for
+// BF16) and x_lo that of x - x_hi: |x - x_hi| <= 2^-p |x| and
+// |x - x_hi - x_lo| <= 2^-2p |x|, so the dropped terms x_lo l_lo and the two
+// remainders are <= 3 2^-2p |x_i||l_i| per coordinate; the 3D products are
 // exact in FP32 and accumulated with at most 3D + 1 roundings (2^-23 each,
 // relative to the sum of |products| <= |x||l|).  Twice that in
 // v_j = |L_j|^2 - 2 T_j, and a factor 2 of margin.
-template <int D>
+template <int D, int PREC>
 __device__ __forceinline__ float tc_dot_bound() {
-    return 4.f * (3.f * 2.3841858e-7f + (float)(3 * D + 1) * 1.1920929e-7f);
+    constexpr float kSplit = PREC == kTcBf16 ? 1.5258789e-5f : 2.3841858e-7f;  // 2^-2p
+    return 4.f * (3.f * kSplit + (float)(3 * D + 1) * 1.1920929e-7f);
 }
 
 // ---------------------------------------------------------------------------
 
-template <int D, int KC>
+template <int D, int KC, int PREC>
 __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const FusedArgs a) {
     static_assert(D % 4 == 0 && D >= 4 && D <= 64, "D must be a multiple of 4 in [4, 64]");
     static_assert(KC >= 8 && KC <= 36 && KC % 4 == 0, "list capacity out of range");
     constexpr int KK = KC - 4;
-    constexpr int RB = tc_row_bytes(D);          // bytes of a row per column block
-    constexpr int NB = tc_nblk(D);
+    constexpr int EB = tc_elem_bytes(PREC);      // bytes of an operand element
+    constexpr int RB = tc_row_bytes(D, PREC);    // bytes of a row per column block
+    constexpr int NB = tc_nblk(D, PREC);
     constexpr int PPB = RB / 16;                 // 16-byte pieces per block row
-    constexpr int KPB = RB / 32;                 // K steps (8 TF32) per block row
-    constexpr int S = tc_stages(D);
-    constexpr int KS = (D + 7) / 8;              // MMA K steps of 8 TF32 values
+    constexpr int KPB = RB / 32;                 // K steps (32 bytes) per block row
+    constexpr int S = tc_stages(D, PREC);
+    constexpr int KS = (D * EB + 31) / 32;       // MMA K steps of 32 bytes
     constexpr uint32_t kAPart = kTcRows * RB * NB;  // x_hi (then x_lo) of a tile
     constexpr uint32_t kBPart = kTcN * RB * NB;     // l_hi (then l_lo) of a chunk
     constexpr uint32_t kBBytes = 2 * kBPart;
-    constexpr uint32_t kIdesc = tc_idesc();
+    constexpr uint32_t kIdesc = tc_idesc<PREC>();
     constexpr int QS = kTcRows;  // queue stride: one column per selection thread
     constexpr int KF = ((KC + 7) & ~7) < 32 ? ((KC + 7) & ~7) : 32;  // first sorted block
 
@@ -274,10 +310,12 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                     for (int ks = 0; ks < KS; ++ks) {
                         const uint32_t ka = (uint32_t)((ks / KPB) * kTcRows * RB + (ks % KPB) * 32);
                         const uint32_t kb = (uint32_t)((ks / KPB) * kTcN * RB + (ks % KPB) * 32);
-                        mma_tf32(dt, sw_desc<RB>(ahi + ka), sw_desc<RB>(bhi + kb), kIdesc,
-                                 ks > 0 ? 1u : 0u);
-                        mma_tf32(dt, sw_desc<RB>(alo + ka), sw_desc<RB>(bhi + kb), kIdesc, 1u);
-                        mma_tf32(dt, sw_desc<RB>(ahi + ka), sw_desc<RB>(blo + kb), kIdesc, 1u);
+                        mma_split<PREC>(dt, sw_desc<RB>(ahi + ka), sw_desc<RB>(bhi + kb), kIdesc,
+                                        ks > 0 ? 1u : 0u);
+                        mma_split<PREC>(dt, sw_desc<RB>(alo + ka), sw_desc<RB>(bhi + kb), kIdesc,
+                                        1u);
+                        mma_split<PREC>(dt, sw_desc<RB>(ahi + ka), sw_desc<RB>(blo + kb), kIdesc,
+                                        1u);
                     }
                     mma_commit(&t_full[tb]);
                     mma_commit(&l_empty[s]);
@@ -311,9 +349,9 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         const uint32_t my_lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         constexpr float kGamma = (2.25f * D + 10.f) * kU * 1.25f;
 
-        // Writes this thread's row of tile `tile`, split into TF32 parts
-        // (swizzled), into the point buffer and returns |x|^2 (FP32, exact
-        // row).
+        // Writes this thread's row of tile `tile`, split into high and low
+        // parts (TF32 or BF16, swizzled), into the point buffer and returns
+        // |x|^2 (FP32, exact row).
         auto write_tile = [&](long long tile) -> float {
             const long long row = tile * kTcRows + tid;
             const bool act = row < a.n;
@@ -323,23 +361,43 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
             for (int blk = 0; blk < NB; ++blk)
 #pragma unroll
                 for (int c = 0; c < PPB; ++c) {
-                    const int e = blk * PPB + c;  // float4 index of the row
-                    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-                    if (e < D / 4 && act) {
-                        const float4 v = __ldg(xp + e);
-                        xx = fmaf(v.x, v.x, xx);
-                        xx = fmaf(v.y, v.y, xx);
-                        xx = fmaf(v.z, v.z, xx);
-                        xx = fmaf(v.w, v.w, xx);
-                        h = make_float4(to_tf32(v.x), to_tf32(v.y), to_tf32(v.z), to_tf32(v.w));
-                        l = make_float4(to_tf32(v.x - h.x), to_tf32(v.y - h.y), to_tf32(v.z - h.z),
-                                        to_tf32(v.w - h.w));
+                    const int b0 = blk * RB + 16 * c;  // first byte of the piece in the row
+                    if (b0 >= 32 * KS) continue;       // pieces the MMA K steps do not read
+                    uint4 h = make_uint4(0u, 0u, 0u, 0u), l = h;
+#pragma unroll
+                    for (int q = 0; q < 4 / EB; ++q) {  // float4s of x in this piece
+                        const int e = b0 / (4 * EB) + q;  // float4 index of the row
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (e < D / 4 && act) {
+                            v = __ldg(xp + e);
+                            xx = fmaf(v.x, v.x, xx);
+                            xx = fmaf(v.y, v.y, xx);
+                            xx = fmaf(v.z, v.z, xx);
+                            xx = fmaf(v.w, v.w, xx);
+                        }
+                        if (PREC == kTcBf16) {
+                            uint2 hh, ll;
+                            split_bf16x4(v, hh, ll);
+                            if (q == 0) {
+                                h.x = hh.x; h.y = hh.y; l.x = ll.x; l.y = ll.y;
+                            } else {
+                                h.z = hh.x; h.w = hh.y; l.z = ll.x; l.w = ll.y;
+                            }
+                        } else {
+                            const float4 hv = make_float4(to_tf32(v.x), to_tf32(v.y),
+                                                          to_tf32(v.z), to_tf32(v.w));
+                            const float4 lv =
+                                make_float4(to_tf32(v.x - hv.x), to_tf32(v.y - hv.y),
+                                            to_tf32(v.z - hv.z), to_tf32(v.w - hv.w));
+                            h = make_uint4(__float_as_uint(hv.x), __float_as_uint(hv.y),
+                                           __float_as_uint(hv.z), __float_as_uint(hv.w));
+                            l = make_uint4(__float_as_uint(lv.x), __float_as_uint(lv.y),
+                                           __float_as_uint(lv.z), __float_as_uint(lv.w));
+                        }
                     }
-                    if (e < 2 * KS) {  // pieces the MMA K steps read
-                        const unsigned off = tc_image_offset(D, kTcRows, tid, blk, c);
-                        *reinterpret_cast<float4 *>(sA + off) = h;
-                        *reinterpret_cast<float4 *>(sA + kAPart + off) = l;
-                    }
+                    const unsigned off = tc_image_offset(D, kTcRows, tid, blk, c, PREC);
+                    *reinterpret_cast<uint4 *>(sA + off) = h;
+                    *reinterpret_cast<uint4 *>(sA + kAPart + off) = l;
                 }
             fence_proxy_async_smem();
             __syncwarp();
@@ -389,7 +447,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
             const float xn = sqrtf(xx);
             const float sx = xn + lmax;
             // |v_j - (exact FP32 distance - |x|^2)| <= M
-            const float M = tc_dot_bound<D>() * xn * lmax + 2.f * kGamma * sx * sx;
+            const float M = tc_dot_bound<D, PREC>() * xn * lmax + 2.f * kGamma * sx * sx;
 
             float keys[KC];
             ScanState st;
@@ -491,34 +549,40 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
     }
 }
 
-template <int D, int KC>
+template <int D, int KC, int PREC>
 cudaError_t launch_tc(const FusedArgs &a, int grid, size_t smem, cudaStream_t stream) {
-    tc_kernel<D, KC><<<grid, kTcThreads, smem, stream>>>(a);
+    tc_kernel<D, KC, PREC><<<grid, kTcThreads, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
-template <int D, int KC>
+template <int D, int KC, int PREC>
 struct TcInstance {
     static const TcOps ops;
 };
 
-template <int D, int KC>
-const TcOps TcInstance<D, KC>::ops = {reinterpret_cast<const void *>(&tc_kernel<D, KC>), KC,
-                                      &launch_tc<D, KC>};
+template <int D, int KC, int PREC>
+const TcOps TcInstance<D, KC, PREC>::ops = {
+    reinterpret_cast<const void *>(&tc_kernel<D, KC, PREC>), KC, &launch_tc<D, KC, PREC>};
+
+#define ESOM_TC_CASES(DV, P)                                         \
+    switch (kc) {                                                    \
+        case 8: return &TcInstance<DV, 8, P>::ops;                   \
+        case 12: return &TcInstance<DV, 12, P>::ops;                 \
+        case 16: return &TcInstance<DV, 16, P>::ops;                 \
+        case 20: return &TcInstance<DV, 20, P>::ops;                 \
+        case 24: return &TcInstance<DV, 24, P>::ops;                 \
+        case 28: return &TcInstance<DV, 28, P>::ops;                 \
+        case 32: return &TcInstance<DV, 32, P>::ops;                 \
+        case 36: return &TcInstance<DV, 36, P>::ops;                 \
+        default: return nullptr;                                     \
+    }
 
 #define ESOM_DEFINE_TC_D(DV)                                         \
-    const TcOps *tc_ops_d##DV(int kc) {                              \
-        switch (kc) {                                                \
-            case 8: return &TcInstance<DV, 8>::ops;                  \
-            case 12: return &TcInstance<DV, 12>::ops;                \
-            case 16: return &TcInstance<DV, 16>::ops;                \
-            case 20: return &TcInstance<DV, 20>::ops;                \
-            case 24: return &TcInstance<DV, 24>::ops;                \
-            case 28: return &TcInstance<DV, 28>::ops;                \
-            case 32: return &TcInstance<DV, 32>::ops;                \
-            case 36: return &TcInstance<DV, 36>::ops;                \
-            default: return nullptr;                                 \
+    const TcOps *tc_ops_d##DV(int kc, int prec) {                    \
+        if (prec == kTcBf16) {                                       \
+            ESOM_TC_CASES(DV, kTcBf16)                               \
         }                                                            \
+        ESOM_TC_CASES(DV, kTcTf32)                                   \
     }
 
 }  // namespace esom

@@ -142,7 +142,7 @@ def test_n_zero_and_errors(esom):
         assert (out == 0).all()      # nothing was launched
 
 
-@pytest.mark.parametrize("plan", [0, 1, 2])
+@pytest.mark.parametrize("plan", [0, 1, 2, 3])
 def test_nan_input_no_fault(esom, plan):
     """NaN/Inf points give unspecified values but no fault, in every
     execution plan (fused, split, tensor-core); the context and later calls

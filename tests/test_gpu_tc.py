@@ -42,13 +42,15 @@ def run_mode(esom, w, mode, X=None):
     return out.cpu().numpy(), idx.cpu().numpy(), d2.cpu().numpy(), cfg
 
 
-def same_as_fp32(esom, w, label, max_rescans=0.02):
+def same_as_fp32(esom, w, label, max_rescans=0.02, mode=None):
+    mode = esom.ESOM_SCREEN_TF32 if mode is None else mode
     ref = run_mode(esom, w, esom.ESOM_SCREEN_FP32)
-    got = run_mode(esom, w, esom.ESOM_SCREEN_TF32)
+    got = run_mode(esom, w, mode)
     cfg = got[3]
-    assert cfg["screening"] == esom.ESOM_SCREEN_TF32 and ref[3]["screening"] == 0
+    assert cfg["screening"] == mode and ref[3]["screening"] == 0
     frac = cfg["stats"]["rescans"] / max(cfg["stats"]["points"], 1)
-    print("TC", json.dumps({"label": label, "n": w.n, "d": w.d, "L": w.L, "k": w.k,
+    print("TC", json.dumps({"label": label, "mode": {1: "tf32", 2: "bf16"}[mode],
+                            "n": w.n, "d": w.d, "L": w.L, "k": w.k,
                             "rescan_fraction": frac, "blocks_per_sm": cfg["blocks_per_sm"],
                             "shared_bytes": cfg["shared_bytes"]}))
     assert np.array_equal(got[1], ref[1]), "k-NN indices differ from the FP32 path"
@@ -208,14 +210,14 @@ def test_split_equals_fused(esom, case):
 
 @pytest.mark.parametrize("name", ["mixture30_d16", "uniform_d16"])
 def test_tune_picks_a_plan_with_the_same_bits(esom, name):
-    """esom_tune times the fused, split and tensor-core plans on the points,
+    """esom_tune times the fused, split, TF32 and BF16 plans on the points,
     keeps the fastest, and every plan gives the same coordinates."""
     w = workloads.make(name, n=200_000)
     X = torch.from_numpy(w.X).cuda()
     with esom.Projector(w.d, w.L, w.k) as P:
         P.set_landmarks(torch.from_numpy(w.hi).cuda(), torch.from_numpy(w.lo).cuda())
         outs = {}
-        for plan in (esom.ESOM_PLAN_FUSED, esom.ESOM_PLAN_SPLIT, esom.ESOM_PLAN_TF32):
+        for plan in esom.PLAN_NAMES:
             P.set_plan(plan)
             assert P.config()["plan"] == plan
             outs[plan] = P.project(X, w.boost, w.adjust).cpu().numpy()
@@ -225,3 +227,23 @@ def test_tune_picks_a_plan_with_the_same_bits(esom, name):
         print("TUNE", name, esom.PLAN_NAMES[chosen])
     for o in outs.values():
         assert np.array_equal(o.view(np.uint32), got.view(np.uint32))
+
+
+
+@pytest.mark.parametrize("d,L,k", [(4, 300, 10), (12, 70, 8), (16, 1024, 20), (20, 129, 20),
+                                   (28, 64, 32), (32, 500, 16), (36, 500, 16), (52, 200, 12),
+                                   (64, 333, 20), (8, 2, 2)])
+def test_bf16_shapes_equal_fp32(esom, d, L, k):
+    """BF16 screening (half the operand bytes, 64-byte rows up to d = 32)
+    gives the FP32 path's bits too; its larger error bound only shows in the
+    rescan rate."""
+    r = np.random.default_rng(d * 1000 + L + 7)
+    w = workloads.random_case(r, 3000, d, L, k, boost=1.5, adjust=0.5)
+    same_as_fp32(esom, w, f"bf16 random d={d} L={L} k={k}", max_rescans=0.5,
+                 mode=esom.ESOM_SCREEN_BF16)
+
+
+@pytest.mark.parametrize("name", ["mixture30_d16", "student50_d32"])
+def test_bf16_named_equal_fp32(esom, name):
+    w = workloads.make(name, n=100_000)
+    same_as_fp32(esom, w, f"bf16 {name}", max_rescans=0.2, mode=esom.ESOM_SCREEN_BF16)
