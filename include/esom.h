@@ -196,6 +196,18 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream);
  * Errors: ESOM_ENOMEM, ESOM_EUNSUPPORTED, ESOM_ECUDA. */
 esom_status esom_set_split(esom_handle h, int on);
 
+/* on != 0: from the next esom_set_landmarks on, the handle centres the data
+ * on c = the landmarks' mean rounded to integers: it stores the landmark
+ * rows minus c and every kernel subtracts c from the points it loads
+ * (distances do not change; FP32 rounding does, slightly).  The screening
+ * error bound grows with |x| max|l|, so data far from the origin fail the
+ * certificate often and are rescanned; centred, they do not.  Integer c
+ * keeps integer-valued data exact.  Off by default.  All plans of the
+ * handle agree bit for bit either way, and esom_batch_* groups follow the
+ * setting of each member's landmark handle; esom_project_noalloc does not
+ * centre.  Errors: ESOM_ENOMEM. */
+esom_status esom_set_centering(esom_handle h, int on);
+
 /* Execution plans of esom_project: one fused FP32 kernel, FP32 k-NN kernel +
  * projection kernel, tensor-core k-NN (TF32 or BF16) + projection kernel.  All give the
  * same bits; which is fastest depends on d, L and k (tensor cores pay at

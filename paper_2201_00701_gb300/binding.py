@@ -106,6 +106,7 @@ def load(build_if_missing: bool = False):
         "esom_get_stats": ([P, P, ctypes.POINTER(_Stats), I], I),
         "esom_set_screening": ([P, I, P], I),
         "esom_set_split": ([P, I], I),
+        "esom_set_centering": ([P, I], I),
         "esom_tune": ([P, P, I64, P, F, F, P, ctypes.POINTER(I)], I),
         "esom_batch_create": ([ctypes.POINTER(BatchItem), I, I, ctypes.POINTER(P)], I),
         "esom_batch_run": ([P, P], I),
@@ -206,6 +207,11 @@ def esom_set_screening(h, mode: int, stream: int = 0) -> int:
 def esom_set_split(h, on: bool) -> int:
     """Two kernels (k-NN, then projection from neighbours) instead of one."""
     return load().esom_set_split(h, int(on))
+
+
+def esom_set_centering(h, on: bool) -> int:
+    """Centre the data on the landmarks' rounded mean (next set_landmarks on)."""
+    return load().esom_set_centering(h, int(on))
 
 
 def esom_tune(h, points_ptr: int, n: int, out_ptr: int, boost: float, adjust: float,
@@ -420,6 +426,9 @@ class Projector:
 
     def set_split(self, on: bool):
         check(esom_set_split(self.h, on))
+
+    def set_centering(self, on: bool):
+        check(esom_set_centering(self.h, on))
 
     def set_plan(self, plan: int):
         """ESOM_PLAN_FUSED, _SPLIT, _TF32 or _BF16."""

@@ -64,6 +64,7 @@ void fill_args(const esom_ctx *h, const float *points, long long n, float *out, 
     // in shared memory (streamed chunks); with resident rows recomputing from
     // shared memory is faster than the L2 gathers.
     a->qtab = h->nchunks > 1 ? h->qtab : nullptr;
+    a->center = h->centered ? h->center : nullptr;
     a->tc_chunks = (h->L + kTcN - 1) / kTcN;
 }
 
@@ -77,7 +78,7 @@ int set_error(int s, const char *msg) {
 // patterns), and the row rewritten in place with its chunks swizzled.
 __global__ void landmark_prep_kernel(float *__restrict__ hi, int L, int D,
                                      float *__restrict__ norms, float *__restrict__ lmax,
-                                     int padded) {
+                                     int padded, const float *__restrict__ center) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= padded) return;
     if (j >= L) {
@@ -91,7 +92,7 @@ __global__ void landmark_prep_kernel(float *__restrict__ hi, int L, int D,
     const int c = D / 4;
     float s = 0.f;
     for (int e = 0; e < c; ++e) {
-        buf[e] = row[e];
+        buf[e] = centred(row[e], center, e);
         s = fmaf(buf[e].x, buf[e].x, s);
         s = fmaf(buf[e].y, buf[e].y, s);
         s = fmaf(buf[e].z, buf[e].z, s);
@@ -104,10 +105,27 @@ __global__ void landmark_prep_kernel(float *__restrict__ hi, int L, int D,
 }
 
 cudaError_t launch_landmark_prep(float *hi, int L, int D, float *norms, float *lmax,
-                                 cudaStream_t stream, int pad) {
+                                 cudaStream_t stream, int pad, const float *center) {
     const int padded = (L + pad - 1) / pad * pad;
     landmark_prep_kernel<<<(padded + 255) / 256, 256, 0, stream>>>(hi, L, D, norms, lmax,
-                                                                   padded);
+                                                                   padded, center);
+    return cudaGetLastError();
+}
+
+// One thread per coordinate: the landmarks' mean, summed in FP64 in landmark
+// order (deterministic), rounded to the nearest integer.
+__global__ void landmark_center_kernel(const float *__restrict__ hi, int L, int D,
+                                       float *__restrict__ center) {
+    const int i = threadIdx.x;
+    if (i >= D) return;
+    double sum = 0.0;
+    for (int j = 0; j < L; ++j) sum += (double)hi[(size_t)j * D + i];
+    center[i] = (float)rint(sum / (double)L);
+}
+
+cudaError_t launch_landmark_center(const float *hi, int L, int D, float *center,
+                                   cudaStream_t stream) {
+    landmark_center_kernel<<<1, 64, 0, stream>>>(hi, L, D, center);
     return cudaGetLastError();
 }
 
@@ -383,9 +401,15 @@ esom_status esom_set_landmarks(esom_handle h, const float *hi, const float *lo,
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->lo, lo, (size_t)h->L * 2 * sizeof(float), cudaMemcpyDefault, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status + 1, 0, sizeof(float), st);
+    // centring: the centre of these landmarks, subtracted from the rows here
+    // and from the points by every kernel
+    h->centered = h->centering;
+    if (e == cudaSuccess && h->centered)
+        e = esom::launch_landmark_center(h->hi, h->L, h->d, h->center, st);
     if (e == cudaSuccess) e = esom::launch_landmark_prep(h->hi, h->L, h->d, h->norms,
                                                          reinterpret_cast<float *>(h->status + 1), st,
-                                                         esom::kTcN);
+                                                         esom::kTcN,
+                                                         h->centered ? h->center : nullptr);
     if (e == cudaSuccess && h->qtab) e = h->ops->launch_qtab(h->hi, h->L, h->qtab, st);
     if (e == cudaSuccess && h->screening)
         e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, tc_prec(h->screening), st);
@@ -608,6 +632,21 @@ esom_status prepare_split(esom_ctx *h) {
 }
 }  // namespace
 
+esom_status esom_set_centering(esom_handle h, int on) {
+    if (!h) return fail(ESOM_EINVAL, "null handle");
+    esom_status s = check_device(h);
+    if (s != ESOM_OK) return s;
+    if (on && !h->center) {
+        const cudaError_t e = cudaMalloc(&h->center, ESOM_MAX_D * sizeof(float));
+        if (e != cudaSuccess) {
+            h->center = nullptr;
+            return fail(ESOM_ENOMEM, "device allocation of the centre: %s", cudaGetErrorString(e));
+        }
+    }
+    h->centering = on ? 1 : 0;
+    return ESOM_OK;
+}
+
 esom_status esom_set_split(esom_handle h, int on) {
     if (!h) return fail(ESOM_EINVAL, "null handle");
     esom_status s = check_device(h);
@@ -756,6 +795,7 @@ esom_status esom_destroy(esom_handle h) {
     cudaFree(h->tc_idx);
     cudaFree(h->tc_d2);
     cudaFree(h->fail_list);
+    cudaFree(h->center);
     for (int b = 0; b < 2; ++b) {
         cudaFree(h->stage_x[b]);
         cudaFree(h->stage_out[b]);

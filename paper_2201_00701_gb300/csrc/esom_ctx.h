@@ -27,6 +27,10 @@ struct esom_ctx {
     // chunk images while it is on
     int screening = 0;
     int split = 0;  // k-NN kernel + projection kernel instead of the fused one
+    // centring (esom_set_centering): requested, and in effect for the
+    // landmarks now stored (set by esom_set_landmarks)
+    int centering = 0, centered = 0;
+    float *center = nullptr;  // ESOM_MAX_D floats
     const esom::TcOps *tc = nullptr;
     unsigned char *img = nullptr;
     int tc_blocks_per_sm = 0;

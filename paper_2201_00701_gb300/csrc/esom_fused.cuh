@@ -934,7 +934,8 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
         float4 xr[D / 4];
         const float4 *xs = reinterpret_cast<const float4 *>(sX) + (size_t)tid * (D / 4);
 #pragma unroll
-        for (int e = 0; e < D / 4; ++e) xr[e] = active ? xs[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = 0; e < D / 4; ++e)
+            xr[e] = active ? centred(xs[e], a.center, e) : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();  // point tile consumed; abort flag visible
         if (s_abort) {
             abort_block();
@@ -1169,7 +1170,8 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchArgs B
         float4 xr[D / 4];
         const float4 *xs = reinterpret_cast<const float4 *>(sX) + (size_t)tid * (D / 4);
 #pragma unroll
-        for (int e = 0; e < D / 4; ++e) xr[e] = active ? xs[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = 0; e < D / 4; ++e)
+            xr[e] = active ? centred(xs[e], a.center, e) : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();  // point tile consumed; abort flag visible
         if (s_abort) {
             abort_block();
@@ -1419,7 +1421,7 @@ __global__ void __launch_bounds__(256) rescan_kernel(const FusedArgs a) {
         const float4 *xp = reinterpret_cast<const float4 *>(a.X) + row * (D / 4);
         float4 x[D / 4];
 #pragma unroll
-        for (int e = 0; e < D / 4; ++e) x[e] = __ldg(xp + e);
+        for (int e = 0; e < D / 4; ++e) x[e] = centred(__ldg(xp + e), a.center, e);
         unsigned long long best[KK];
 #pragma unroll
         for (int t = 0; t < KK; ++t) best[t] = ~0ull;

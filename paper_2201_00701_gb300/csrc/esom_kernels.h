@@ -45,7 +45,17 @@ struct FusedArgs {
     // *fail_count; rescan_kernel then finds its neighbours exactly
     long long *fail_list;
     unsigned *fail_count;
+    // when set, the landmark rows are stored centred on this point (d floats,
+    // 16-byte aligned) and every kernel subtracts it from the points it loads
+    const float *center;
 };
+
+// x - c, four at a time (c may be null: no centring).
+__device__ __forceinline__ float4 centred(float4 x, const float *c, int e) {
+    if (!c) return x;
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(c) + e);
+    return make_float4(x.x - v.x, x.y - v.y, x.z - v.z, x.w - v.w);
+}
 
 // Many datasets of one (D, list capacity) in one launch: every block walks a
 // contiguous range [cta_begin[b], cta_begin[b+1]) of the global tile list;
@@ -178,9 +188,15 @@ int set_error(int s, const char *msg);
 
 // Squared landmark norms (norms[j], j < L; NaN padding up to a multiple of
 // `pad`, itself a multiple of 4), the largest norm (*lmax, which must hold 0
-// on entry), and the rows of hi swizzled in place (see swz).
+// on entry), and the rows of hi swizzled in place (see swz) -- after
+// subtracting `center` from them when it is given.
 cudaError_t launch_landmark_prep(float *hi, int L, int D, float *norms, float *lmax,
-                                 cudaStream_t stream, int pad = 4);
+                                 cudaStream_t stream, int pad = 4, const float *center = nullptr);
+
+// center[i] = the landmarks' mean coordinate i rounded to an integer (FP64
+// sums in landmark order; integers keep integer-valued data exact).
+cudaError_t launch_landmark_center(const float *hi, int L, int D, float *center,
+                                   cudaStream_t stream);
 
 // Landmark rows are stored with their 16-byte chunks permuted: logical chunk
 // e of row j sits at physical chunk e ^ swz(j), with g = gcd(d/4, 8) and

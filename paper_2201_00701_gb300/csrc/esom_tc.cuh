@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                         const int e = b0 / (4 * EB) + q;  // float4 index of the row
                         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (e < D / 4 && act) {
-                            v = __ldg(xp + e);
+                            v = centred(__ldg(xp + e), a.center, e);
                             xx = fmaf(v.x, v.x, xx);
                             xx = fmaf(v.y, v.y, xx);
                             xx = fmaf(v.z, v.z, xx);
@@ -518,7 +518,8 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
             const float4 *xp = reinterpret_cast<const float4 *>(a.X) + (active ? row : 0) * (D / 4);
 #pragma unroll
             for (int e = 0; e < D / 4; ++e)
-                xr[e] = active ? __ldg(xp + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+                xr[e] = active ? centred(__ldg(xp + e), a.center, e)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
             float sd[KK];
             int si[KK];
             const bool cert = rerank<D, KC, KK>(xr, keys, Lg, mask, a.L, a.k, M, q, sd, si, xx);
