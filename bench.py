@@ -33,8 +33,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "mixture30_d16"
-PROFILES = {"fp32": os.path.join(ROOT, "profiles", "fused_kernel_mixture30_d16.txt"),
-            "tf32": os.path.join(ROOT, "profiles", "tc_knn_kernel_mixture30_d16.txt")}
+PROFILES = {"fused": os.path.join(ROOT, "profiles", "fused_kernel_mixture30_d16.txt"),
+            "tf32": os.path.join(ROOT, "profiles", "tc_knn_kernel_mixture30_d16.txt"),
+            "bf16": os.path.join(ROOT, "profiles", "tc_knn_kernel_bf16_mixture30_d16.txt")}
 
 
 def baseline_metric():
@@ -45,9 +46,17 @@ def baseline_metric():
         return "points/s projected"
 
 
+# The sources that define the profiled kernels (fused_kernel, tc_kernel,
+# project_kernel, rescan_kernel at d = 16): a change to any of them makes the
+# committed DRAM counters stale.
+KERNEL_SOURCES = ("esom_kernels.h", "esom_fused.cuh", "esom_tc.cuh", "esom_k_d16.cu",
+                  "esom_tc_d16.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2201_00701_gb300", "csrc", "*"))):
+    for name in KERNEL_SOURCES:
+        p = os.path.join(ROOT, "paper_2201_00701_gb300", "csrc", name)
         with open(p, "rb") as f:
             h.update(os.path.basename(p).encode())
             h.update(f.read())
@@ -207,6 +216,59 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def time_ablations(binding, P, X, w, flush, stream, reps, knn_ms, screen):
+    """The paper's alternative kernels on the benchmark's points (Section
+    4.2 k-NN algorithms, Section 4.3 projection algorithms), each timed by
+    CUDA events over `reps` launches after one warm-up, L2 flushed before
+    each: the k-NN by Base and Bitonic against the plan's own k-NN, and steps
+    2-4 from the same neighbours by the library's projection kernel and by
+    Registers.  Also checks that the variants' neighbours are the library's."""
+    import torch
+
+    n, k = w.n, w.k
+    dev = X.device
+    sid = stream.cuda_stream
+
+    def timed(fn):
+        ms = []
+        for i in range(1 + reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 1:
+                ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    idx = torch.empty((n, k), dtype=torch.int32, device=dev)
+    d2 = torch.empty((n, k), dtype=torch.float32, device=dev)
+    binding.check(binding.esom_knn(P.h, X.data_ptr(), n, idx.data_ptr(), d2.data_ptr(), sid))
+    vi, vd = torch.empty_like(idx), torch.empty_like(d2)
+    knn = {f"library_{screen}": knn_ms}
+    same = True
+    for name, v in (("base", binding.ESOM_KNN_BASE), ("bitonic", binding.ESOM_KNN_BITONIC)):
+        knn[name] = timed(lambda v=v: binding.check(binding.esom_knn_variant(
+            P.h, v, X.data_ptr(), n, vi.data_ptr(), vd.data_ptr(), sid)))
+        same = same and torch.equal(vi, idx) and torch.equal(vd, d2)
+    outs, proj = {}, {}
+    for name, v in (("library_table", binding.ESOM_PROJ_TABLE),
+                    ("registers", binding.ESOM_PROJ_REGISTERS)):
+        o = torch.empty((n, 2), dtype=torch.float32, device=dev)
+        proj[name] = timed(lambda v=v, o=o: binding.check(binding.esom_project_knn(
+            P.h, v, X.data_ptr(), n, idx.data_ptr(), d2.data_ptr(), o.data_ptr(), w.boost,
+            w.adjust, sid)))
+        outs[name] = o
+    torch.cuda.synchronize()
+    if P.device_status() != 0:
+        raise RuntimeError("device status flag raised by the ablation kernels")
+    dev_max = float((outs["registers"] - outs["library_table"]).abs().max())
+    return {"knn_ms": knn, "projection_ms": proj, "neighbours_identical": bool(same),
+            "registers_vs_library_max_abs": dev_max, "launches_timed": reps,
+            "paper_sections": "4.2 (Base, Bitonic k-NN), 4.3 (Registers projection)"}
+
+
 def run_esom(args, world, rank, local):
     import torch
     import torch.distributed as dist
@@ -309,6 +371,9 @@ def run_esom(args, world, rank, local):
             knn_ms.append(e0.elapsed_time(e1))
     del idx_buf
 
+    ablations = None if args.no_ablations else time_ablations(
+        binding, P, X, w, flush, stream, min(args.steps, 5), float(np.median(knn_ms)), screen)
+
     # end to end through the host-buffer entry point (pinned host memory)
     Xh = torch.from_numpy(w.X).pin_memory()
     outh = torch.empty((n, 2), dtype=torch.float32).pin_memory()
@@ -344,8 +409,8 @@ def run_esom(args, world, rank, local):
             roof_note = (f"n*L*d on {screen.upper()} tensor cores at {tf32_peak:.0f} TFLOP/s "
                          f"(the measured sustained BF16 rate{', halved' if screen == 'tf32' else ''}"
                          f") + n*k^2*d on the FP32 lanes at {alu_peak:.1f} TFLOP/s")
-        traffic = (profile_traffic("tf32" if screen == "tf32" else "fp32")
-                   if args.workload == WORKLOAD and screen in ("tf32", "fused") else None)
+        traffic = (profile_traffic(screen)
+                   if args.workload == WORKLOAD and screen in PROFILES else None)
         line = {
             "metric": baseline_metric(), "value": value, "unit": "points/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -371,6 +436,7 @@ def run_esom(args, world, rank, local):
                            "p99": float(np.percentile(step_ms, 99)),
                            "rsd": float(np.std(step_ms) / np.mean(step_ms))},
             "wall_s_timed_region": wall,
+            "ablations": ablations,
             "phases_ms": {"knn_only": float(np.median(knn_ms)),
                           "projection_share": 1.0 - float(np.median(knn_ms))
                           / float(np.median(step_ms))},
@@ -593,6 +659,8 @@ def main():
     ap.add_argument("--ref-points", type=int, default=4000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ablations", action="store_true",
+                    help="skip timing the paper's alternative kernels")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "student50_d32", "batch64", "serve8"])
     ap.add_argument("--batch-n-max", type=float, default=2e6)

@@ -196,6 +196,42 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream);
  * Errors: ESOM_ENOMEM, ESOM_EUNSUPPORTED, ESOM_ECUDA. */
 esom_status esom_set_split(esom_handle h, int on);
 
+/* The paper's alternative kernel designs, for ablation (Section 4.2 k-NN
+ * algorithms, Section 4.3 projection algorithms).
+ *
+ * esom_knn_variant: the k nearest landmarks of each point, as esom_knn
+ * returns them (same layout, same indices and distances bit for bit: the
+ * exact FP32 squared distances ranked by (distance, index)), computed by
+ *   ESOM_KNN_BASE     one thread per point, insertion into a sorted array
+ *                     of k, landmark rows from global memory;
+ *   ESOM_KNN_BITONIC  next_pow2(k) threads per point, bitonic sort of each
+ *                     block of that many distances and a bitonic merge into
+ *                     the best block so far.
+ * idx (n x k int32) and dist2 (n x k float, nullable) are device memory,
+ * 4-byte aligned; points as for esom_project.  Finite inputs only.
+ *
+ * esom_project_knn: steps 2-4 (scores, pair sums, solve) from neighbours
+ * the caller gives (idx, dist2: n x k, device memory, 16-byte aligned, the
+ * exact squared distances esom_knn returns, ascending), writing out (n x 2):
+ *   ESOM_PROJ_TABLE      the library's projection kernel: one thread per
+ *                        point, D_uv from the law of cosines and the table
+ *                        of squared landmark distances; with esom_knn's
+ *                        neighbours the result equals esom_project's bits;
+ *   ESOM_PROJ_REGISTERS  one warp per point, pairs in 2 x 2 blocks, D_uv by
+ *                        direct dot products over d; equal to the former
+ *                        within FP32 rounding.
+ * Indices outside [0, L) are clamped.  Errors: ESOM_EINVAL (unknown
+ * variant, null pointer, boost/adjust as for esom_project), ESOM_EALIGN. */
+#define ESOM_KNN_BASE 1
+#define ESOM_KNN_BITONIC 2
+#define ESOM_PROJ_TABLE 0
+#define ESOM_PROJ_REGISTERS 1
+esom_status esom_knn_variant(esom_handle h, int variant, const float *points, int64_t n,
+                             int32_t *idx, float *dist2, esom_stream_t stream);
+esom_status esom_project_knn(esom_handle h, int variant, const float *points, int64_t n,
+                             const int32_t *idx, const float *dist2, float *out, float boost,
+                             float adjust, esom_stream_t stream);
+
 /* on != 0: from the next esom_set_landmarks on, the handle centres the data
  * on c = the landmarks' mean rounded to integers: it stores the landmark
  * rows minus c and every kernel subtracts c from the points it loads

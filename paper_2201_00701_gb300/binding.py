@@ -32,6 +32,10 @@ ESOM_PLAN_FUSED = 0
 ESOM_PLAN_SPLIT = 1
 ESOM_PLAN_TF32 = 2
 ESOM_PLAN_BF16 = 3
+ESOM_KNN_BASE = 1
+ESOM_KNN_BITONIC = 2
+ESOM_PROJ_TABLE = 0
+ESOM_PROJ_REGISTERS = 1
 PLAN_NAMES = {ESOM_PLAN_FUSED: "fused", ESOM_PLAN_SPLIT: "split", ESOM_PLAN_TF32: "tf32",
               ESOM_PLAN_BF16: "bf16"}
 
@@ -98,6 +102,8 @@ def load(build_if_missing: bool = False):
         "esom_landmark_version": ([P], ctypes.c_uint64),
         "esom_project": ([P, P, I64, P, F, F, P], I),
         "esom_knn": ([P, P, I64, P, P, P], I),
+        "esom_knn_variant": ([P, I, P, I64, P, P, P], I),
+        "esom_project_knn": ([P, I, P, I64, P, P, P, F, F, P], I),
         "esom_project_host": ([P, P, I64, P, F, F, P], I),
         "esom_device_status": ([P, P], I),
         "esom_set_landmark_chunk": ([P, I], I),
@@ -170,6 +176,19 @@ def esom_project(h, points_ptr: int, n: int, out_ptr: int, boost: float, adjust:
 def esom_knn(h, points_ptr: int, n: int, idx_ptr: int, dist2_ptr: int | None,
              stream: int = 0) -> int:
     return load().esom_knn(h, points_ptr, n, idx_ptr, dist2_ptr, stream)
+
+
+def esom_knn_variant(h, variant: int, points_ptr: int, n: int, idx_ptr: int,
+                     dist2_ptr: int | None, stream: int = 0) -> int:
+    """The k-NN by one of the paper's alternative kernels (ablation)."""
+    return load().esom_knn_variant(h, variant, points_ptr, n, idx_ptr, dist2_ptr, stream)
+
+
+def esom_project_knn(h, variant: int, points_ptr: int, n: int, idx_ptr: int, dist2_ptr: int,
+                     out_ptr: int, boost: float, adjust: float, stream: int = 0) -> int:
+    """Steps 2-4 from given neighbours, by the library's or the paper's kernel."""
+    return load().esom_project_knn(h, variant, points_ptr, n, idx_ptr, dist2_ptr, out_ptr,
+                                   boost, adjust, stream)
 
 
 def esom_project_host(h, points_ptr: int, n: int, out_ptr: int, boost: float, adjust: float,
@@ -399,6 +418,32 @@ class Projector:
         check(esom_knn(self.h, X.data_ptr(), X.shape[0], idx.data_ptr(),
                        d2.data_ptr() if d2 is not None else None, self._stream()))
         return idx, d2
+
+    def knn_variant(self, X, variant: int, with_dist: bool = True):
+        """esom_knn by ESOM_KNN_BASE or ESOM_KNN_BITONIC (same results)."""
+        import torch
+        X = self._points(X)
+        idx = torch.empty((X.shape[0], self.k), dtype=torch.int32, device=X.device)
+        d2 = (torch.empty((X.shape[0], self.k), dtype=torch.float32, device=X.device)
+              if with_dist else None)
+        check(esom_knn_variant(self.h, variant, X.data_ptr(), X.shape[0], idx.data_ptr(),
+                               d2.data_ptr() if d2 is not None else None, self._stream()))
+        return idx, d2
+
+    def project_knn(self, X, idx, d2, variant: int = ESOM_PROJ_TABLE, boost: float = 1.0,
+                    adjust: float = 1.0, out=None):
+        """Steps 2-4 from the neighbours idx / d2 (n x k, as knn returns)."""
+        import torch
+        X = self._points(X)
+        n = X.shape[0]
+        for t, dt in ((idx, torch.int32), (d2, torch.float32)):
+            if not (t.is_cuda and t.dtype == dt and t.shape == (n, self.k) and t.is_contiguous()):
+                raise ValueError(f"neighbours must be contiguous CUDA {dt} tensors n x {self.k}")
+        if out is None:
+            out = torch.empty((n, 2), dtype=torch.float32, device=X.device)
+        check(esom_project_knn(self.h, variant, X.data_ptr(), n, idx.data_ptr(), d2.data_ptr(),
+                               out.data_ptr(), boost, adjust, self._stream()))
+        return out
 
     def project_host(self, X_host, boost: float = 1.0, adjust: float = 1.0, out_host=None):
         """Host (CPU) tensors in and out; pinned memory overlaps the copies."""

@@ -10,6 +10,7 @@
 #include "esom.h"
 #include "esom_ctx.h"
 #include "esom_kernels.h"
+#include "esom_variants.h"
 
 using esom::FusedArgs;
 using esom::KernelOps;
@@ -244,6 +245,20 @@ esom_status check_device(const esom_ctx *h) {
     return ESOM_OK;
 }
 
+// Projection from given neighbours by the library's kernel (one thread per
+// point, distance table), the launch the split path makes after its k-NN.
+esom_status launch_projection(esom_ctx *h, FusedArgs p, cudaStream_t stream) {
+    const bool res = h->nchunks == 1 && esom::project_smem_bytes(h->d, h->L, true) <= h->proj_smem;
+    p.nchunks = res ? 1 : 2;
+    p.qtab = h->qtab;
+    p.mode = esom::kProject;
+    p.ntiles = (p.n + esom::kThreads - 1) / esom::kThreads;
+    long long grid = (long long)h->proj_blocks_per_sm * h->num_sms;
+    if (grid > p.ntiles) grid = p.ntiles;
+    const cudaError_t e = h->ops->launch_proj(p, (int)grid, h->proj_smem, stream);
+    return e == cudaSuccess ? ESOM_OK : cuda_fail(e, "projection kernel launch");
+}
+
 esom_status launch(esom_ctx *h, const float *points, long long n, float *out, int *idx,
                    float *dist2, float boost, float adjust, int mode, cudaStream_t stream) {
     FusedArgs a;
@@ -302,19 +317,12 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                 if (e != cudaSuccess) break;
                 FusedArgs p = k;
                 p.out = out + off * 2;
-                p.mode = esom::kProject;
-                // rows resident when they fit the configured shared memory
-                const bool res = h->nchunks == 1 &&
-                                 esom::project_smem_bytes(h->d, h->L, true) <= h->proj_smem;
-                p.nchunks = res ? 1 : 2;
+                // rows resident when they fit the configured shared memory;
                 // the projection kernel reads the distance table whenever
                 // there is one (measured 22% faster than recomputing from
                 // resident rows at mixture30_d16; the values are the same)
-                p.qtab = h->qtab;
-                p.ntiles = (cnt + esom::kThreads - 1) / esom::kThreads;
-                long long grid = (long long)h->proj_blocks_per_sm * h->num_sms;
-                if (grid > p.ntiles) grid = p.ntiles;
-                e = h->ops->launch_proj(p, (int)grid, h->proj_smem, stream);
+                const esom_status ps = launch_projection(h, p, stream);
+                if (ps != ESOM_OK) return ps;
             }
         }
     } else {
@@ -597,7 +605,9 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg) {
 namespace {
 // Configures the projection-from-neighbours kernel and allocates the
 // neighbour scratch of the split (two-kernel) execution.
-esom_status prepare_split(esom_ctx *h) {
+// Launch configuration of the projection kernel (steps 2-4 from given
+// neighbours).
+esom_status prepare_projection(esom_ctx *h) {
     int optin = 0;
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(shared memory opt-in)");
@@ -611,6 +621,17 @@ esom_status prepare_split(esom_ctx *h) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pbps, h->ops->proj_func, esom::kThreads, psmem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (pbps < 1) return fail(ESOM_EUNSUPPORTED, "projection launch does not fit on an SM");
+    h->proj_smem = psmem;
+    h->proj_blocks_per_sm = pbps;
+    return ESOM_OK;
+}
+
+// The split execution: the projection kernel's configuration and the
+// neighbour scratch of one pass.
+esom_status prepare_split(esom_ctx *h) {
+    esom_status s = prepare_projection(h);
+    if (s != ESOM_OK) return s;
+    cudaError_t e = cudaSuccess;
     if (!h->tc_idx) {
         e = cudaMalloc(&h->tc_idx, (size_t)esom::kTcPass * h->k * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&h->tc_d2, (size_t)esom::kTcPass * h->k * sizeof(float));
@@ -626,11 +647,70 @@ esom_status prepare_split(esom_ctx *h) {
                         cudaGetErrorString(e));
         }
     }
-    h->proj_smem = psmem;
-    h->proj_blocks_per_sm = pbps;
     return ESOM_OK;
 }
+
 }  // namespace
+
+esom_status esom_knn_variant(esom_handle h, int variant, const float *points, int64_t n,
+                             int32_t *idx, float *dist2, esom_stream_t stream) {
+    esom_status s = check_common(h, points, n);
+    if (s != ESOM_OK) return s;
+    if (variant != ESOM_KNN_BASE && variant != ESOM_KNN_BITONIC)
+        return fail(ESOM_EINVAL, "unknown k-NN variant %d", variant);
+    if (n > 0 && !idx) return fail(ESOM_EINVAL, "null idx");
+    if (((uintptr_t)idx & 3u) != 0 || ((uintptr_t)dist2 & 3u) != 0)
+        return fail(ESOM_EALIGN, "idx and dist2 must be 4-byte aligned");
+    if (n == 0) return ESOM_OK;
+    const esom::VariantOps *v = esom::variant_ops(h->d);
+    if (!v) return fail(ESOM_EUNSUPPORTED, "no variant kernels for d = %d", h->d);
+    FusedArgs a;
+    esom::fill_args(h, points, n, nullptr, 1.0f, 1.0f, &a);
+    a.idx = idx;
+    a.dist2 = dist2;
+    a.mode = esom::kKnn;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const cudaError_t e = variant == ESOM_KNN_BASE ? v->knn_base(a, st) : v->knn_bitonic(a, st);
+    if (e != cudaSuccess) return cuda_fail(e, "k-NN variant launch");
+    return ESOM_OK;
+}
+
+esom_status esom_project_knn(esom_handle h, int variant, const float *points, int64_t n,
+                             const int32_t *idx, const float *dist2, float *out, float boost,
+                             float adjust, esom_stream_t stream) {
+    esom_status s = check_common(h, points, n);
+    if (s != ESOM_OK) return s;
+    if (variant != ESOM_PROJ_TABLE && variant != ESOM_PROJ_REGISTERS)
+        return fail(ESOM_EINVAL, "unknown projection variant %d", variant);
+    if (n > 0 && (!idx || !dist2 || !out)) return fail(ESOM_EINVAL, "null idx, dist2 or out");
+    if ((((uintptr_t)idx | (uintptr_t)dist2) & 15u) != 0)
+        return fail(ESOM_EALIGN, "idx and dist2 must be 16-byte aligned");
+    if (((uintptr_t)out & 7u) != 0) return fail(ESOM_EALIGN, "out must be 8-byte aligned");
+    if (!(boost > 0.0f) || !(boost < INFINITY)) return fail(ESOM_EINVAL, "boost must be > 0");
+    if (!(adjust >= 0.0f) || !(adjust < INFINITY)) return fail(ESOM_EINVAL, "adjust must be >= 0");
+    if (n == 0) return ESOM_OK;
+    FusedArgs p;
+    esom::fill_args(h, points, n, out, boost, adjust, &p);
+    p.idx = const_cast<int *>(idx);
+    p.dist2 = const_cast<float *>(dist2);
+    p.mode = esom::kProject;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (variant == ESOM_PROJ_TABLE) {
+        if (h->proj_smem == 0) {
+            s = prepare_projection(h);
+            if (s != ESOM_OK) return s;
+        }
+        s = launch_projection(h, p, st);
+        if (s != ESOM_OK) return s;
+    } else {
+        const esom::VariantOps *v = esom::variant_ops(h->d);
+        if (!v) return fail(ESOM_EUNSUPPORTED, "no variant kernels for d = %d", h->d);
+        const cudaError_t e = v->project_registers(p, st);
+        if (e != cudaSuccess) return cuda_fail(e, "projection variant launch");
+    }
+    h->points += (uint64_t)n;
+    return ESOM_OK;
+}
 
 esom_status esom_set_centering(esom_handle h, int on) {
     if (!h) return fail(ESOM_EINVAL, "null handle");

@@ -1,5 +1,6 @@
 // Maps (D, list capacity) to the kernel instantiation compiled for it.
 #include "esom_kernels.h"
+#include "esom_variants.h"
 
 namespace esom {
 
@@ -55,6 +56,34 @@ const TcOps *tc_ops(int D, int kc, int prec) {
         case 56: return tc_ops_d56(kc, prec);
         case 60: return tc_ops_d60(kc, prec);
         case 64: return tc_ops_d64(kc, prec);
+        default: return nullptr;
+    }
+}
+
+#define ESOM_DECLARE_VAR_D(DV) const VariantOps *variant_ops_d##DV();
+ESOM_DECLARE_VAR_D(4) ESOM_DECLARE_VAR_D(8) ESOM_DECLARE_VAR_D(12) ESOM_DECLARE_VAR_D(16)
+ESOM_DECLARE_VAR_D(20) ESOM_DECLARE_VAR_D(24) ESOM_DECLARE_VAR_D(28) ESOM_DECLARE_VAR_D(32)
+ESOM_DECLARE_VAR_D(36) ESOM_DECLARE_VAR_D(40) ESOM_DECLARE_VAR_D(44) ESOM_DECLARE_VAR_D(48)
+ESOM_DECLARE_VAR_D(52) ESOM_DECLARE_VAR_D(56) ESOM_DECLARE_VAR_D(60) ESOM_DECLARE_VAR_D(64)
+
+const VariantOps *variant_ops(int D) {
+    switch (D) {
+        case 4: return variant_ops_d4();
+        case 8: return variant_ops_d8();
+        case 12: return variant_ops_d12();
+        case 16: return variant_ops_d16();
+        case 20: return variant_ops_d20();
+        case 24: return variant_ops_d24();
+        case 28: return variant_ops_d28();
+        case 32: return variant_ops_d32();
+        case 36: return variant_ops_d36();
+        case 40: return variant_ops_d40();
+        case 44: return variant_ops_d44();
+        case 48: return variant_ops_d48();
+        case 52: return variant_ops_d52();
+        case 56: return variant_ops_d56();
+        case 60: return variant_ops_d60();
+        case 64: return variant_ops_d64();
         default: return nullptr;
     }
 }
