@@ -32,7 +32,20 @@ esom_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 // Points per chunk of the host-buffer pipeline.
-constexpr long long kHostChunk = 1 << 20;
+// Host-buffer pipeline: points move in chunks of at most kHostChunk (one
+// k-NN pass), the first and the last of one wave of the handle's k-NN kernel
+// (its resident blocks x the points of a tile), so that only a small input
+// copy precedes the first launch and a small output copy follows the last
+// one, and neither edge chunk leaves a partial wave; every other copy
+// overlaps a launch.
+constexpr long long kHostChunk = 1 << 19;
+
+long long host_chunk(long long p0, long long n, long long edge) {
+    const long long left = n - p0;
+    if (p0 == 0) return left < edge ? left : edge;
+    if (left <= edge) return left;
+    return left - edge < kHostChunk ? left - edge : kHostChunk;
+}
 
 // Operand precision of a tensor-core screening mode.
 int tc_prec(int screening) { return screening == ESOM_SCREEN_BF16 ? esom::kTcBf16 : esom::kTcTf32; }
@@ -491,9 +504,13 @@ esom_status esom_project_host(esom_handle h, const float *points_host, int64_t n
     if (e != cudaSuccess) return cuda_fail(e, "pipeline ordering");
     bool used[2] = {false, false};
     int c = 0;
-    for (long long p0 = 0; p0 < n; p0 += kHostChunk, ++c) {
+    long long edge = h->screening ? (long long)h->tc_blocks_per_sm * h->num_sms * esom::kTcRows
+                                  : (long long)h->blocks_per_sm * h->num_sms * esom::kThreads;
+    if (edge < 1 || edge > kHostChunk) edge = kHostChunk;
+    long long cnt = 0;
+    for (long long p0 = 0; p0 < n; p0 += cnt, ++c) {
         const int b = c & 1;
-        const long long cnt = n - p0 < kHostChunk ? n - p0 : kHostChunk;
+        cnt = host_chunk(p0, n, edge);
         // input copy waits until the previous result in this buffer left the device
         if (used[b]) e = cudaStreamWaitEvent(h->s_in, h->ev_free[b], 0);
         if (e == cudaSuccess)

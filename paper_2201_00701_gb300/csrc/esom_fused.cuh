@@ -1393,13 +1393,18 @@ cudaError_t launch_project(const FusedArgs &a, int grid, size_t smem, cudaStream
 
 // ---------------------------------------------------------------------------
 // Exact k-NN of the points whose screening certificate failed (deferred by
-// the k-NN kernels to keep their warps on the fast path), one warp per point:
-// FP32 difference-form distances to all L landmarks (dist2_row, the same
-// arithmetic as exact_rescan), each lane keeping the nearest KK of the
-// landmarks j = lane (mod 32), then KK rounds of a warp minimum over the
-// lanes' heads.  Keys are (distance bits << 32) | j: distances are >= 0, so
-// their bit patterns order like the values and ties go to the lower index,
-// as in exact_rescan.
+// the k-NN kernels to keep their warps on the fast path): FP32
+// difference-form distances to all L landmarks (dist2_row, the same
+// arithmetic as exact_rescan), each thread keeping the nearest KK of the
+// landmarks it scans, then k rounds of a warp minimum over the lanes' heads.
+// Keys are (distance bits << 32) | j: distances are >= 0, so their bit
+// patterns order like the values and ties go to the lower index, as in
+// exact_rescan.  With at most one failed point per block (the usual case:
+// a handful of points a pass) the whole block scans one point, j = thread
+// (mod 256), and warp 0 merges the eight warps' sorted lists from shared
+// memory, which cuts the serial chain of landmark loads eightfold; with more,
+// one warp scans each point, j = lane (mod 32).  Keys are unique, so both
+// give the same neighbours.
 
 __device__ __forceinline__ unsigned long long umin64(unsigned long long x, unsigned long long y) {
     return x < y ? x : y;
@@ -1408,47 +1413,98 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long x, unsig
     return x < y ? y : x;
 }
 
+// This thread's nearest KK (ascending keys) of the landmarks j0, j0 + step, ...
+template <int D, int KK>
+__device__ __forceinline__ void rescan_scan(const float4 (&x)[D / 4], const float4 *Lg, int L,
+                                            int j0, int step, unsigned long long (&best)[KK]) {
+#pragma unroll
+    for (int t = 0; t < KK; ++t) best[t] = ~0ull;
+    for (int j = j0; j < L; j += step) {
+        const float d2 = dist2_row<D>(x, Lg, j);
+        const unsigned long long key = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
+        if (key < best[KK - 1]) {
+            unsigned long long prev = best[0];
+            best[0] = umin64(key, best[0]);
+#pragma unroll
+            for (int t = 1; t < KK; ++t) {
+                const unsigned long long cur = best[t];
+                best[t] = umax64(prev, umin64(key, cur));
+                prev = cur;
+            }
+        }
+    }
+}
+
+// Round r of a warp's merge: the r-th smallest key over the lanes' lists
+// (every lane gets it); the lane that held it pops its head.
+template <int KK>
+__device__ __forceinline__ unsigned long long warp_pop(unsigned long long (&best)[KK]) {
+    unsigned long long m = best[0];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = umin64(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (best[0] == m) {  // keys are unique: one lane pops its head
+#pragma unroll
+        for (int t = 0; t + 1 < KK; ++t) best[t] = best[t + 1];
+        best[KK - 1] = ~0ull;
+    }
+    return m;
+}
+
 template <int D, int KC>
 __global__ void __launch_bounds__(256) rescan_kernel(const FusedArgs a) {
     constexpr int KK = KC - 4;
+    constexpr int kWarps = 256 / 32;
+    __shared__ unsigned long long s_top[kWarps][KK];
     const unsigned count = *reinterpret_cast<volatile const unsigned *>(a.fail_count);
-    const int lane = threadIdx.x & 31;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float4 *Lg = reinterpret_cast<const float4 *>(a.hi);
+    float4 x[D / 4];
+    unsigned long long best[KK];
+    if (count <= gridDim.x) {
+        // block per point
+        if (blockIdx.x >= count) return;  // whole blocks
+        const long long row = a.fail_list[blockIdx.x];
+        const float4 *xp = reinterpret_cast<const float4 *>(a.X) + row * (D / 4);
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) x[e] = centred(__ldg(xp + e), a.center, e);
+        rescan_scan<D, KK>(x, Lg, a.L, threadIdx.x, 256, best);
+        for (int r = 0; r < a.k; ++r) {
+            const unsigned long long m = warp_pop<KK>(best);
+            if (lane == 0) s_top[warp][r] = m;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // lane w < kWarps walks warp w's ascending list
+            int pos = 0;
+            unsigned long long head = lane < kWarps ? s_top[lane][0] : ~0ull;
+            for (int r = 0; r < a.k; ++r) {
+                unsigned long long m = head;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+                    m = umin64(m, __shfl_xor_sync(0xffffffffu, m, off));
+                if (head == m && lane < kWarps) {
+                    ++pos;
+                    head = pos < a.k ? s_top[lane][pos] : ~0ull;
+                }
+                if (lane == 0) {
+                    a.idx[row * a.k + r] = (int)(unsigned)(m & 0xffffffffu);
+                    if (a.dist2) a.dist2[row * a.k + r] = __uint_as_float((unsigned)(m >> 32));
+                }
+            }
+        }
+        return;
+    }
+    // warp per point
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (long long)count;
          w += nwarps) {
         const long long row = a.fail_list[w];
         const float4 *xp = reinterpret_cast<const float4 *>(a.X) + row * (D / 4);
-        float4 x[D / 4];
 #pragma unroll
         for (int e = 0; e < D / 4; ++e) x[e] = centred(__ldg(xp + e), a.center, e);
-        unsigned long long best[KK];
-#pragma unroll
-        for (int t = 0; t < KK; ++t) best[t] = ~0ull;
-        for (int j = lane; j < a.L; j += 32) {
-            const float d2 = dist2_row<D>(x, Lg, j);
-            const unsigned long long key =
-                ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)j;
-            if (key < best[KK - 1]) {
-                unsigned long long prev = best[0];
-                best[0] = umin64(key, best[0]);
-#pragma unroll
-                for (int t = 1; t < KK; ++t) {
-                    const unsigned long long cur = best[t];
-                    best[t] = umax64(prev, umin64(key, cur));
-                    prev = cur;
-                }
-            }
-        }
+        rescan_scan<D, KK>(x, Lg, a.L, lane, 32, best);
         for (int r = 0; r < a.k; ++r) {
-            unsigned long long m = best[0];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) m = umin64(m, __shfl_xor_sync(0xffffffffu, m, off));
-            if (best[0] == m) {  // keys are unique: one lane pops its head
-#pragma unroll
-                for (int t = 0; t + 1 < KK; ++t) best[t] = best[t + 1];
-                best[KK - 1] = ~0ull;
-            }
+            const unsigned long long m = warp_pop<KK>(best);
             if (lane == 0) {
                 a.idx[row * a.k + r] = (int)(unsigned)(m & 0xffffffffu);
                 if (a.dist2) a.dist2[row * a.k + r] = __uint_as_float((unsigned)(m >> 32));

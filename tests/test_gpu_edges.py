@@ -196,13 +196,22 @@ def test_landmark_update_and_version(esom):
     assert not np.allclose(a, b)
 
 
-@pytest.mark.parametrize("pinned", [True, False])
-def test_project_host_matches_device(esom, pinned):
-    """Host-buffer entry point (chunked H2D / kernel / D2H pipeline) gives the
-    same bits as the device entry point; n spans several pipeline chunks."""
-    w = workloads.mixture30_d16(n=(1 << 20) * 2 + 1234)
+@pytest.mark.parametrize("pinned,n,plan", [(True, (1 << 20) * 2 + 1234, 0),
+                                           (False, (1 << 20) * 2 + 1234, 0),
+                                           (True, 1000, 0), (True, 77824 + 1, 0),
+                                           (True, 2 * 77824 + 5, 0),
+                                           (True, (1 << 19) + 2 * 77824 + 3, 0),
+                                           (True, 58368 + 1, 2), (True, 2 * 58368 + 7, 3),
+                                           (True, (1 << 20) + 12345, 2)])
+def test_project_host_matches_device(esom, pinned, n, plan):
+    """Host-buffer entry point (chunked H2D / kernel / D2H pipeline: a first
+    and a last chunk of one k-NN wave, passes of 2^19 between) gives the same
+    bits as the device entry point; n spans one, two, three and several
+    chunks."""
+    w = workloads.mixture30_d16(n=n)
     with esom.Projector(w.d, w.L, w.k) as P:
         P.set_landmarks(torch.from_numpy(w.hi).cuda(), torch.from_numpy(w.lo).cuda())
+        P.set_plan(plan)
         ref = P.project(torch.from_numpy(w.X).cuda(), w.boost, w.adjust).cpu()
         Xh = torch.from_numpy(w.X)
         if pinned:

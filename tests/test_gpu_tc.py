@@ -122,6 +122,20 @@ def test_far_from_origin_is_still_exact(esom):
     same_as_fp32(esom, w, "shifted by 200", max_rescans=1.0)
 
 
+@pytest.mark.parametrize("n,L,k", [(200, 512, 12), (300, 70, 20), (5, 1000, 32), (2000, 300, 8)])
+def test_rescan_modes(esom, n, L, k):
+    """Shifted data: every point fails its certificate.  Up to one failed
+    point per rescan block (n <= 304 here) the block-per-point rescan runs,
+    above it the warp-per-point one; both give the FP32 path's bits, also
+    with fewer landmarks than threads in a block (L = 70)."""
+    r = np.random.default_rng(n + L)
+    w = workloads.random_case(r, n, 16, L, k)
+    w.X = (w.X + 200.0).astype(np.float32)
+    w.hi = (w.hi + 200.0).astype(np.float32)
+    for mode in (esom.ESOM_SCREEN_TF32, esom.ESOM_SCREEN_BF16):
+        same_as_fp32(esom, w, f"rescan n={n} L={L} k={k}", max_rescans=1.0, mode=mode)
+
+
 def test_landmark_update_rebuilds_images(esom):
     """set_landmarks after switching to TF32 rebuilds the chunk images."""
     w1 = workloads.mixture30_d16(n=5000)
