@@ -830,7 +830,7 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
     if (major != 10 || minor != 3)
         return fail(ESOM_EUNSUPPORTED, "tensor-core screening needs sm_103 (device is sm_%d%d)",
                     major, minor);
-    const size_t smem = esom::tc_smem_bytes(h->d, prec);
+    const size_t smem = esom::tc_smem_bytes(h->d, h->kc, prec);
     int optin = 0;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(shared memory opt-in)");

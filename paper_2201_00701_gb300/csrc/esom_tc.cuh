@@ -219,6 +219,9 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
     constexpr uint32_t kBBytes = 2 * kBPart;
     constexpr uint32_t kIdesc = tc_idesc<PREC>();
     constexpr int QS = kTcRows;  // queue stride: one column per selection thread
+    constexpr int QC = tc_queue(D, KC);   // queue capacity (keys a thread)
+    constexpr int QI = tc_check(D, KC);   // values pushed between fullness checks
+    static_assert(QI == 16 || QI == 32, "fullness checks every 16 or 32 values");
     constexpr int KF = ((KC + 7) & ~7) < 32 ? ((KC + 7) & ~7) : 32;  // first sorted block
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
     unsigned char *sA = base;                      // point tile: x_hi, x_lo
     unsigned char *sB = base + 2 * kAPart;         // S landmark chunk stages
     uint32_t *qk = reinterpret_cast<uint32_t *>(sB + S * kBBytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(qk + kQueue * kTcRows);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(qk + QC * kTcRows);
     uint64_t *l_full = bars, *l_empty = bars + S;
     uint64_t *t_full = bars + 2 * S, *t_empty = bars + 2 * S + 2;
     uint64_t *a_ready = bars + 2 * S + 4, *done_bar = bars + 2 * S + 5;
@@ -408,8 +411,8 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         // Keys of 32 values of chunk base (columns h32 .. h32 + 31) into the
         // queue: one FMA for the screening value, the key, the threshold
         // test and a predicated push.  Padding columns (beyond L) have NaN
-        // norms, so they never pass.  The queue is flushed after every 16
-        // values when a lane may not have room for 16 more.
+        // norms, so they never pass.  Every QI values the queue is flushed
+        // when a lane may not have room for QI more.
         auto push32 = [&](const float (&v)[32], int jbase, float (&keys)[KC], ScanState &st,
                           float M) {
             const float4 *N4 = reinterpret_cast<const float4 *>(a.norms + jbase);
@@ -431,7 +434,9 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                     }
                 }
                 st.qn = (int)((qp - (qk + tid)) / QS);
-                if (__any_sync(0xffffffffu, st.qn > kQueue - 16))
+                // after the check no lane holds more than QC - QI keys, so
+                // the next QI values fit
+                if ((QI == 16 || hb == 16) && __any_sync(0xffffffffu, st.qn > QC - QI))
                     queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
             }
         };
