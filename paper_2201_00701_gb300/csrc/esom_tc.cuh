@@ -409,8 +409,8 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         };
 
         // Keys of 32 values of chunk base (columns h32 .. h32 + 31) into the
-        // queue: one FMA for the screening value, the key, the threshold
-        // test and a predicated push.  Padding columns (beyond L) have NaN
+        // queue: half a packed FMA for the screening value, the key, the
+        // threshold test and a predicated push.  Padding columns (beyond L) have NaN
         // norms, so they never pass.  Every QI values the queue is flushed
         // when a lane may not have room for QI more.
         auto push32 = [&](const float (&v)[32], int jbase, float (&keys)[KC], ScanState &st,
@@ -421,12 +421,17 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                 uint32_t *qp = qk + st.qn * QS + tid;
 #pragma unroll
                 for (int jb = 0; jb < 16; jb += 4) {
+                    // screening values two at a time on the packed FP32x2
+                    // pipe (each lane the same fma as fmaf(-2, v, |l|^2))
                     const float4 n4 = __ldg(N4 + (hb + jb) / 4);
-                    const float nn[4] = {n4.x, n4.y, n4.z, n4.w};
+                    const float2 s01 = __ffma2_rn(make_float2(v[hb + jb], v[hb + jb + 1]),
+                                                  make_float2(-2.f, -2.f), make_float2(n4.x, n4.y));
+                    const float2 s23 = __ffma2_rn(make_float2(v[hb + jb + 2], v[hb + jb + 3]),
+                                                  make_float2(-2.f, -2.f), make_float2(n4.z, n4.w));
+                    const float sv[4] = {s01.x, s01.y, s23.x, s23.y};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const float key = make_key(fmaf(-2.f, v[hb + jb + e], nn[e]),
-                                                   (uint32_t)(jbase + hb + jb + e), mask);
+                        const float key = make_key(sv[e], (uint32_t)(jbase + hb + jb + e), mask);
                         if (key < st.thr) {
                             *qp = __float_as_uint(key);
                             qp += QS;
