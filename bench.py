@@ -455,7 +455,22 @@ def run_esom(args, world, rank, local):
                          "peak_from": roof_note,
                          "frac_of_fp32_alu_peak": achieved / alu_peak,
                          "frac_at_sampled_clock": (achieved / peak * max_mhz / clocks["sm_mhz"])
-                         if clocks.get("sm_mhz") else None},
+                         if clocks.get("sm_mhz") else None,
+                         # work the FMA count omits: one screening compare per
+                         # (point, landmark), the pairs u < v of the scored
+                         # neighbours
+                         "selection_compares_per_step": n * L,
+                         "pairs_per_step": n * (k - 1) * (k - 2) // 2,
+                         # the k-NN passes alone (CUDA events on the launching
+                         # stream): the dominant kernels of a split plan
+                         "dominant": ({"kernel": "fused_kernel", "ms": float(np.mean(step_ms)),
+                                       "share_of_step": 1.0} if screen == "fused" else
+                                      {"kernel": ("tc_kernel + rescan_kernel (k-NN passes)"
+                                                  if screen in ("tf32", "bf16") else
+                                                  "fused_kernel in k-NN mode + rescan_kernel"),
+                                       "ms": float(np.median(knn_ms)),
+                                       "share_of_step": float(np.median(knn_ms))
+                                       / float(np.median(step_ms))})},
             "clocks": clocks,
             "e2e": {"value": sharding.job_throughput(n, world, args.steps, e2e_s),
                     "unit": "points/s",
