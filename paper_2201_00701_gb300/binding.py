@@ -235,7 +235,7 @@ def esom_set_centering(h, on: bool) -> int:
 
 def esom_tune(h, points_ptr: int, n: int, out_ptr: int, boost: float, adjust: float,
               stream: int = 0):
-    """Returns (status, plan): ESOM_PLAN_FUSED / _SPLIT / _TF32, now set."""
+    """Returns (status, plan): ESOM_PLAN_FUSED / _SPLIT / _TF32 / _BF16, now set."""
     plan = ctypes.c_int(-1)
     st = load().esom_tune(h, points_ptr, n, out_ptr, boost, adjust, stream, ctypes.byref(plan))
     return st, plan.value

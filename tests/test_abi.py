@@ -59,6 +59,12 @@ def test_null_handle_calls(lib):
     st, _ = B.esom_get_config(None)
     assert st == B.ESOM_EINVAL
     assert B.esom_project_host(None, 0, 0, 0, 1.0, 1.0) == B.ESOM_EINVAL
+    assert B.esom_set_screening(None, B.ESOM_SCREEN_TF32) == B.ESOM_EINVAL
+    assert B.esom_set_split(None, True) == B.ESOM_EINVAL
+    assert B.esom_set_centering(None, True) == B.ESOM_EINVAL
+    assert B.esom_tune(None, 0, 1, 0, 1.0, 1.0)[0] == B.ESOM_EINVAL
+    assert B.esom_knn_variant(None, B.ESOM_KNN_BASE, 0, 0, 0, None) == B.ESOM_EINVAL
+    assert B.esom_project_knn(None, B.ESOM_PROJ_TABLE, 0, 0, 0, 0, 0, 1.0, 1.0) == B.ESOM_EINVAL
 
 
 def test_header_declares_c_linkage():
