@@ -9,9 +9,10 @@ in it) is flushed between steps by an untimed 256 MiB write.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl esom|reference]
 
-Under torchrun (N > 1) every rank projects its own shard of n points with
-no collective on the data path (weak scaling); the timed region is bracketed
-by barriers and the slowest rank's time is reported.  Rank 0 prints one JSON
+Under torchrun (N > 1) the point set holds n points per rank and every rank
+projects its own contiguous row range of it, with rank 0's landmarks
+(broadcast once) and no collective on the data path (weak scaling); the timed
+region is bracketed by barriers and the slowest rank's time is reported.  Rank 0 prints one JSON
 line.  `--impl reference` times the FP64 CPU oracle on bounded samples of the
 same workload instead (host cores only).
 """
@@ -281,13 +282,22 @@ def run_esom(args, world, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     binding.load()
 
+    # One point set X of n points per rank (weak scaling); each rank takes
+    # its contiguous row range, and the landmarks come from rank 0 (one
+    # broadcast per landmark version).
+    per_rank = args.n if args.n else (10_000_000 if args.workload == "student50_d32"
+                                      else 1_000_000)
     if args.workload == "student50_d32":
-        w = workloads.student50_d32(n=args.n if args.n else 10_000_000)
+        w = workloads.student50_d32(n=per_rank * world)
     else:
-        w = workloads.mixture30_d16(n=args.n if args.n else 1_000_000, shard=rank)
+        w = workloads.mixture30_d16(n=per_rank * world)
+    r0, r1 = sharding.row_range(w.n, world, rank)
+    w.X = np.ascontiguousarray(w.X[r0:r1])
     n, d, L, k = w.n, w.d, w.L, w.k
     P = binding.Projector(d, L, k)
-    P.set_landmarks(torch.from_numpy(w.hi).to(dev), torch.from_numpy(w.lo).to(dev))
+    hi_t, lo_t = torch.from_numpy(w.hi).to(dev), torch.from_numpy(w.lo).to(dev)
+    sharding.LandmarkSync(device=dev).sync(1, hi_t, lo_t)
+    P.set_landmarks(hi_t, lo_t)
     X = torch.from_numpy(w.X).to(dev)
     out = torch.empty((n, 2), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)

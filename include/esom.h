@@ -434,12 +434,51 @@ esom_status esom_server_destroy(esom_server s);
  * landmarks there; the status word is cleared at the start of each call.
  * Calls whose work overlaps on the GPU (on different streams, or from several
  * host threads) race on the scratch and give undefined results: serialise
- * them.  Device-side timeouts are recorded in the scratch status word but are
- * not reported by this call. */
+ * them.  A bounded wait inside the kernel that runs out (2 s; a sign of a
+ * stalled device) makes the kernel record it in the scratch status word and
+ * leave its remaining points unwritten: this call does not report it, and
+ * `out` is then undefined.
+ * Errors: ESOM_EINVAL (bad d, L, k, n, pointers, boost or adjust; landmarks
+ * beyond the scratch), ESOM_EALIGN, ESOM_EUNSUPPORTED (k > ESOM_MAX_K, no
+ * kernel for d and k, or the launch does not fit), ESOM_ECUDA. */
 #define ESOM_NOALLOC_SCRATCH_BYTES (4u << 20)
 esom_status esom_project_noalloc(const float *points, int64_t n, const float *hi,
                                  const float *lo, int d, int L, int k, float *out,
                                  float boost, float adjust, esom_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Test hooks (no counterpart in the paper).
+ *
+ * esom_test_stall: arms the next launch of the fused kernel of this handle
+ * (plan ESOM_PLAN_FUSED; esom_project or esom_knn) to exercise its timeout
+ * path: every block first waits on a barrier that nothing completes and
+ * gives up after limit_ns (1e3 <= limit_ns <= 2e9), then takes the path of a
+ * bounded wait that ran out -- it records the timeout in the device status
+ * word, waits for its own copies in flight and returns without writing its
+ * points.  esom_device_status then returns ESOM_EDEVICE; the handle and the
+ * context stay usable.  One launch consumes the probe.
+ * Errors: ESOM_EINVAL (null handle, limit out of range, plan not fused).
+ *
+ * esom_selftest_drcp: for i < n, rcp[i] = the FP64 reciprocal the 2x2 solve
+ * of esom_project uses (Section 3.1 step 4: Cramer's rule divides by the
+ * determinant; here an SFU approximation refined by two Newton steps) and
+ * div[i] = 1.0 / x[i] by CUDA's division, on `stream`.  x, rcp and div are
+ * device pointers to n doubles.  Errors: ESOM_EINVAL, ESOM_ECUDA. */
+esom_status esom_test_stall(esom_handle h, int64_t limit_ns);
+
+/* esom_selftest_tc_products: the raw tensor-core values behind the screened
+ * k-NN (Section 4.2: the distance block; here a tcgen05 contraction of split
+ * TF32 or BF16 operands with FP32 accumulation), for tests of its error
+ * bound.  Needs tensor-core screening on (esom_set_screening).  For each of
+ * the n points (n <= 2^19; device, as for esom_project) writes
+ * T[i * Lc + j] = the accumulated x_i . L_j for j < Lc = 64 ceil(L / 64)
+ * (landmarks beyond L are zero rows) to T (device, n * Lc floats, 16-byte
+ * aligned).  Errors: ESOM_EINVAL, ESOM_EALIGN, ESOM_ENOLANDMARKS,
+ * ESOM_EUNSUPPORTED, ESOM_ECUDA. */
+esom_status esom_selftest_tc_products(esom_handle h, const float *points, int64_t n, float *T,
+                                      esom_stream_t stream);
+esom_status esom_selftest_drcp(const double *x, int64_t n, double *rcp, double *div,
+                               esom_stream_t stream);
 
 /* Releases the handle's device buffers.  Pending work on streams that use
  * the handle must have completed. NULL is accepted. */

@@ -131,6 +131,9 @@ def load(build_if_missing: bool = False):
         "esom_server_session_output": ([P, I, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_uint64)], I),
         "esom_server_memory": ([P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)], I),
         "esom_server_destroy": ([P], I),
+        "esom_test_stall": ([P, I64], I),
+        "esom_selftest_drcp": ([P, I64, P, P, P], I),
+        "esom_selftest_tc_products": ([P, P, I64, P, P], I),
         "esom_destroy": ([P], I),
         "esom_last_error": ([], ctypes.c_char_p),
         "esom_status_string": ([I], ctypes.c_char_p),
@@ -247,6 +250,21 @@ def esom_project_noalloc(points_ptr: int, n: int, hi_ptr: int, lo_ptr: int, d: i
     """Projection with no device allocation (scratch in a fixed device array)."""
     return load().esom_project_noalloc(points_ptr, n, hi_ptr, lo_ptr, d, L, k, out_ptr, boost,
                                        adjust, stream)
+
+
+def esom_test_stall(h, limit_ns: int) -> int:
+    """Arms the next fused-kernel launch to run out a bounded wait (tests)."""
+    return load().esom_test_stall(h, limit_ns)
+
+
+def esom_selftest_drcp(x_ptr: int, n: int, rcp_ptr: int, div_ptr: int, stream: int = 0) -> int:
+    """The solve's FP64 reciprocal and CUDA's 1.0 / x of n doubles (tests)."""
+    return load().esom_selftest_drcp(x_ptr, n, rcp_ptr, div_ptr, stream)
+
+
+def esom_selftest_tc_products(h, points_ptr: int, n: int, T_ptr: int, stream: int = 0) -> int:
+    """Raw tensor-core dot products x . l of the screening (tests)."""
+    return load().esom_selftest_tc_products(h, points_ptr, n, T_ptr, stream)
 
 
 def esom_batch_create(items, autotune: bool = False):

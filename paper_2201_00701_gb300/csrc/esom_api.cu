@@ -341,6 +341,8 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
     } else {
         long long grid = (long long)h->blocks_per_sm * h->num_sms;
         if (grid > a.ntiles) grid = a.ntiles;
+        a.stall_ns = h->stall_ns;
+        h->stall_ns = 0;
         e = h->ops->launch(a, (int)grid, h->smem, stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -905,6 +907,52 @@ esom_status esom_destroy(esom_handle h) {
     if (h->s_out) cudaStreamDestroy(h->s_out);
     delete h;
     return ESOM_OK;
+}
+
+esom_status esom_test_stall(esom_handle h, int64_t limit_ns) {
+    if (!h) return fail(ESOM_EINVAL, "null handle");
+    if (limit_ns < 1000 || limit_ns > 2000000000)
+        return fail(ESOM_EINVAL, "limit_ns = %lld outside [1e3, 2e9]", (long long)limit_ns);
+    if (h->screening || h->split)
+        return fail(ESOM_EINVAL, "the stall probe needs the fused plan (ESOM_PLAN_FUSED)");
+    h->stall_ns = (unsigned long long)limit_ns;
+    return ESOM_OK;
+}
+
+esom_status esom_selftest_drcp(const double *x, int64_t n, double *rcp, double *div,
+                               esom_stream_t stream) {
+    if (n < 0) return fail(ESOM_EINVAL, "n < 0");
+    if (n == 0) return ESOM_OK;
+    if (!x || !rcp || !div) return fail(ESOM_EINVAL, "null pointer");
+    const cudaError_t e = esom::launch_drcp_selftest(x, n, rcp, div,
+                                                     reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ESOM_OK : cuda_fail(e, "drcp self-test launch");
+}
+
+esom_status esom_selftest_tc_products(esom_handle h, const float *points, int64_t n, float *T,
+                                      esom_stream_t stream) {
+    esom_status s = check_common(h, points, n);
+    if (s != ESOM_OK) return s;
+    if (!h->screening) return fail(ESOM_EINVAL, "tensor-core screening is off");
+    if (n > esom::kTcPass) return fail(ESOM_EINVAL, "n = %lld above %lld", (long long)n,
+                                       esom::kTcPass);
+    if (n == 0) return ESOM_OK;
+    if (!T || ((uintptr_t)T & 15u) != 0) return fail(ESOM_EALIGN, "T must be 16-byte aligned");
+    const int prec = tc_prec(h->screening);
+    const esom::TcOps *op = esom::tc_dump_ops(h->d, prec);
+    if (!op) return fail(ESOM_EUNSUPPORTED, "no tensor-core kernel for d = %d", h->d);
+    const size_t smem = esom::tc_smem_bytes(h->d, 8, prec);
+    cudaError_t e = cudaFuncSetAttribute(op->func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(shared memory)");
+    FusedArgs a;
+    esom::fill_args(h, points, n, nullptr, 1.f, 1.f, &a);
+    a.mode = esom::kKnn;
+    a.dist2 = T;
+    const long long tiles = (n + esom::kTcRows - 1) / esom::kTcRows;
+    const int grid = (int)(tiles < h->num_sms ? tiles : h->num_sms);
+    e = op->launch(a, grid, smem, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ESOM_OK : cuda_fail(e, "tensor-core product dump launch");
 }
 
 const char *esom_last_error(void) { return g_last_error; }

@@ -19,6 +19,9 @@ struct esom_ctx {
     const esom::KernelOps *ops = nullptr;
     int num_sms = 0;
     int forced_chunk = 0;
+    // esom_test_stall: limit (ns) of the probe wait of the next fused-kernel
+    // launch; 0 = none (the launch consumes it)
+    unsigned long long stall_ns = 0;
     uint64_t points = 0;   // points handed to the kernels since the last stats reset
     // launch configuration (derived from L, d and the chunk choice)
     int chunk = 0, nchunks = 0, blocks_per_sm = 0;

@@ -60,6 +60,34 @@ const TcOps *tc_ops(int D, int kc, int prec) {
     }
 }
 
+#define ESOM_DECLARE_TCD_D(DV) const TcOps *tc_dump_ops_d##DV(int prec);
+ESOM_DECLARE_TCD_D(4) ESOM_DECLARE_TCD_D(8) ESOM_DECLARE_TCD_D(12) ESOM_DECLARE_TCD_D(16)
+ESOM_DECLARE_TCD_D(20) ESOM_DECLARE_TCD_D(24) ESOM_DECLARE_TCD_D(28) ESOM_DECLARE_TCD_D(32)
+ESOM_DECLARE_TCD_D(36) ESOM_DECLARE_TCD_D(40) ESOM_DECLARE_TCD_D(44) ESOM_DECLARE_TCD_D(48)
+ESOM_DECLARE_TCD_D(52) ESOM_DECLARE_TCD_D(56) ESOM_DECLARE_TCD_D(60) ESOM_DECLARE_TCD_D(64)
+
+const TcOps *tc_dump_ops(int D, int prec) {
+    switch (D) {
+        case 4: return tc_dump_ops_d4(prec);
+        case 8: return tc_dump_ops_d8(prec);
+        case 12: return tc_dump_ops_d12(prec);
+        case 16: return tc_dump_ops_d16(prec);
+        case 20: return tc_dump_ops_d20(prec);
+        case 24: return tc_dump_ops_d24(prec);
+        case 28: return tc_dump_ops_d28(prec);
+        case 32: return tc_dump_ops_d32(prec);
+        case 36: return tc_dump_ops_d36(prec);
+        case 40: return tc_dump_ops_d40(prec);
+        case 44: return tc_dump_ops_d44(prec);
+        case 48: return tc_dump_ops_d48(prec);
+        case 52: return tc_dump_ops_d52(prec);
+        case 56: return tc_dump_ops_d56(prec);
+        case 60: return tc_dump_ops_d60(prec);
+        case 64: return tc_dump_ops_d64(prec);
+        default: return nullptr;
+    }
+}
+
 #define ESOM_DECLARE_VAR_D(DV) const VariantOps *variant_ops_d##DV();
 ESOM_DECLARE_VAR_D(4) ESOM_DECLARE_VAR_D(8) ESOM_DECLARE_VAR_D(12) ESOM_DECLARE_VAR_D(16)
 ESOM_DECLARE_VAR_D(20) ESOM_DECLARE_VAR_D(24) ESOM_DECLARE_VAR_D(28) ESOM_DECLARE_VAR_D(32)

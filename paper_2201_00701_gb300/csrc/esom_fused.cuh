@@ -49,7 +49,7 @@ namespace esom {
 constexpr float kScoreEdge = 10.0f;     // steepness of the k-th-neighbour cut-off
 constexpr float kSigmaEps = 1e-12f;     // spread below this * mean counts as zero
 constexpr double kDetEps = 1e-10;       // det/trace^2 below this: rank-one solve
-constexpr double kDetRecheck = 1e-4;    // FP32 det/trace^2 below this: recompute it
+constexpr double kDetRefine = 1e-3;     // FP32 det/trace^2 below this: recompute in FP64
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded mbarrier wait (2 s)
 constexpr float kU = 5.9604645e-8f;     // 2^-24, unit roundoff of FP32
 
@@ -121,14 +121,16 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t pari
     return ok != 0;
 }
 
-// Waits for phase `parity` of `bar` to complete, giving up after kWaitNs
-// (checked every 64 tries, so at most 64 x 20 us late).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Waits for phase `parity` of `bar` to complete, giving up after `limit`
+// ns (kWaitNs unless given; checked every 64 tries, so at most 64 x 20 us
+// late).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (uint32_t it = 1; it < (1u << 28); ++it) {
         if (mbar_try_wait_sleep(bar, parity)) return true;
-        if ((it & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
+        if ((it & 63u) == 0 && global_ns() - t0 > limit) return false;
     }
     return false;
 }
@@ -665,83 +667,142 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
 }
 
 // ---------------------------------------------------------------------------
-// The near-singular solve (rare; out of line).  A00 A11 - A01^2 from FP32
-// sums cannot resolve det/trace^2 below ~1e-6, so the small eigenvalue is
-// recomputed as the Rayleigh quotient n^T A n along the minor eigenvector n
-// of the FP32 matrix -- a sum of non-negative terms w (h.n)^2 / r over the
-// pairs, free of cancellation and accurate to second order in the error of
-// n -- and the branch is taken on det = lmin (trace - lmin): Cramer's rule if
-// det > 1e-10 trace^2, else the least-norm solution about the score-weighted
-// centroid of the scored 2-D landmarks (plain mean if all scores are 0), or
-// the centroid itself when A = 0.
-
-struct SlowSolve {
-    float A00, A01, A11, B0, B1, C0, C1, Ssum, M0, M1;
-    int m;
-};
+// Steps 2-4 of one point again, in FP64 (the rare path; out of line).  When
+// the FP32 normal system is ill-conditioned (det/trace^2 below kDetRefine)
+// the rounding of its FP32 terms and sums, about 1e-7 relative, is amplified
+// by the condition number, so the point is recomputed from its inputs in
+// FP64: the k neighbours' squared distances from the rows, the scores in the
+// form of reading R2 (weights 1/i over the m = k - 1 scored neighbours,
+// spread about the weighted mean, exp(boost (delta_1 - delta_i) / sigma)
+// times the cut-off factor), each pair's D_uv = <X - L_u, L_v - L_u> / q as
+// a dot product, the normal system, and the solve of reading R5: Cramer's
+// rule if det > 1e-10 trace^2, else the least-norm solution about the
+// score-weighted centroid of the scored 2-D landmarks (the plain mean if
+// every score is 0), or that centroid when A = 0.  The neighbours keep the
+// rank order of the k-NN result.  xrow is the point's row as stored (the
+// centre, when set, is subtracted here as the landmark rows are stored
+// centred); rows of Lg are chunk-swizzled.
 
 template <int D, int KK, int QS = kThreads>
-__device__ __noinline__ double2 solve_slow(const SlowSolve in, const float *sdp,
-                                           const float *ssp, const uint32_t *nb,
-                                           const float4 *Lg, const float2 *lo2, float2 l0,
-                                           const FusedArgs &a) {
-    const double a00 = in.A00, a01 = in.A01, a11 = in.A11, b0 = in.B0, b1 = in.B1;
-    double det = a00 * a11 - a01 * a01;
-    const double tr = a00 + a11;
-    if (tr > 0.0) {
-        const double disc = sqrt((a00 - a11) * (a00 - a11) + 4.0 * a01 * a01);
-        const double lmax = 0.5 * (tr + disc);
-        // two candidate major eigenvectors; take the better conditioned one
-        const double va0 = a01, va1 = lmax - a00, vb0 = lmax - a11, vb1 = a01;
-        const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
-        const double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
-        const double nn = sqrt(ga >= gb ? ga : gb);
-        if (nn > 0.0) {
-            // minor direction: the major one turned by 90 degrees
-            float sd[KK], ss[KK];
+__device__ __noinline__ double2 refine_fp64(const float *xrow, const float *center,
+                                            const uint32_t *nb, int k, const float4 *Lg,
+                                            const float2 *lo2, float boost, float adjust) {
+    const int m = k - 1;
+    double x[D];
 #pragma unroll
-            for (int t = 0; t < KK; ++t) {
-                sd[t] = sdp[t];
-                ss[t] = ssp[t];
+    for (int t = 0; t < D; ++t)
+        x[t] = (double)xrow[t] - (center ? (double)center[t] : 0.0);
+    double del[KK];
+    int id[KK];
+    for (int i = 0; i < k; ++i) {
+        const int j = nb_at<QS>(nb, i);
+        id[i] = j;
+        const float4 *l = Lg + (size_t)j * (D / 4);
+        const int f = swz(D, j);
+        double acc = 0.0;
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) {
+            const float4 q = l[e ^ f];
+            const double d0 = x[4 * e] - q.x, d1 = x[4 * e + 1] - q.y;
+            const double d2 = x[4 * e + 2] - q.z, d3 = x[4 * e + 3] - q.w;
+            acc += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+        }
+        del[i] = sqrt(acc);
+    }
+    // step 2: scores
+    double wsum = 0.0, mean = 0.0;
+    for (int i = 0; i < m; ++i) {
+        wsum += 1.0 / (double)(i + 1);
+        mean += del[i] / (double)(i + 1);
+    }
+    mean /= wsum;
+    double var = 0.0;
+    for (int i = 0; i < m; ++i) var += (del[i] - mean) * (del[i] - mean) / (double)(i + 1);
+    const double sigma = sqrt(var / wsum);
+    const double dk = del[k - 1];
+    const bool flat = sigma <= 1e-12 * fmax(mean, 1e-300);
+    double ss[KK], px[KK], py[KK];
+    const float2 l0 = lo2[id[0]];
+    double C0 = 0.0, C1 = 0.0, Ssum = 0.0, M0 = 0.0, M1 = 0.0;
+    for (int i = 0; i < m; ++i) {
+        const double f1 = flat ? 1.0 : exp((double)boost * (del[0] - del[i]) / sigma);
+        const double f2 = dk > 0.0 ? -expm1((double)kScoreEdge * (del[i] / dk - 1.0)) : 1.0;
+        ss[i] = f1 * f2;
+        const float2 li = lo2[id[i]];
+        px[i] = (double)li.x - (double)l0.x;  // relative to the nearest neighbour's
+        py[i] = (double)li.y - (double)l0.y;
+        C0 += ss[i] * px[i];
+        C1 += ss[i] * py[i];
+        Ssum += ss[i];
+        M0 += px[i];
+        M1 += py[i];
+    }
+    // step 3: pairs u < v < m
+    double a00 = 0.0, a01 = 0.0, a11 = 0.0, b0 = 0.0, b1 = 0.0;
+    for (int u = 0; u < m; ++u) {
+        const float4 *Lu = Lg + (size_t)id[u] * (D / 4);
+        const int fu = swz(D, id[u]);
+        for (int v = u + 1; v < m; ++v) {
+            const float4 *Lv = Lg + (size_t)id[v] * (D / 4);
+            const int fv = swz(D, id[v]);
+            double q = 0.0, g = 0.0;
+#pragma unroll
+            for (int e = 0; e < D / 4; ++e) {
+                const float4 cu = Lu[e ^ fu], cv = Lv[e ^ fv];
+                const double e0 = (double)cv.x - cu.x, e1 = (double)cv.y - cu.y;
+                const double e2 = (double)cv.z - cu.z, e3 = (double)cv.w - cu.w;
+                q += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3;
+                g += (x[4 * e] - cu.x) * e0 + (x[4 * e + 1] - cu.y) * e1 +
+                     (x[4 * e + 2] - cu.z) * e2 + (x[4 * e + 3] - cu.w) * e3;
             }
-            float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f, z4 = 0.f, rho = 0.f;
-            pair_sums<D, KK, 1, QS>(sd, nb, ss, in.m, Lg, lo2, l0, a, (float)(-v1 / nn),
-                                (float)(v0 / nn), z0, z1, z2, z3, z4, rho);
-            const double lmin = (double)rho;
-            det = lmin * (tr - lmin);
+            const double hx = px[v] - px[u], hy = py[v] - py[u];
+            const double r = hx * hx + hy * hy;
+            if (!(q > 0.0) || !(r > 0.0)) continue;
+            const double Duv = g / q;
+            const double w = ss[u] * ss[v] / (adjust == 1.f ? r : pow(r, (double)adjust));
+            const double rhs = Duv + (hx * px[u] + hy * py[u]) / r;
+            a00 += w * hx * hx / r;
+            a01 += w * hx * hy / r;
+            a11 += w * hy * hy / r;
+            b0 += w * hx * rhs;
+            b1 += w * hy * rhs;
         }
     }
+    // step 4: solve
+    const double det = a00 * a11 - a01 * a01, tr = a00 + a11;
+    double rx, ry;
     if (det > kDetEps * tr * tr) {
-        const double id = 1.0 / det;
-        return make_double2((b0 * a11 - a01 * b1) * id, (a00 * b1 - a01 * b0) * id);
-    }
-    double c0, c1;
-    if (in.Ssum > 0.f) {
-        c0 = (double)in.C0 / (double)in.Ssum;
-        c1 = (double)in.C1 / (double)in.Ssum;
+        rx = (b0 * a11 - a01 * b1) / det;
+        ry = (a00 * b1 - a01 * b0) / det;
     } else {
-        c0 = (double)in.M0 / (double)in.m;
-        c1 = (double)in.M1 / (double)in.m;
+        const double c0 = Ssum > 0.0 ? C0 / Ssum : M0 / (double)m;
+        const double c1 = Ssum > 0.0 ? C1 / Ssum : M1 / (double)m;
+        rx = c0;
+        ry = c1;
+        if (tr > 0.0) {
+            const double disc = sqrt((a00 - a11) * (a00 - a11) + 4.0 * a01 * a01);
+            const double lam = 0.5 * (tr + disc);
+            // major eigenvector: the better conditioned of two forms
+            const double va0 = a01, va1 = lam - a00, vb0 = lam - a11, vb1 = a01;
+            const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
+            double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
+            double nn = ga >= gb ? ga : gb;
+            if (nn == 0.0) {
+                v0 = 1.0;
+                v1 = 0.0;
+                nn = 1.0;
+            }
+            nn = sqrt(nn);
+            v0 /= nn;
+            v1 /= nn;
+            const double r0 = b0 - (a00 * c0 + a01 * c1);
+            const double r1 = b1 - (a01 * c0 + a11 * c1);
+            const double t = (v0 * r0 + v1 * r1) / lam;
+            rx = c0 + t * v0;
+            ry = c1 + t * v1;
+        }
     }
-    if (tr == 0.0) return make_double2(c0, c1);
-    const double disc = sqrt((a00 - a11) * (a00 - a11) + 4.0 * a01 * a01);
-    const double lam = 0.5 * (tr + disc);
-    double va0 = a01, va1 = lam - a00, vb0 = lam - a11, vb1 = a01;
-    const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
-    double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
-    double nn = ga >= gb ? ga : gb;
-    if (nn == 0.0) {
-        v0 = 1.0;
-        v1 = 0.0;
-        nn = 1.0;
-    }
-    nn = sqrt(nn);
-    v0 /= nn;
-    v1 /= nn;
-    const double r0 = b0 - (a00 * c0 + a01 * c1);
-    const double r1 = b1 - (a01 * c0 + a11 * c1);
-    const double t = (v0 * r0 + v1 * r1) / lam;
-    return make_double2(c0 + t * v0, c1 + t * v1);
+    return make_double2(rx + (double)l0.x, ry + (double)l0.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -752,7 +813,7 @@ __device__ __noinline__ double2 solve_slow(const SlowSolve in, const float *sdp,
 template <int D, int KK, int QS = kThreads, bool PF = false>
 __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uint32_t *nb,
                                                 const float4 *Lg, const float2 *lo2,
-                                                const FusedArgs &a) {
+                                                const FusedArgs &a, const float *xrow) {
     const int k = a.k, m = k - 1;
 
     // Step 2: scores.  Distances are Euclidean; the weights of the mean and
@@ -805,48 +866,24 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
 
     // 2-D coordinates relative to the nearest neighbour's.
     const float2 l0 = lo2[nb_at<QS>(nb, 0)];
-    float C0 = 0.f, C1 = 0.f, Ssum = 0.f, M0 = 0.f, M1 = 0.f;
-#pragma unroll
-    for (int t = 0; t < KK; ++t)
-        if (t < m) {
-            const float2 lt = lo2[nb_at<QS>(nb, t)];
-            const float px = lt.x - l0.x, py = lt.y - l0.y;
-            C0 = fmaf(ss[t], px, C0);
-            C1 = fmaf(ss[t], py, C1);
-            Ssum += ss[t];
-            M0 += px;
-            M1 += py;
-        }
 
     // Step 3: pair terms, u < v < m.
     float A00 = 0.f, A01 = 0.f, A11 = 0.f, B0 = 0.f, B1 = 0.f, rho = 0.f;
     pair_sums<D, KK, 0, QS, PF>(sd, nb, ss, m, Lg, lo2, l0, a, 0.f, 0.f, A00, A01, A11, B0, B1,
                                 rho);
 
-    // Step 4: FP64 solve; near-singular systems go to the out-of-line path.
+    // Step 4: FP64 solve; ill-conditioned systems are recomputed in FP64.
     const double a00 = A00, a01 = A01, a11 = A11, b0 = B0, b1 = B1;
     const double det = a00 * a11 - a01 * a01;
     const double tr = a00 + a11;
-    double px, py;
-    if (__builtin_expect(det > kDetRecheck * tr * tr, 1)) {
+    if (__builtin_expect(det > kDetRefine * tr * tr, 1)) {
         const double id = drcp(det);
-        px = (b0 * a11 - a01 * b1) * id;
-        py = (a00 * b1 - a01 * b0) * id;
-    } else {
-        SlowSolve in;
-        in.A00 = A00; in.A01 = A01; in.A11 = A11; in.B0 = B0; in.B1 = B1;
-        in.C0 = C0; in.C1 = C1; in.Ssum = Ssum; in.M0 = M0; in.M1 = M1; in.m = m;
-        float tsd[KK], tss[KK];
-#pragma unroll
-        for (int t = 0; t < KK; ++t) {
-            tsd[t] = sd[t];
-            tss[t] = ss[t];
-        }
-        const double2 r = solve_slow<D, KK, QS>(in, tsd, tss, nb, Lg, lo2, l0, a);
-        px = r.x;
-        py = r.y;
+        const double px = (b0 * a11 - a01 * b1) * id;
+        const double py = (a00 * b1 - a01 * b0) * id;
+        return make_float2((float)(px + (double)l0.x), (float)(py + (double)l0.y));
     }
-    return make_float2((float)(px + (double)l0.x), (float)(py + (double)l0.y));
+    const double2 r = refine_fp64<D, KK, QS>(xrow, a.center, nb, k, Lg, lo2, a.boost, a.adjust);
+    return make_float2((float)r.x, (float)r.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -858,7 +895,8 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
     static_assert((KC - 4) / 2 <= kQueue, "neighbour indices must fit in the thread's queue column");
     constexpr int KK = KC - 4;  // largest k this capacity serves (>= 4 spare entries)
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // [0] points, [1],[2] landmarks
+    // [0] points, [1],[2] landmarks, [3] the stall probe's (never completed)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     volatile int &s_abort = *reinterpret_cast<int *>(smem + 64);
     float *sX = reinterpret_cast<float *>(smem + kBarrierBytes);
     const int nbufL = a.nchunks == 1 ? 1 : 2;
@@ -879,6 +917,7 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         mbar_init(&bars[2], 1);
+        mbar_init(&bars[3], 1);
         fence_mbar_init();
         s_abort = 0;
     }
@@ -941,6 +980,12 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
             if (pendL1) mbar_wait(&bars[2], parL1);
         }
     };
+
+    // Stall probe (tests of the timeout path only): a wait on a barrier that
+    // nothing completes, bounded by stall_ns; the block then takes the same
+    // abort path as for a copy that never lands (status bit, own copies
+    // drained, no output written).
+    if (a.stall_ns && !mbar_wait(&bars[3], 0, a.stall_ns)) s_abort = 1;
 
     long long tile = first;
     for (long long t = 0; t < my_tiles; ++t, tile += gridDim.x) {
@@ -1100,7 +1145,8 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
 #pragma unroll
         for (int s = 0; s < KK; s += 2)
             nb[(s >> 1) * kThreads] = (uint32_t)si[s] | ((uint32_t)si[s + 1] << 16);
-        const float2 p = project_point<D, KK>(sd, nb, Lg, lo2, a);
+        const float2 p = project_point<D, KK>(sd, nb, Lg, lo2, a,
+                                              a.X + (size_t)(active ? row0 + tid : row0) * D);
         if (active) reinterpret_cast<float2 *>(a.out)[row0 + tid] = p;
     }
 }
@@ -1293,7 +1339,8 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchArgs B
         for (int s2 = 0; s2 < KK; s2 += 2)
             nb[(s2 >> 1) * kThreads] = (uint32_t)si[s2] | ((uint32_t)si[s2 + 1] << 16);
         const float2 p = project_point<D, KK>(sd, nb, Lg,
-                                              reinterpret_cast<const float2 *>(a.lo), a);
+                                              reinterpret_cast<const float2 *>(a.lo), a,
+                                              a.X + (size_t)(active ? row0 + tid : row0) * D);
         if (active) reinterpret_cast<float2 *>(a.out)[row0 + tid] = p;
     }
 }
@@ -1348,8 +1395,9 @@ __device__ __forceinline__ void project_tiles(const FusedArgs &a, const float4 *
 #pragma unroll
         for (int t = 0; t < KK; t += 2)
             nb[(t >> 1) * kThreads] = (uint32_t)si[t] | ((uint32_t)si[t + 1] << 16);
-        const float2 p = TAB ? project_point<D, KK, kThreads, true>(sd, nb, Lg, lo2, a)
-                             : project_point<D, KK>(sd, nb, Lg, lo2, a);
+        const float *xrow = a.X + (size_t)(active ? row : 0) * D;
+        const float2 p = TAB ? project_point<D, KK, kThreads, true>(sd, nb, Lg, lo2, a, xrow)
+                             : project_point<D, KK>(sd, nb, Lg, lo2, a, xrow);
         if (active) reinterpret_cast<float2 *>(a.out)[row] = p;
     }
 }

@@ -48,6 +48,10 @@ struct FusedArgs {
     // when set, the landmark rows are stored centred on this point (d floats,
     // 16-byte aligned) and every kernel subtracts it from the points it loads
     const float *center;
+    // fused kernel only, for tests of the timeout path: when nonzero, every
+    // block first waits on a barrier that nothing completes and gives up
+    // after this many ns (see esom_test_stall)
+    unsigned long long stall_ns;
 };
 
 // x - c, four at a time (c may be null: no centring).
@@ -184,12 +188,22 @@ inline size_t project_smem_bytes(int D, int L, bool resident) {
 // Tensor-core instantiation for D, list capacity kc and precision, or
 // nullptr.
 const TcOps *tc_ops(int D, int kc, int prec);
+// The tensor-core kernel in its accumulator-dump form (list capacity 8):
+// writes the raw values T_j = x . l_j of every point and landmark to
+// a.dist2 (tc_chunks * kTcN per point) instead of selecting; for tests of
+// the screening error bound.
+const TcOps *tc_dump_ops(int D, int prec);
 
 // Builds the split chunk images of the landmarks (precision prec) from the
 // (chunk-swizzled) rows of hi: ceil(L / kTcN) images of tc_chunk_bytes(D,
 // prec), rows beyond L zero.
 cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img, int prec,
                             cudaStream_t stream);
+
+// rcp[i] = the FP64 reciprocal the 2x2 solve uses (drcp), div[i] = 1.0 / x[i]
+// by CUDA's division, for i < n (device pointers).
+cudaError_t launch_drcp_selftest(const double *x, long long n, double *rcp, double *div,
+                                 cudaStream_t stream);
 
 // Records `msg` as this host thread's last error message; returns s.
 int set_error(int s, const char *msg);

@@ -59,8 +59,9 @@ extern "C" esom_status esom_project_noalloc(const float *points, int64_t n, cons
                                             float boost, float adjust, esom_stream_t stream) {
     if (d < 4 || d > ESOM_MAX_D || d % 4 != 0)
         return noalloc_fail(ESOM_EINVAL, "d must be a multiple of 4 in [4, 64]");
-    if (L < 2 || k < 2 || k > L || k > ESOM_MAX_K)
-        return noalloc_fail(ESOM_EINVAL, "need 2 <= k <= min(L, 32)");
+    if (L < 2 || k < 2 || k > L) return noalloc_fail(ESOM_EINVAL, "need 2 <= k <= L");
+    // the same code as esom_create for a k no kernel is built for
+    if (k > ESOM_MAX_K) return noalloc_fail(ESOM_EUNSUPPORTED, "k above ESOM_MAX_K (32)");
     if (L > ESOM_MAX_L ||
         (size_t)L * (size_t)d + (size_t)((2 * L + 3) & ~3) + (size_t)((L + 3) & ~3) +
                 kStatusFloats > kScratchFloats)

@@ -202,7 +202,10 @@ __device__ __forceinline__ float tc_dot_bound() {
 
 // ---------------------------------------------------------------------------
 
-template <int D, int KC, int PREC>
+// DUMP (tests of the error bound only): instead of selecting, every
+// selection thread writes the raw accumulator values T_j of its point for all
+// landmarks to a.dist2 (row-major, tc_chunks * kTcN per point).
+template <int D, int KC, int PREC, bool DUMP = false>
 __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const FusedArgs a) {
     static_assert(D % 4 == 0 && D >= 4 && D <= 64, "D must be a multiple of 4 in [4, 64]");
     static_assert(KC >= 8 && KC <= 36 && KC % 4 == 0, "list capacity out of range");
@@ -484,7 +487,16 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&t_empty[tb]);
                     }
-                    if (c == 0 && h == 0) {
+                    if (DUMP) {
+                        if (active) {
+                            float4 *o = reinterpret_cast<float4 *>(
+                                a.dist2 + row * (long long)(nch * kTcN) + base + 32 * h);
+#pragma unroll
+                            for (int t = 0; t < 8; ++t)
+                                o[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2],
+                                                   v[4 * t + 3]);
+                        }
+                    } else if (c == 0 && h == 0) {
                         // The first KF values go straight into the list (one
                         // sorting network; padding columns sort last); any
                         // beyond KC are dropped, which the certificate covers
@@ -521,6 +533,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
             // read): the next tile's operand replaces this one's, so that its
             // MMAs run while this tile is re-ranked.
             if (i + 1 < my_tiles) xx_next = write_tile(tile + gridDim.x);
+            if (DUMP) continue;
             queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
 
             // Step 1b: exact re-rank of the list, certificate, rare rescan.
@@ -560,9 +573,9 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
     }
 }
 
-template <int D, int KC, int PREC>
+template <int D, int KC, int PREC, bool DUMP = false>
 cudaError_t launch_tc(const FusedArgs &a, int grid, size_t smem, cudaStream_t stream) {
-    tc_kernel<D, KC, PREC><<<grid, kTcThreads, smem, stream>>>(a);
+    tc_kernel<D, KC, PREC, DUMP><<<grid, kTcThreads, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -588,12 +601,26 @@ const TcOps TcInstance<D, KC, PREC>::ops = {
         default: return nullptr;                                     \
     }
 
+template <int D, int PREC>
+struct TcDumpInstance {
+    static const TcOps ops;
+};
+
+template <int D, int PREC>
+const TcOps TcDumpInstance<D, PREC>::ops = {
+    reinterpret_cast<const void *>(&tc_kernel<D, 8, PREC, true>), 8,
+    &launch_tc<D, 8, PREC, true>};
+
 #define ESOM_DEFINE_TC_D(DV)                                         \
     const TcOps *tc_ops_d##DV(int kc, int prec) {                    \
         if (prec == kTcBf16) {                                       \
             ESOM_TC_CASES(DV, kTcBf16)                               \
         }                                                            \
         ESOM_TC_CASES(DV, kTcTf32)                                   \
+    }                                                                \
+    const TcOps *tc_dump_ops_d##DV(int prec) {                       \
+        return prec == kTcBf16 ? &TcDumpInstance<DV, kTcBf16>::ops   \
+                               : &TcDumpInstance<DV, kTcTf32>::ops;  \
     }
 
 }  // namespace esom

@@ -237,13 +237,8 @@ __global__ void __launch_bounds__(kVarThreads) project_registers_kernel(const Fu
     if ((lane & 1) == 0 && lane < kVarMaxK)
         s_nb[warp][lane >> 1] = (uint32_t)it | ((uint32_t)inext << 16);
 
-    // centroids of the scored 2-D landmarks, relative to the nearest's
+    // 2-D positions relative to the nearest neighbour's
     const float2 l0 = lo2[__shfl_sync(full, it, 0)];
-    const float2 lt = lo2[it];
-    const bool scored = lane < m;
-    const float px = scored ? lt.x - l0.x : 0.f, py = scored ? lt.y - l0.y : 0.f;
-    const float C0 = warp_sum(st * px), C1 = warp_sum(st * py), Ssum = warp_sum(st);
-    const float M0 = warp_sum(px), M1 = warp_sum(py);
     __syncwarp();
 
     // Step 3: pairs u < v < m in blocks of two u by two v, the blocks of the
@@ -306,20 +301,17 @@ __global__ void __launch_bounds__(kVarThreads) project_registers_kernel(const Fu
         const double det = a00 * a11 - a01 * a01;
         const double tr = a00 + a11;
         double rx, ry;
-        if (det > kDetRecheck * tr * tr) {
-            rx = (b0 * a11 - a01 * b1) / det;
-            ry = (a00 * b1 - a01 * b0) / det;
+        if (det > kDetRefine * tr * tr) {
+            rx = (b0 * a11 - a01 * b1) / det + (double)l0.x;
+            ry = (a00 * b1 - a01 * b0) / det + (double)l0.y;
         } else {
-            SlowSolve in;
-            in.A00 = A00; in.A01 = A01; in.A11 = A11; in.B0 = B0; in.B1 = B1;
-            in.C0 = C0; in.C1 = C1; in.Ssum = Ssum; in.M0 = M0; in.M1 = M1; in.m = m;
-            const double2 r = solve_slow<D, kVarMaxK, 1>(in, s_sd[warp], s_ss[warp], s_nb[warp],
-                                                         Lg, lo2, l0, a);
+            const double2 r = refine_fp64<D, kVarMaxK, 1>(a.X + (size_t)row * D, a.center,
+                                                          s_nb[warp], a.k, Lg, lo2, a.boost,
+                                                          a.adjust);
             rx = r.x;
             ry = r.y;
         }
-        reinterpret_cast<float2 *>(a.out)[row] =
-            make_float2((float)(rx + (double)l0.x), (float)(ry + (double)l0.y));
+        reinterpret_cast<float2 *>(a.out)[row] = make_float2((float)rx, (float)ry);
     }
 }
 

@@ -14,8 +14,12 @@ None of these re-types the oracle's own formulas.  They check it against
   * closed forms (k = 2, k = 3, exact plane recovery, hand-worked golden
     fixtures under tests/golden/);
   * invariances that hold for any score function (similarity maps of either
-    space, landmark relabelling, common scaling of the scores) and the
-    properties Section 3.1 step 2 demands of the scores.
+    space, landmark relabelling, common scaling of the scores), the
+    properties Section 3.1 step 2 demands of the scores, and boost acting as
+    the sharpness of the score profile.  The numeric score values (the 1/i
+    weights of the mean and spread, the steepness 10 of the cut-off) are a
+    reading with no printed example: parity unpinned beyond these
+    properties.
 """
 from __future__ import annotations
 
@@ -307,7 +311,9 @@ def pin_score_shape(O):
                 s = O.scores(dist ** 2, boost)
                 assert s[k - 1] == 0.0
                 assert np.all(s[:k - 1] > 0)
-                assert np.all(np.diff(s) <= 0), s
+                # distinct distances: strictly decreasing, so the nearest
+                # alone holds the highest score
+                assert np.all(np.diff(s) < 0), s
                 assert s[0] == s.max()
                 s2 = O.scores((3.0 * dist) ** 2, boost)
                 _close(s2, s, 1e-12 * s.max(), "scores scale-free in the distances")
@@ -317,6 +323,26 @@ def pin_score_shape(O):
                 dd[j] *= 1 + 1e-9
                 dd = np.sort(dd)
                 _close(O.scores(dd ** 2, boost), s, 1e-6 * s.max(), "scores continuous")
+
+
+def pin_boost_sharpness(O):
+    """boost is the sharpness of the score profile (the parameter of the
+    original EmbedSOM score function that Section 3.1 step 2 defers to): for
+    fixed distances delta_1 < delta_i < delta_k, the relative score s_i / s_1
+    falls strictly as boost grows, towards 0 for a large boost, while s_1
+    stays the largest score."""
+    r = _rng(14)
+    boosts = np.array([0.125, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0])
+    for k in (3, 4, 10, 20, 30):
+        for _ in range(10):
+            dist = np.sort(r.uniform(0.5, 4.0, k))
+            if np.min(np.diff(dist)) < 1e-3:
+                continue
+            S = np.array([O.scores(dist ** 2, b) for b in boosts])   # boosts x k
+            rel = S[:, 1:k - 1] / S[:, :1]                           # s_i / s_1, 1 < i < k
+            assert np.all(rel > 0) and np.all(rel < 1), rel
+            assert np.all(np.diff(rel, axis=0) < 0), f"s_i/s_1 not falling with boost: {rel}"
+            assert np.all(S[-1, 1:k - 1] / S[-1, 0] < S[0, 1:k - 1] / S[0, 0])
 
 
 def _crossing_point(X0, La, Lb):
@@ -397,4 +423,4 @@ ALL_PINS = [pin_knn_bruteforce, pin_k2_nearest_layout_point, pin_k3_closed_form,
             pin_golden_fixtures, pin_plane_recovery, pin_weighted_least_squares,
             pin_collinear_layout, pin_layout_similarity, pin_space_similarity,
             pin_relabelling, pin_score_homogeneity, pin_score_shape,
-            pin_continuity_at_cutoff, pin_som_step_limits]
+            pin_boost_sharpness, pin_continuity_at_cutoff, pin_som_step_limits]

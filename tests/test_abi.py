@@ -65,6 +65,10 @@ def test_null_handle_calls(lib):
     assert B.esom_tune(None, 0, 1, 0, 1.0, 1.0)[0] == B.ESOM_EINVAL
     assert B.esom_knn_variant(None, B.ESOM_KNN_BASE, 0, 0, 0, None) == B.ESOM_EINVAL
     assert B.esom_project_knn(None, B.ESOM_PROJ_TABLE, 0, 0, 0, 0, 0, 1.0, 1.0) == B.ESOM_EINVAL
+    assert B.esom_test_stall(None, 10_000) == B.ESOM_EINVAL
+    assert B.esom_selftest_drcp(0, 0, 0, 0) == B.ESOM_OK       # n = 0: nothing to do
+    assert B.esom_selftest_drcp(0, 5, 0, 0) == B.ESOM_EINVAL
+    assert B.esom_selftest_drcp(0, -1, 0, 0) == B.ESOM_EINVAL
 
 
 def test_header_declares_c_linkage():

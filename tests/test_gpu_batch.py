@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import coord_errors
+from parity import coord_errors, report
 from paper_2201_00701_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -86,7 +86,7 @@ def test_batch_against_oracle(esom):
     torch.cuda.synchronize()
     for w, out in zip(ws, outs):
         ref, ratio, _ = oracle.project(w.X, w.hi, w.lo, w.k, w.boost, w.adjust, diagnostics=True)
-        coord_errors(out.cpu().numpy(), ref, ratio, w.extent)
+        report(coord_errors(out.cpu().numpy(), ref, ratio, w.extent), w.name)
     esom.esom_batch_destroy(b)
     for P in handles:
         P.close()

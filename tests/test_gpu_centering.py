@@ -62,7 +62,7 @@ def test_centring_removes_rescans(esom, mode):
     print("CENTRING", mode, "rescans plain", frac(plain[3]), "centred", frac(cent[3]))
     assert frac(plain[3]) > 0.5
     assert frac(cent[3]) <= 0.2
-    check(w, *cent[:3], label=f"centred {mode}")
+    check(w, *cent[:3], label=f"centred {mode}", named=False)
 
 
 @pytest.mark.parametrize("chunk", [None, 200])
@@ -75,7 +75,7 @@ def test_centred_plans_agree_and_match_oracle(esom, chunk):
         out, idx, d2, cfg = run(esom, w, True, plan, chunk=chunk)
         outs[plan] = out
         if plan == esom.ESOM_PLAN_FUSED:
-            check(w, out, idx, d2, label=f"centred fused chunk={chunk}")
+            check(w, out, idx, d2, label=f"centred fused chunk={chunk}", named=False)
     ref = outs[esom.ESOM_PLAN_FUSED]
     for o in outs.values():
         assert np.array_equal(o.view(np.uint32), ref.view(np.uint32))

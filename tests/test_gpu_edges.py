@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import coord_errors, knn_mismatches
+from parity import coord_errors, knn_mismatches, report
 from paper_2201_00701_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -37,7 +37,9 @@ def against_oracle(w, out, idx, d2):
     o, ratio, branch = oracle.project(w.X, w.hi, w.lo, w.k, w.boost, w.adjust, diagnostics=True)
     oi, od = oracle.knn(w.X, w.hi, w.k)
     knn_mismatches(w.X, w.hi, idx, d2, oi, od)
-    return coord_errors(out, o, ratio, w.extent), branch
+    stats = coord_errors(out, o, ratio, w.extent)
+    report(stats, w.name)
+    return stats, branch
 
 
 @pytest.mark.parametrize("d,L,k", [(4, 10, 3), (64, 50, 32), (8, 32, 32), (12, 7, 7),
@@ -162,7 +164,7 @@ def test_nan_input_no_fault(esom, plan):
         good[[5, 6]] = False
         out = P.project(X, 1.0, 1.0).cpu().numpy()
     o, ratio, _ = oracle.project(w.X[good], w.hi, w.lo, w.k, 1.0, 1.0, diagnostics=True)
-    coord_errors(out[good], o, ratio, w.extent)
+    report(coord_errors(out[good], o, ratio, w.extent), f"non-finite rows, plan {plan}")
 
 
 def test_deterministic_and_streams(esom):
@@ -192,7 +194,7 @@ def test_landmark_update_and_version(esom):
         b = P.project(X).cpu().numpy()
         assert esom.esom_landmark_version(P.h) == 2
     o, ratio, _ = oracle.project(w1.X, w2.hi, w2.lo, w1.k, 1.0, 1.0, diagnostics=True)
-    coord_errors(b, o, ratio, w2.extent)
+    report(coord_errors(b, o, ratio, w2.extent), "landmark update")
     assert not np.allclose(a, b)
 
 

@@ -1,11 +1,9 @@
 """CUDA path vs the FP64 oracle on the named workloads (GPU)."""
-import json
-
 import numpy as np
 import pytest
 
 import oracle
-from parity import coord_errors, knn_mismatches
+from parity import coord_errors, knn_mismatches, report
 from paper_2201_00701_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -46,10 +44,12 @@ def rescan_fraction(cfg):
     return st["rescans"] / max(st["points"], 1)
 
 
-def check(w, out, idx, d2, rows=None, label="", cfg=None, max_rescans=0.01):
+def check(w, out, idx, d2, rows=None, label="", cfg=None, max_rescans=0.01, named=True):
     """Coordinates and k-NN against the oracle.  The screening certificate
     must fail (forcing an exact rescan) for at most `max_rescans` of the
-    points on these continuous-valued workloads."""
+    points on these continuous-valued workloads.  The named workloads have
+    no point near a singular normal system: none may be exempt or
+    ill-conditioned (`named`)."""
     X = w.X if rows is None else w.X[rows]
     o_out, ratio, _ = oracle.project(X, w.hi, w.lo, w.k, w.boost, w.adjust, diagnostics=True)
     sel = slice(None) if rows is None else rows
@@ -58,10 +58,11 @@ def check(w, out, idx, d2, rows=None, label="", cfg=None, max_rescans=0.01):
         o_idx, o_d2 = oracle.knn(X, w.hi, w.k)
         nd, ties = knn_mismatches(X, w.hi, idx[sel], d2[sel], o_idx, o_d2)
         stats.update(knn_rows_differing=nd, knn_tie_swaps=ties)
-    stats["label"] = label
     if cfg is not None:
         stats["rescan_fraction"] = rescan_fraction(cfg)
-    print("PARITY", json.dumps(stats))
+    report(stats, label)
+    if named:
+        assert stats["exempt"] == 0 and stats["ill_conditioned"] == 0, stats
     if cfg is not None:
         assert stats["rescan_fraction"] <= max_rescans, stats
     return stats
@@ -125,10 +126,32 @@ def test_batch_members(esom):
 
 
 def test_student50_d32_full_size_sampled(esom):
-    """n = 10,000,000, d = 32, L = 4096 (chunked), k = 30; 1500 sampled points."""
+    """n = 10,000,000, d = 32, L = 4096 (chunked), k = 30, every execution
+    plan: the plain FP32 path and the tensor-core screened paths (TF32 and
+    BF16 contraction, FP32 accumulation, certified FP32 re-rank) give the
+    same bits, and their error against the FP64 oracle is measured on a fixed
+    100,000-point subsample: within 1e-4 of the layout extent (the FP32 bar,
+    tighter than the 1e-3 asked of a screened path)."""
     w = workloads.student50_d32()
-    out, idx, d2, cfg = run_gpu(esom, w, knn=False)
-    assert cfg["landmark_chunks"] > 1
-    rows = np.sort(np.random.default_rng(3).choice(w.n, 1500, replace=False))
-    check(w, out, None, None, rows=rows, label="student50_d32 1e7 sampled", cfg=cfg)
+    X = torch.from_numpy(w.X).cuda()
+    outs = {}
+    with esom.Projector(w.d, w.L, w.k) as P:
+        P.set_landmarks(torch.from_numpy(w.hi).cuda(), torch.from_numpy(w.lo).cuda())
+        cfg = P.config()
+        assert cfg["landmark_chunks"] > 1
+        for plan, name in esom.PLAN_NAMES.items():
+            P.set_plan(plan)
+            out = P.project(X, w.boost, w.adjust)
+            torch.cuda.synchronize()
+            assert P.device_status() == 0
+            outs[name] = out.cpu().numpy()
+        cfg["stats"] = P.stats()
+    for name, o in outs.items():
+        assert np.array_equal(o.view(np.uint32), outs["fused"].view(np.uint32)), name
+    out = outs["fused"]
     assert np.isfinite(out).all()
+    rows = np.sort(np.random.default_rng(3).choice(w.n, 100_000, replace=False))
+    stats = check(w, out, None, None, rows=rows, label="student50_d32 1e7, 1e5 sampled, all plans",
+                  cfg=cfg)
+    print(f"STUDENT50 screened = FP32 bits; max error {stats['max_err'] / w.extent:.3e} and "
+          f"p99 {stats['p99_err'] / w.extent:.3e} of the extent {w.extent}")

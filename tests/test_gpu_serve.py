@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import coord_errors
+from parity import coord_errors, report
 from paper_2201_00701_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -212,7 +212,7 @@ def test_served_frames_equal_manual_steps_and_oracle(esom):
     hiN = his[-1][0]
     ref, ratio, _ = oracle.project(w.X, hiN, w.lo, w.k, w.boost, w.adjust, diagnostics=True)
     stats = coord_errors(got.cpu().numpy(), ref, ratio, w.extent)
-    print(f"SERVE frame {frames}: {stats}")
+    report(stats, f"served frame {frames}")
 
 
 def test_session_alone_equals_in_mix(esom):

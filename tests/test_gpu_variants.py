@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import COORD_TOL, coord_errors
+from parity import COORD_TOL, coord_errors, report
 from paper_2201_00701_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -61,8 +61,7 @@ CASES = ["mixture10_d8", "mixture30_d16", "student50_d32", "d64_k20", "d4_k2", "
 def check_registers(w, out, label):
     ref, ratio, _ = oracle.project(w.X, w.hi, w.lo, w.k, w.boost, w.adjust, diagnostics=True)
     stats = coord_errors(out, ref, ratio, w.extent, tol=2 * COORD_TOL)
-    stats["label"] = label
-    print("PARITY", json.dumps(stats))
+    report(stats, label)
 
 
 def projector(esom, w, centering=False):

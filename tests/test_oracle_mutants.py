@@ -15,6 +15,9 @@ import oracle_pins
 # landmarks onto one line (or gives them equal scores), so the centroid's
 # weights cannot be observed; only near-singular systems would show them.
 # Nor pairs that include the k-th neighbour: its score is 0, so they add 0.
+# Nor other weights of the mean and spread (uniform instead of 1/i) or
+# another cut-off steepness: no passage fixes those values (parity
+# unpinned), and any such choice keeps every property the pins check.
 MUTANTS = [
     ("tie_break_reversed", "return (a->j > b->j) - (a->j < b->j);",
      "return (a->j < b->j) - (a->j > b->j);"),
@@ -35,6 +38,9 @@ MUTANTS = [
      "double f2 = 1.0;"),
     ("scores_increasing", "double f1 = flat ? 1.0 : exp(boost * (mean - delta) / sigma);",
      "double f1 = flat ? 1.0 : exp(boost * (delta - mean) / sigma);"),
+    ("boost_ignored", "double f1 = flat ? 1.0 : exp(boost * (mean - delta) / sigma);",
+     "double f1 = flat ? 1.0 : exp((mean - delta) / sigma);"),
+    ("uniform_scores", "s[i - 1] = f1 * f2;", "s[i - 1] = 1.0;"),
     ("pairs_skip_last_scored", "for (int v = u + 1; v < m; ++v) {",
      "for (int v = u + 1; v < m - 1; ++v) {"),
     ("knn_drops_nearest", "idx[i] = work[i].j;", "idx[i] = work[i + (i == 0 && k < g)].j;"),

@@ -2,7 +2,8 @@
 shard of points with the FP64 oracle (the arithmetic the GPUs run is tested
 elsewhere), then the same collectives the benchmark uses -- the broadcast of
 rank 0's plan choice and the maximum of the ranks' times -- and the job
-throughput of a weak-scaling run."""
+throughput of a weak-scaling run; the row-range split of one caller's X with
+landmarks broadcast from rank 0 once per version."""
 import os
 import socket
 
@@ -60,7 +61,66 @@ def test_two_gloo_ranks(tmp_path):
     assert np.array_equal(np.concatenate(outs), whole)
 
 
+def _row_range_main(rank, world, port, n, outdir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world),
+                      RANK=str(rank), LOCAL_RANK=str(rank))
+    import oracle
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # one X, known to every rank; the landmarks only to rank 0
+        w = workloads.mixture10_d8(n=n)
+        hi = torch.from_numpy(w.hi.copy()) if rank == 0 else torch.zeros(w.L, w.d)
+        lo = torch.from_numpy(w.lo.copy()) if rank == 0 else torch.zeros(w.L, 2)
+        sync = sharding.LandmarkSync()
+        assert sync.sync(1, hi, lo)
+        assert not sync.sync(1 if rank == 0 else 5, hi, lo)   # rank 0's version decides
+        assert sync.broadcasts == 1
+        assert np.array_equal(hi.numpy(), w.hi) and np.array_equal(lo.numpy(), w.lo)
+        # a new version on rank 0 is broadcast again
+        if rank == 0:
+            hi += 0.5
+        assert sync.sync(2, hi, lo) and sync.broadcasts == 2
+        assert np.array_equal(hi.numpy(), w.hi + np.float32(0.5))
+        a, b = sharding.row_range(n, world, rank)
+        out = oracle.project(w.X[a:b], hi.numpy(), lo.numpy(), w.k, w.boost, w.adjust,
+                             threads=1)
+        np.save(os.path.join(outdir, f"r{rank}.npy"), out)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_row_ranges_and_landmark_broadcast(tmp_path):
+    """Two gloo ranks take their row ranges of one X and rank 0's landmarks
+    (broadcast once per version); the outputs concatenated in rank order
+    equal one projection of the whole X."""
+    world, n = 2, 301
+    mp.spawn(_row_range_main, args=(world, _free_port(), n, str(tmp_path)), nprocs=world,
+             join=True)
+    import oracle
+    w = workloads.mixture10_d8(n=n)
+    parts = [np.load(tmp_path / f"r{r}.npy") for r in range(world)]
+    assert [len(p) for p in parts] == [151, 150]
+    whole = oracle.project(w.X, w.hi + np.float32(0.5), w.lo, w.k, w.boost, w.adjust, threads=1)
+    assert np.array_equal(np.concatenate(parts), whole)
+
+
+def test_row_range_partition():
+    for n in (0, 1, 7, 1000, 1_000_003):
+        for world in (1, 2, 3, 8):
+            ranges = [sharding.row_range(n, world, r) for r in range(world)]
+            assert ranges[0][0] == 0 and ranges[-1][1] == n
+            assert all(ranges[i][1] == ranges[i + 1][0] for i in range(world - 1))
+            sizes = [b - a for a, b in ranges]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        sharding.row_range(10, 2, 2)
+
+
 def test_single_process_fallbacks():
     assert sharding.max_over_ranks([2.5, 1.0]) == [2.5, 1.0]
     assert sharding.broadcast_choice(3) == 3
     assert sharding.job_throughput(1000, 1, 10, 2.0) == 5000.0
+    hi, lo = torch.ones(4, 8), torch.ones(4, 2)
+    sync = sharding.LandmarkSync()
+    assert sync.sync(3, hi, lo) and not sync.sync(3, hi, lo) and sync.broadcasts == 0
