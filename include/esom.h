@@ -124,6 +124,9 @@ typedef struct {
     uint64_t points;    /* points projected or searched */
     uint64_t rescans;   /* points whose screening certificate failed, so their k
                            nearest were found by an exact rescan (slower path) */
+    uint64_t refines;   /* points whose FP32 normal system was too ill-conditioned
+                           (det/trace^2 <= 1e-3), so steps 1-4 were recomputed
+                           in FP64 (slower path) */
 } esom_stats;
 
 /* Waits for `stream`, then returns the handle's counters accumulated since
@@ -423,10 +426,12 @@ esom_status esom_server_destroy(esom_server s);
  * The function allocates nothing.  Its scratch -- a staged copy of the
  * landmarks, their squared norms and the kernel's status word -- lives in
  * one fixed ESOM_NOALLOC_SCRATCH_BYTES array in device memory that every GPU
- * that loads the library holds until the process exits.  Landmark sets with
- * (L * (d + 2) + L rounded up to a multiple of 4) * 4 + 256 bytes above
- * ESOM_NOALLOC_SCRATCH_BYTES are rejected with ESOM_EINVAL before anything is
- * queued.
+ * that loads the library holds until the process exits.  The rest of the
+ * array holds the list of points whose normal system needs the FP64
+ * recomputation; the points are projected in passes that list fits (at least
+ * 8192 points a pass).  Landmark sets with (L * (d + 2) + L rounded up to a
+ * multiple of 4) * 4 + 256 + 65536 bytes above ESOM_NOALLOC_SCRATCH_BYTES are
+ * rejected with ESOM_EINVAL before anything is queued.
  *
  * The first call on a device looks up that device's address of the scratch
  * array (cudaGetSymbolAddress, with the device current); make that first call

@@ -49,7 +49,8 @@ class EsomError(RuntimeError):
 
 
 class _Stats(ctypes.Structure):
-    _fields_ = [("points", ctypes.c_uint64), ("rescans", ctypes.c_uint64)]
+    _fields_ = [("points", ctypes.c_uint64), ("rescans", ctypes.c_uint64),
+                ("refines", ctypes.c_uint64)]
 
 
 class BatchItem(ctypes.Structure):
@@ -218,7 +219,8 @@ def esom_get_stats(h, stream: int = 0, reset: bool = False):
     """Returns (status, {"points": ..., "rescans": ...})."""
     st_ = _Stats()
     st = load().esom_get_stats(h, stream, ctypes.byref(st_), int(reset))
-    return st, {"points": int(st_.points), "rescans": int(st_.rescans)}
+    return st, {"points": int(st_.points), "rescans": int(st_.rescans),
+                "refines": int(st_.refines)}
 
 
 def esom_set_screening(h, mode: int, stream: int = 0) -> int:

@@ -80,6 +80,8 @@ void fill_args(const esom_ctx *h, const float *points, long long n, float *out, 
     a->qtab = h->nchunks > 1 ? h->qtab : nullptr;
     a->center = h->centered ? h->center : nullptr;
     a->tc_chunks = (h->L + kTcN - 1) / kTcN;
+    a->refine_list = h->refine_list;
+    a->refine_count = reinterpret_cast<unsigned *>(h->status) + 4;
 }
 
 int set_error(int s, const char *msg) {
@@ -162,7 +164,8 @@ __device__ __forceinline__ uint32_t bf16_rn(float x) {
 }
 
 __global__ void tc_image_kernel(const float *__restrict__ hi, int L, int D,
-                                unsigned char *__restrict__ img, int Lpad, int prec) {
+                                unsigned char *__restrict__ img, int Lpad, int prec,
+                                const int *__restrict__ lperm) {
     const int eb = tc_elem_bytes(prec);
     const int rb = tc_row_bytes(D, prec), nb = tc_nblk(D, prec), ppb = rb / 16;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -175,7 +178,11 @@ __global__ void tc_image_kernel(const float *__restrict__ hi, int L, int D,
     for (int q = 0; q < 4 / eb; ++q) {
         const int e = b0 / (4 * eb) + q;  // float4 index of the row
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j < L && e < D / 4) v = reinterpret_cast<const float4 *>(hi + (size_t)j * D)[e ^ swz(D, j)];
+        if (j < L && e < D / 4) {
+            // internal position j holds landmark lperm[j] (the spatial order)
+            const int src = lperm ? lperm[j] : j;
+            v = reinterpret_cast<const float4 *>(hi + (size_t)src * D)[e ^ swz(D, src)];
+        }
         const float a[4] = {v.x, v.y, v.z, v.w};
         uint32_t hw[4], lw[4];
         for (int i = 0; i < 4; ++i) {
@@ -208,12 +215,12 @@ __global__ void tc_image_kernel(const float *__restrict__ hi, int L, int D,
 }
 
 cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img, int prec,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, const int *lperm) {
     const int Lpad = (L + kTcN - 1) / kTcN * kTcN;
     const long long threads =
         (long long)Lpad * tc_nblk(D, prec) * (tc_row_bytes(D, prec) / 16);
     tc_image_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(hi, L, D, img, Lpad,
-                                                                           prec);
+                                                                           prec, lperm);
     return cudaGetLastError();
 }
 }  // namespace esom
@@ -248,6 +255,22 @@ esom_status configure(esom_ctx *h) {
     return ESOM_OK;
 }
 
+// The tensor-core screening's landmark operands for the current landmarks:
+// the spatial order (when on), then the split chunk images in that order.
+cudaError_t build_screening(esom_ctx *h, int prec, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (h->order_on)
+        e = esom::launch_landmark_order(h->hi, h->norms, h->L, h->d, h->lperm, h->centers,
+                                        h->norms_int, h->corder, st);
+    if (e == cudaSuccess)
+        e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, prec, st,
+                                  h->order_on ? h->lperm : nullptr);
+    return e;
+}
+
+// Largest landmark rows (bytes) the re-rank kernel keeps in shared memory.
+constexpr size_t kRerankResidentBytes = 100 * 1024;
+
 esom_status check_device(const esom_ctx *h) {
     int cur = -1;
     cudaError_t e = cudaGetDevice(&cur);
@@ -260,16 +283,39 @@ esom_status check_device(const esom_ctx *h) {
 
 // Projection from given neighbours by the library's kernel (one thread per
 // point, distance table), the launch the split path makes after its k-NN.
-esom_status launch_projection(esom_ctx *h, FusedArgs p, cudaStream_t stream) {
-    const bool res = h->nchunks == 1 && esom::project_smem_bytes(h->d, h->L, true) <= h->proj_smem;
-    p.nchunks = res ? 1 : 2;
-    p.qtab = h->qtab;
-    p.mode = esom::kProject;
-    p.ntiles = (p.n + esom::kThreads - 1) / esom::kThreads;
-    long long grid = (long long)h->proj_blocks_per_sm * h->num_sms;
-    if (grid > p.ntiles) grid = p.ntiles;
-    const cudaError_t e = h->ops->launch_proj(p, (int)grid, h->proj_smem, stream);
-    return e == cudaSuccess ? ESOM_OK : cuda_fail(e, "projection kernel launch");
+// The FP64 recomputation of the rows the projection just listed (one warp a
+// row), and the reset of the list for the next launch is the caller's.
+cudaError_t launch_refine(esom_ctx *h, const FusedArgs &p, cudaStream_t stream) {
+    return h->ops->launch_refine(p, 2 * h->num_sms, stream);
+}
+
+esom_status launch_projection(esom_ctx *h, FusedArgs p0, cudaStream_t stream) {
+    p0.qtab = h->qtab;
+    p0.mode = esom::kProject;
+    unsigned *rcount = reinterpret_cast<unsigned *>(h->status) + 4;
+    // passes of at most kTcPass points: the refine list holds one pass
+    for (long long off = 0; off < p0.n; off += esom::kTcPass) {
+        FusedArgs p = p0;
+        p.n = p0.n - off < esom::kTcPass ? p0.n - off : esom::kTcPass;
+        p.X = p0.X + off * h->d;
+        p.idx = p0.idx + off * h->k;
+        p.dist2 = p0.dist2 + off * h->k;
+        p.out = p0.out + off * 2;
+        if (off > 0) p.perm = nullptr;  // a visiting order covers one pass
+        cudaError_t e = cudaMemsetAsync(rcount, 0, sizeof(unsigned), stream);
+        if (e == cudaSuccess) {
+            const bool res =
+                h->nchunks == 1 && esom::project_smem_bytes(h->d, h->L, true) <= h->proj_smem;
+            p.nchunks = res ? 1 : 2;
+            p.ntiles = (p.n + esom::kThreads - 1) / esom::kThreads;
+            long long grid = (long long)h->proj_blocks_per_sm * h->num_sms;
+            if (grid > p.ntiles) grid = p.ntiles;
+            e = h->ops->launch_proj(p, (int)grid, h->proj_smem, stream);
+        }
+        if (e == cudaSuccess) e = launch_refine(h, p, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "projection kernel launch");
+    }
+    return ESOM_OK;
 }
 
 esom_status launch(esom_ctx *h, const float *points, long long n, float *out, int *idx,
@@ -295,10 +341,35 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
             cudaError_t r = cudaMemsetAsync(fail_count, 0, sizeof(unsigned), stream);
             if (r != cudaSuccess) return r;
             if (h->screening) {
+                // points grouped by home chunk; the tensor-core k-NN writes
+                // screened lists, re-ranked exactly by the next kernel
+                FusedArgs t = k;
+                t.m_dot = esom::tc_dot_bound(h->d, tc_prec(h->screening));
+                t.cand = h->cand;
+                if (h->order_on) {
+                    r = esom::launch_point_order(k.X, cnt, h->d, h->centers,
+                                                 (h->L + esom::kTcN - 1) / esom::kTcN, k.center,
+                                                 h->home, h->counts, esom::kOrderBlocks, h->perm,
+                                                 h->tile_home, stream);
+                    if (r != cudaSuccess) return r;
+                    t.perm = h->perm;
+                    t.tile_home = h->tile_home;
+                    t.corder = h->corder;
+                    t.lperm = h->lperm;
+                    t.norms = h->norms_int;
+                }
                 const long long tiles = (cnt + esom::kTcRows - 1) / esom::kTcRows;
                 long long grid = (long long)h->tc_blocks_per_sm * h->num_sms;
                 if (grid > tiles) grid = tiles;
-                r = h->tc->launch(k, (int)grid, h->tc_smem, stream);
+                r = h->tc->launch(t, (int)grid, h->tc_smem, stream);
+                if (r != cudaSuccess) return r;
+                FusedArgs rr = t;
+                rr.norms = h->norms;
+                rr.nchunks = h->rerank_smem > esom::rerank_smem_bytes(h->d, h->L, false) ? 1 : 2;
+                const long long rtiles = (cnt + esom::kThreads - 1) / esom::kThreads;
+                long long rgrid = (long long)h->rerank_blocks_per_sm * h->num_sms;
+                if (rgrid > rtiles) rgrid = rtiles;
+                r = h->ops->launch_rerank(rr, (int)rgrid, h->rerank_smem, stream);
             } else {
                 k.ntiles = (cnt + esom::kThreads - 1) / esom::kThreads;
                 long long grid = (long long)h->blocks_per_sm * h->num_sms;
@@ -330,6 +401,9 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                 if (e != cudaSuccess) break;
                 FusedArgs p = k;
                 p.out = out + off * 2;
+                // the points in the k-NN's visiting order: neighbouring
+                // threads then share landmark rows and table rows
+                p.perm = h->screening && h->order_on ? h->perm : nullptr;
                 // rows resident when they fit the configured shared memory;
                 // the projection kernel reads the distance table whenever
                 // there is one (measured 22% faster than recomputing from
@@ -339,11 +413,29 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
             }
         }
     } else {
-        long long grid = (long long)h->blocks_per_sm * h->num_sms;
-        if (grid > a.ntiles) grid = a.ntiles;
-        a.stall_ns = h->stall_ns;
-        h->stall_ns = 0;
-        e = h->ops->launch(a, (int)grid, h->smem, stream);
+        // the fused kernel, in passes of at most kTcPass points (the refine
+        // list holds one pass), each projection followed by the FP64
+        // recomputation of the points it listed
+        unsigned *rcount = reinterpret_cast<unsigned *>(h->status) + 4;
+        for (long long off = 0; off < n && e == cudaSuccess; off += esom::kTcPass) {
+            FusedArgs f = a;
+            f.n = n - off < esom::kTcPass ? n - off : esom::kTcPass;
+            f.X = points + off * h->d;
+            if (mode == esom::kKnn) {
+                f.idx = idx + off * h->k;
+                f.dist2 = dist2 ? dist2 + off * h->k : nullptr;
+            } else {
+                f.out = out + off * 2;
+            }
+            f.ntiles = (f.n + esom::kThreads - 1) / esom::kThreads;
+            long long grid = (long long)h->blocks_per_sm * h->num_sms;
+            if (grid > f.ntiles) grid = f.ntiles;
+            f.stall_ns = h->stall_ns;
+            h->stall_ns = 0;
+            if (mode == esom::kProject) e = cudaMemsetAsync(rcount, 0, sizeof(unsigned), stream);
+            if (e == cudaSuccess) e = h->ops->launch(f, (int)grid, h->smem, stream);
+            if (e == cudaSuccess && mode == esom::kProject) e = launch_refine(h, f, stream);
+        }
     }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     h->points += (uint64_t)n;
@@ -397,6 +489,7 @@ esom_status esom_create(int d, int L, int k, esom_handle *out) {
                                       sizeof(float));
     if (e == cudaSuccess && L <= esom::kQtabMaxL)
         e = cudaMalloc(&h->qtab, (size_t)L * L * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->refine_list, (size_t)esom::kTcPass * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->status, 256);
     if (e == cudaSuccess) e = cudaMemset(h->status, 0, 256);
     if (e != cudaSuccess) {
@@ -434,8 +527,7 @@ esom_status esom_set_landmarks(esom_handle h, const float *hi, const float *lo,
                                                          esom::kTcN,
                                                          h->centered ? h->center : nullptr);
     if (e == cudaSuccess && h->qtab) e = h->ops->launch_qtab(h->hi, h->L, h->qtab, st);
-    if (e == cudaSuccess && h->screening)
-        e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, tc_prec(h->screening), st);
+    if (e == cudaSuccess && h->screening) e = build_screening(h, tc_prec(h->screening), st);
     if (e != cudaSuccess) return cuda_fail(e, "landmark copy");
     ++h->version;
     return ESOM_OK;
@@ -566,13 +658,15 @@ esom_status esom_get_stats(esom_handle h, esom_stream_t stream, esom_stats *out,
     esom_status s = check_device(h);
     if (s != ESOM_OK) return s;
     cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
-    unsigned words[4] = {0, 0, 0, 0};
+    unsigned words[6] = {0, 0, 0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpy(words, h->status, sizeof(words), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "stats read");
     out->points = h->points;
     out->rescans = words[2];
+    out->refines = words[5];
     if (reset) {
         e = cudaMemset(h->status + 2, 0, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemset(h->status + 5, 0, sizeof(unsigned));
         if (e != cudaSuccess) return cuda_fail(e, "stats reset");
         h->points = 0;
     }
@@ -871,9 +965,62 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
                         cudaGetErrorString(e));
         }
     }
+    // the exact re-rank of the screened lists, and its candidate buffer
+    {
+        const bool res = (size_t)h->L * h->d * sizeof(float) <= kRerankResidentBytes;
+        const size_t rsmem = esom::rerank_smem_bytes(h->d, h->L, res);
+        e = cudaFuncSetAttribute(h->ops->rerank_func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin);
+        int rbps = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rbps, h->ops->rerank_func,
+                                                              esom::kThreads, rsmem);
+        if (e != cudaSuccess) return cuda_fail(e, "re-rank kernel configuration");
+        if (rbps < 1) return fail(ESOM_EUNSUPPORTED, "re-rank launch does not fit on an SM");
+        h->rerank_smem = rsmem;
+        h->rerank_blocks_per_sm = rbps;
+    }
+    const int nch = (h->L + esom::kTcN - 1) / esom::kTcN;
+    if (!h->cand) {
+        e = cudaMalloc(&h->cand, (size_t)esom::kTcPass * h->kc * sizeof(float));
+        if (e != cudaSuccess) {
+            h->cand = nullptr;
+            return fail(ESOM_ENOMEM, "device allocation of the candidate lists: %s",
+                        cudaGetErrorString(e));
+        }
+    }
+    if (h->L <= esom::kOrderMaxL && !h->lperm) {
+        e = cudaMalloc(&h->lperm, (size_t)h->L * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&h->centers, (size_t)nch * h->d * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&h->norms_int, (size_t)nch * esom::kTcN * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&h->corder, (size_t)nch * nch * sizeof(unsigned short));
+        if (e == cudaSuccess) e = cudaMalloc(&h->home, (size_t)esom::kTcPass * sizeof(unsigned short));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&h->counts, (size_t)esom::kOrderBlocks * nch * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&h->perm, (size_t)esom::kTcPass * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&h->tile_home,
+                           (size_t)(esom::kTcPass / esom::kTcRows) * sizeof(unsigned short));
+        if (e != cudaSuccess) {
+            cudaFree(h->lperm);
+            cudaFree(h->centers);
+            cudaFree(h->norms_int);
+            cudaFree(h->corder);
+            cudaFree(h->home);
+            cudaFree(h->counts);
+            cudaFree(h->perm);
+            cudaFree(h->tile_home);
+            h->lperm = nullptr;
+            h->centers = h->norms_int = nullptr;
+            h->corder = h->home = h->tile_home = nullptr;
+            h->counts = h->perm = nullptr;
+            return fail(ESOM_ENOMEM, "device allocation of the screening orders: %s",
+                        cudaGetErrorString(e));
+        }
+    }
+    h->order_on = h->lperm != nullptr;
     if (h->version > 0) {
-        e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, prec,
-                                  reinterpret_cast<cudaStream_t>(stream));
+        e = build_screening(h, prec, reinterpret_cast<cudaStream_t>(stream));
         if (e != cudaSuccess) return cuda_fail(e, "landmark image build");
     }
     h->tc = tc;
@@ -889,12 +1036,22 @@ esom_status esom_destroy(esom_handle h) {
     cudaFree(h->lo);
     cudaFree(h->norms);
     cudaFree(h->status);
+    cudaFree(h->refine_list);
     cudaFree(h->img);
     cudaFree(h->qtab);
     cudaFree(h->tc_idx);
     cudaFree(h->tc_d2);
     cudaFree(h->fail_list);
     cudaFree(h->center);
+    cudaFree(h->cand);
+    cudaFree(h->lperm);
+    cudaFree(h->centers);
+    cudaFree(h->norms_int);
+    cudaFree(h->corder);
+    cudaFree(h->home);
+    cudaFree(h->counts);
+    cudaFree(h->perm);
+    cudaFree(h->tile_home);
     for (int b = 0; b < 2; ++b) {
         cudaFree(h->stage_x[b]);
         cudaFree(h->stage_out[b]);
@@ -949,6 +1106,7 @@ esom_status esom_selftest_tc_products(esom_handle h, const float *points, int64_
     esom::fill_args(h, points, n, nullptr, 1.f, 1.f, &a);
     a.mode = esom::kKnn;
     a.dist2 = T;
+    a.lperm = h->order_on ? h->lperm : nullptr;  // the images are in this order
     const long long tiles = (n + esom::kTcRows - 1) / esom::kTcRows;
     const int grid = (int)(tiles < h->num_sms ? tiles : h->num_sms);
     e = op->launch(a, grid, smem, reinterpret_cast<cudaStream_t>(stream));

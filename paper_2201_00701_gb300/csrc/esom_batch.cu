@@ -55,6 +55,7 @@ struct Group {
     FusedArgs *d_items = nullptr;
     long long *d_tile_base = nullptr, *d_cta_begin = nullptr;
     int *d_tile_item = nullptr;
+    int2 *d_refine = nullptr;        // (dataset, row) of ill-conditioned points
     int grid = 0;
     size_t smem = 0;
     Shape shape{0, 0};
@@ -173,7 +174,13 @@ esom_status launch_group(esom_batch_ctx *b, const Group &g, cudaStream_t st) {
     a.tile_item = g.d_tile_item;
     a.cta_begin = g.d_cta_begin;
     a.status = b->status;
-    const cudaError_t e = g.ops->launch_batch(a, g.grid, g.smem, st);
+    // points whose FP32 system is too ill-conditioned: listed by the group's
+    // launch, recomputed in FP64 right after it
+    a.refine_list = g.d_refine;
+    a.refine_count = reinterpret_cast<unsigned *>(b->status) + 4;
+    cudaError_t e = cudaMemsetAsync(a.refine_count, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = g.ops->launch_batch(a, g.grid, g.smem, st);
+    if (e == cudaSuccess) e = g.ops->launch_refine_batch(a, 2 * b->num_sms, st);
     return e == cudaSuccess ? ESOM_OK : bcuda(e, "batch launch");
 }
 
@@ -298,7 +305,11 @@ esom_status esom_batch_create(const esom_batch_item *items, int count, int autot
             g.tiles += nt;
             g.args.push_back(a);
         }
+        long long group_points = 0;
+        for (const FusedArgs &fa : g.args) group_points += fa.n;
         e = cudaMalloc(&g.d_items, g.args.size() * sizeof(FusedArgs));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&g.d_refine, (size_t)(group_points > 0 ? group_points : 1) * sizeof(int2));
         if (e == cudaSuccess) e = cudaMalloc(&g.d_tile_base, g.tile_base.size() * sizeof(long long));
         if (e == cudaSuccess && g.tiles > 0) e = cudaMalloc(&g.d_tile_item, g.tile_item.size() * sizeof(int));
         if (e == cudaSuccess)
@@ -373,6 +384,7 @@ esom_status esom_batch_destroy(esom_batch b) {
         cudaFree(g.d_tile_base);
         cudaFree(g.d_tile_item);
         cudaFree(g.d_cta_begin);
+        cudaFree(g.d_refine);
     }
     cudaFree(b->status);
     delete b;

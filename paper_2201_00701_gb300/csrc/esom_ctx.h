@@ -13,7 +13,11 @@ struct esom_ctx {
     float *hi = nullptr;   // L x d
     float *lo = nullptr;   // L x 2
     float *norms = nullptr; // squared landmark norms, zero-padded to a multiple of kTcN
-    int *status = nullptr; // device status word; the float after it: largest norm
+    // device status words: [0] error bits, [1] the largest norm (float),
+    // [2] rescans since the stats reset, [3] certificate failures of the
+    // current pass, [4] refine-list length of the current pass
+    int *status = nullptr;
+    long long *refine_list = nullptr;  // rows of one pass for the FP64 recomputation
     float *qtab = nullptr; // L x L squared landmark distances (L <= kQtabMaxL)
     uint64_t version = 0;
     const esom::KernelOps *ops = nullptr;
@@ -44,6 +48,24 @@ struct esom_ctx {
     long long *fail_list = nullptr;  // rows whose certificate failed (kTcPass)
     int proj_blocks_per_sm = 0;
     size_t proj_smem = 0;
+    // tensor-core k-NN: screened lists of one pass (kTcPass x kc keys) and
+    // the exact re-rank kernel's configuration
+    float *cand = nullptr;
+    int rerank_blocks_per_sm = 0;
+    size_t rerank_smem = 0;
+    // spatial orders of the tensor-core screening (L <= kOrderMaxL):
+    // landmark order, chunk centroids, norms in the internal order, chunk
+    // visiting orders; per pass: point homes, block counts, visiting order
+    // of the points, home chunk of each tile
+    int order_on = 0;
+    int *lperm = nullptr;
+    float *centers = nullptr;
+    float *norms_int = nullptr;
+    unsigned short *corder = nullptr;
+    unsigned short *home = nullptr;
+    int *counts = nullptr;
+    int *perm = nullptr;
+    unsigned short *tile_home = nullptr;
     // host-buffer pipeline state (created on first use)
     float *stage_x[2] = {nullptr, nullptr};
     float *stage_out[2] = {nullptr, nullptr};

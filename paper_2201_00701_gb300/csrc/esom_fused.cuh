@@ -467,14 +467,16 @@ template <int D, int KC, int KK>
 __device__ __forceinline__ bool rerank(const float4 (&x)[D / 4], const float (&keys)[KC],
                                        const float4 *Lg, uint32_t mask, int L, int k, float M,
                                        float q, float (&ed)[KK], int (&ei)[KK],
-                                       float koff = 0.f) {
+                                       float koff = 0.f, const int *lperm = nullptr) {
     float cd[KC];
     int ci[KC];
 #pragma unroll
     for (int t = 0; t < KC; ++t) {
         const bool valid = keys[t] < INFINITY;
         // (the min() only guards the row read; listed keys carry indices < L)
-        ci[t] = valid ? min((int)(__float_as_uint(keys[t]) & mask), L - 1) : 0;
+        const int j = valid ? min((int)(__float_as_uint(keys[t]) & mask), L - 1) : 0;
+        // keys of a reordered screening carry internal positions
+        ci[t] = lperm ? __ldg(lperm + j) : j;
         cd[t] = valid ? dist2_row<D>(x, Lg, ci[t]) : INFINITY;
     }
     // The screened order is the exact order except near ties; when it is
@@ -522,19 +524,12 @@ __device__ __forceinline__ int nb_at(const uint32_t *col, int t) {
 }
 
 // ---------------------------------------------------------------------------
-// Step 3: pair terms over u < v < m.  PASS 0 accumulates the normal system
-// (A, b); PASS 1 accumulates rho = sum w (h.n)^2 / r for a unit 2-D direction
-// n (the Rayleigh quotient n^T A n) and skips the work only PASS 0 needs.
-// D_uv uses the law of cosines on the exact squared distances:
+// Step 3: pair terms over u < v < m, accumulated into the normal system
+// (A, b).  D_uv uses the law of cosines on the exact squared distances:
 // <X - L_u, L_v - L_u> = (|X - L_u|^2 + |L_v - L_u|^2 - |X - L_v|^2) / 2.
-
-// One pair's contribution: D_uv by the law of cosines, the 2-D operator,
-// the weight w = s_u s_v r^-adjust, and the normal-system terms.  `ok` is
-// false when L_u = L_v or l_u = l_v (the pair is skipped).
-struct PairTerm {
-    float a00, a01, a11, b0, b1, rho;
-    bool ok;
-};
+// Every kernel that projects adds the same terms in the same order (u
+// ascending, then v ascending) with pair_add, so all execution plans give
+// the same bits whatever layout their neighbour data has.
 
 // |L_v - L_u|^2 in the FP32 difference form with four partial sums; the
 // table of squared landmark distances (landmark_dist_kernel) holds exactly
@@ -555,56 +550,50 @@ __device__ __forceinline__ float pair_q(const float4 (&lu)[D / 4], const float4 
     return (q0 + q1) + (q2 + q3);
 }
 
-// qq = |L_v - L_u|^2 (from the distance table or pair_q).
-template <int D, int PASS>
-__device__ __forceinline__ PairTerm pair_term(float2 lut, float lux, float luy, float su,
-                                              float du, int iv, float sv, float dv, float qq,
-                                              const float2 *lo2, float adjust, float nx,
-                                              float ny) {
-    const float2 lvt = lo2[iv];
-    const float hx = lvt.x - lut.x, hy = lvt.y - lut.y;
+struct NormalSys {
+    float a00, a01, a11, b0, b1;
+};
+
+// One pair's terms: the 2-D operator h = l_v - l_u (positions relative to
+// the nearest neighbour's), r = |h|^2, the weight w = s_u s_v r^-adjust
+// (1/r itself for adjust = 1, else by the SFU, relative error ~1e-6), D_uv,
+// and w h h^T / r and w h (D_uv + <h, l_u>/r) added to the system.  A pair
+// that does not count (use false: outside u < v < m; or L_u = L_v, qq = 0;
+// or l_u = l_v, r = 0) gets weight 0 with finite intermediates, so it adds
+// exact zeros.
+template <bool ADJ1>
+__device__ __forceinline__ void pair_add(float ux, float uy, float su, float du, float vx,
+                                         float vy, float sv, float dv, float qq, bool use,
+                                         float adjust, NormalSys &S) {
+    const float hx = vx - ux, hy = vy - uy;
     const float r = fmaf(hx, hx, hy * hy);
-    PairTerm t;
-    t.ok = qq > 0.f && r > 0.f;
-    const float ir = rcp_fast(r);
-    // r^-adjust: 1/r itself for the common adjust = 1, else by the SFU
-    // (relative error ~1e-6)
-    const float w = su * sv * (adjust == 1.f ? ir : exp2f_fast(-adjust * log2f_fast(r)));
+    const bool ok = use && qq > 0.f && r > 0.f;
+    const float ir = r > 0.f ? rcp_fast(r) : 0.f;
+    const float wr0 = ADJ1 ? ir : exp2f_fast(-adjust * log2f_fast(r));
+    const float w = ok ? su * sv * wr0 : 0.f;
     const float wr = w * ir;
-    if (PASS == 0) {
-        const float Duv = fmaf(0.5f * (du - dv), rcp_fast(qq), 0.5f);
-        const float rhs = fmaf(fmaf(hx, lux, hy * luy), ir, Duv);
-        t.a00 = wr * hx * hx;
-        t.a01 = wr * hx * hy;
-        t.a11 = wr * hy * hy;
-        const float wrhs = w * rhs;
-        t.b0 = wrhs * hx;
-        t.b1 = wrhs * hy;
-        t.rho = 0.f;
-    } else {
-        const float tt = fmaf(hx, nx, hy * ny);
-        t.rho = wr * tt * tt;
-        t.a00 = t.a01 = t.a11 = t.b0 = t.b1 = 0.f;
-    }
-    return t;
+    const float Duv = fmaf(0.5f * (du - dv), qq > 0.f ? rcp_fast(qq) : 0.f, 0.5f);
+    const float rhs = fmaf(fmaf(hx, ux, hy * uy), ir, Duv);
+    const float th = wr * hx;
+    S.a00 = fmaf(th, hx, S.a00);
+    S.a01 = fmaf(th, hy, S.a01);
+    S.a11 = fmaf(wr * hy, hy, S.a11);
+    const float wrhs = w * rhs;
+    S.b0 = fmaf(wrhs, hx, S.b0);
+    S.b1 = fmaf(wrhs, hy, S.b1);
 }
 
-// Step 3: pair terms over u < v < m.  PASS 0 accumulates the normal system
-// (A, b); PASS 1 accumulates rho = sum w (h.n)^2 / r for a unit 2-D direction
-// n (the Rayleigh quotient n^T A n).  D_uv uses the law of cosines on the
-// exact squared distances:
-// <X - L_u, L_v - L_u> = (|X - L_u|^2 + |L_v - L_u|^2 - |X - L_v|^2) / 2.
-// The v loop runs in groups of two pairs with independent chains; pairs
-// outside u < v < m inside a group are masked by selects.
-// PF: gather this u's table entries up front (the projection kernel, which
-// always has the table); else each pair reads its entry, or computes it
-// from the rows when there is no table.
-template <int D, int KK, int PASS, int QS = kThreads, bool PF = false>
-__device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t *nb,
-                                          const float (&ss)[KK], int m, const float4 *Lg,
-                                          const float2 *lo2, float2 l0, const FusedArgs &a,
-                                          float nx, float ny, float &A00, float &A01,
-                                          float &A11, float &B0, float &B1, float &rho) {
+// The pairs of one point whose neighbour indices sit in this thread's column
+// of shared memory (nb_at) and whose scores and distances are in registers;
+// 2-D positions gathered from lo2, |L_v - L_u|^2 from the table when given,
+// else from the rows.  PF (the projection kernel, which always has the
+// table): row u's table entries are gathered up front, predicated and
+// independent, so their L2 latencies overlap.
+template <int D, int KK, bool ADJ1, int QS = kThreads, bool PF = false>
+__device__ __forceinline__ void pair_sums_regs(const float (&sd)[KK], const float (&ss)[KK],
+                                               const uint32_t *nb, int m, const float4 *Lg,
+                                               const float2 *lo2, float2 l0, const FusedArgs &a,
+                                               NormalSys &S) {
 #pragma unroll 1
     for (int u = 0; u < m - 1; ++u) {
         const int iu = nb_at<QS>(nb, u);
@@ -623,43 +612,23 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
         for (int e = 0; e < D / 4; ++e)
             lu[e] = qrow ? make_float4(0.f, 0.f, 0.f, 0.f) : Lu[e ^ fu];
         const float2 lut = lo2[iu];
-        const float lux = lut.x - l0.x, luy = lut.y - l0.y;  // l_u relative to l_0
-        // With PF, this u's distances are gathered up front (predicated,
-        // independent loads) so their L2 latencies overlap.
+        const float ux = lut.x - l0.x, uy = lut.y - l0.y;
         float qv[PF ? KK : 1];
 #pragma unroll
         for (int v = 0; v < (PF ? KK : 1); ++v)
             qv[v] = (PF && v > u && v < m) ? __ldg(qrow + nb_at<QS>(nb, v)) : 1.f;
-        auto qof = [&](int v, int iv) -> float {
-            if (PF) return qv[v < (PF ? KK : 1) ? v : 0];
-            return qrow ? __ldg(qrow + iv) : pair_q<D>(lu, Lg + (size_t)iv * (D / 4), swz(D, iv));
-        };
 #pragma unroll
         for (int v0 = 1; v0 < KK; v0 += 2) {
             if (v0 + 1 > u && v0 < m) {
-                const int iv0 = nb_at<QS>(nb, v0);
-                const PairTerm c0 = pair_term<D, PASS>(lut, lux, luy, su, du, iv0, ss[v0], sd[v0],
-                                                       qof(v0, iv0), lo2, a.adjust, nx, ny);
-                const bool k0 = c0.ok && v0 > u;
-                A00 = k0 ? A00 + c0.a00 : A00;
-                A01 = k0 ? A01 + c0.a01 : A01;
-                A11 = k0 ? A11 + c0.a11 : A11;
-                B0 = k0 ? B0 + c0.b0 : B0;
-                B1 = k0 ? B1 + c0.b1 : B1;
-                rho = k0 ? rho + c0.rho : rho;
-                if (v0 + 1 < KK) {
-                    const int v1 = v0 + 1 < KK ? v0 + 1 : v0;
-                    const int iv1 = nb_at<QS>(nb, v1);
-                    const PairTerm c1 =
-                        pair_term<D, PASS>(lut, lux, luy, su, du, iv1, ss[v1], sd[v1],
-                                           qof(v1, iv1), lo2, a.adjust, nx, ny);
-                    const bool k1 = c1.ok && v1 < m;
-                    A00 = k1 ? A00 + c1.a00 : A00;
-                    A01 = k1 ? A01 + c1.a01 : A01;
-                    A11 = k1 ? A11 + c1.a11 : A11;
-                    B0 = k1 ? B0 + c1.b0 : B0;
-                    B1 = k1 ? B1 + c1.b1 : B1;
-                    rho = k1 ? rho + c1.rho : rho;
+#pragma unroll
+                for (int v = v0; v < v0 + 2 && v < KK; ++v) {
+                    const int iv = nb_at<QS>(nb, v);
+                    const float2 lvt = lo2[iv];
+                    const float qq = PF     ? qv[v < (PF ? KK : 1) ? v : 0]
+                                     : qrow ? __ldg(qrow + iv)
+                                            : pair_q<D>(lu, Lg + (size_t)iv * (D / 4), swz(D, iv));
+                    pair_add<ADJ1>(ux, uy, su, du, lvt.x - l0.x, lvt.y - l0.y, ss[v], sd[v], qq,
+                                   v > u && v < m, a.adjust, S);
                 }
             }
         }
@@ -667,161 +636,16 @@ __device__ __forceinline__ void pair_sums(const float (&sd)[KK], const uint32_t 
 }
 
 // ---------------------------------------------------------------------------
-// Steps 2-4 of one point again, in FP64 (the rare path; out of line).  When
-// the FP32 normal system is ill-conditioned (det/trace^2 below kDetRefine)
-// the rounding of its FP32 terms and sums, about 1e-7 relative, is amplified
-// by the condition number, so the point is recomputed from its inputs in
-// FP64: the k neighbours' squared distances from the rows, the scores in the
-// form of reading R2 (weights 1/i over the m = k - 1 scored neighbours,
-// spread about the weighted mean, exp(boost (delta_1 - delta_i) / sigma)
-// times the cut-off factor), each pair's D_uv = <X - L_u, L_v - L_u> / q as
-// a dot product, the normal system, and the solve of reading R5: Cramer's
-// rule if det > 1e-10 trace^2, else the least-norm solution about the
-// score-weighted centroid of the scored 2-D landmarks (the plain mean if
-// every score is 0), or that centroid when A = 0.  The neighbours keep the
-// rank order of the k-NN result.  xrow is the point's row as stored (the
-// centre, when set, is subtracted here as the landmark rows are stored
-// centred); rows of Lg are chunk-swizzled.
-
-template <int D, int KK, int QS = kThreads>
-__device__ __noinline__ double2 refine_fp64(const float *xrow, const float *center,
-                                            const uint32_t *nb, int k, const float4 *Lg,
-                                            const float2 *lo2, float boost, float adjust) {
+// Step 2: scores from the exact squared distances of the k nearest.
+// Distances are Euclidean; the weights of the mean and spread are 1/i over
+// the m scored neighbours.  exp(boost (d_1 - d_i) / sigma) differs from
+// exp(boost (mean - d_i) / sigma) by one common factor, which cancels in the
+// solve, and it cannot overflow.  Euclidean distances by the SFU reciprocal
+// square root (relative error ~2^-22, far below what the scores need).
+template <int KK>
+__device__ __forceinline__ void point_scores(const float (&sd)[KK], int k, float boost,
+                                             float (&ss)[KK]) {
     const int m = k - 1;
-    double x[D];
-#pragma unroll
-    for (int t = 0; t < D; ++t)
-        x[t] = (double)xrow[t] - (center ? (double)center[t] : 0.0);
-    double del[KK];
-    int id[KK];
-    for (int i = 0; i < k; ++i) {
-        const int j = nb_at<QS>(nb, i);
-        id[i] = j;
-        const float4 *l = Lg + (size_t)j * (D / 4);
-        const int f = swz(D, j);
-        double acc = 0.0;
-#pragma unroll
-        for (int e = 0; e < D / 4; ++e) {
-            const float4 q = l[e ^ f];
-            const double d0 = x[4 * e] - q.x, d1 = x[4 * e + 1] - q.y;
-            const double d2 = x[4 * e + 2] - q.z, d3 = x[4 * e + 3] - q.w;
-            acc += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
-        }
-        del[i] = sqrt(acc);
-    }
-    // step 2: scores
-    double wsum = 0.0, mean = 0.0;
-    for (int i = 0; i < m; ++i) {
-        wsum += 1.0 / (double)(i + 1);
-        mean += del[i] / (double)(i + 1);
-    }
-    mean /= wsum;
-    double var = 0.0;
-    for (int i = 0; i < m; ++i) var += (del[i] - mean) * (del[i] - mean) / (double)(i + 1);
-    const double sigma = sqrt(var / wsum);
-    const double dk = del[k - 1];
-    const bool flat = sigma <= 1e-12 * fmax(mean, 1e-300);
-    double ss[KK], px[KK], py[KK];
-    const float2 l0 = lo2[id[0]];
-    double C0 = 0.0, C1 = 0.0, Ssum = 0.0, M0 = 0.0, M1 = 0.0;
-    for (int i = 0; i < m; ++i) {
-        const double f1 = flat ? 1.0 : exp((double)boost * (del[0] - del[i]) / sigma);
-        const double f2 = dk > 0.0 ? -expm1((double)kScoreEdge * (del[i] / dk - 1.0)) : 1.0;
-        ss[i] = f1 * f2;
-        const float2 li = lo2[id[i]];
-        px[i] = (double)li.x - (double)l0.x;  // relative to the nearest neighbour's
-        py[i] = (double)li.y - (double)l0.y;
-        C0 += ss[i] * px[i];
-        C1 += ss[i] * py[i];
-        Ssum += ss[i];
-        M0 += px[i];
-        M1 += py[i];
-    }
-    // step 3: pairs u < v < m
-    double a00 = 0.0, a01 = 0.0, a11 = 0.0, b0 = 0.0, b1 = 0.0;
-    for (int u = 0; u < m; ++u) {
-        const float4 *Lu = Lg + (size_t)id[u] * (D / 4);
-        const int fu = swz(D, id[u]);
-        for (int v = u + 1; v < m; ++v) {
-            const float4 *Lv = Lg + (size_t)id[v] * (D / 4);
-            const int fv = swz(D, id[v]);
-            double q = 0.0, g = 0.0;
-#pragma unroll
-            for (int e = 0; e < D / 4; ++e) {
-                const float4 cu = Lu[e ^ fu], cv = Lv[e ^ fv];
-                const double e0 = (double)cv.x - cu.x, e1 = (double)cv.y - cu.y;
-                const double e2 = (double)cv.z - cu.z, e3 = (double)cv.w - cu.w;
-                q += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3;
-                g += (x[4 * e] - cu.x) * e0 + (x[4 * e + 1] - cu.y) * e1 +
-                     (x[4 * e + 2] - cu.z) * e2 + (x[4 * e + 3] - cu.w) * e3;
-            }
-            const double hx = px[v] - px[u], hy = py[v] - py[u];
-            const double r = hx * hx + hy * hy;
-            if (!(q > 0.0) || !(r > 0.0)) continue;
-            const double Duv = g / q;
-            const double w = ss[u] * ss[v] / (adjust == 1.f ? r : pow(r, (double)adjust));
-            const double rhs = Duv + (hx * px[u] + hy * py[u]) / r;
-            a00 += w * hx * hx / r;
-            a01 += w * hx * hy / r;
-            a11 += w * hy * hy / r;
-            b0 += w * hx * rhs;
-            b1 += w * hy * rhs;
-        }
-    }
-    // step 4: solve
-    const double det = a00 * a11 - a01 * a01, tr = a00 + a11;
-    double rx, ry;
-    if (det > kDetEps * tr * tr) {
-        rx = (b0 * a11 - a01 * b1) / det;
-        ry = (a00 * b1 - a01 * b0) / det;
-    } else {
-        const double c0 = Ssum > 0.0 ? C0 / Ssum : M0 / (double)m;
-        const double c1 = Ssum > 0.0 ? C1 / Ssum : M1 / (double)m;
-        rx = c0;
-        ry = c1;
-        if (tr > 0.0) {
-            const double disc = sqrt((a00 - a11) * (a00 - a11) + 4.0 * a01 * a01);
-            const double lam = 0.5 * (tr + disc);
-            // major eigenvector: the better conditioned of two forms
-            const double va0 = a01, va1 = lam - a00, vb0 = lam - a11, vb1 = a01;
-            const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
-            double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
-            double nn = ga >= gb ? ga : gb;
-            if (nn == 0.0) {
-                v0 = 1.0;
-                v1 = 0.0;
-                nn = 1.0;
-            }
-            nn = sqrt(nn);
-            v0 /= nn;
-            v1 /= nn;
-            const double r0 = b0 - (a00 * c0 + a01 * c1);
-            const double r1 = b1 - (a01 * c0 + a11 * c1);
-            const double t = (v0 * r0 + v1 * r1) / lam;
-            rx = c0 + t * v0;
-            ry = c1 + t * v1;
-        }
-    }
-    return make_double2(rx + (double)l0.x, ry + (double)l0.y);
-}
-
-// ---------------------------------------------------------------------------
-// Steps 2-4 for one point: scores, pair sums, FP64 solve.  sd holds the
-// exact squared distances of the k nearest; their landmark indices are in
-// this thread's column of shared memory (nb_at(nb, t) for rank t).
-
-template <int D, int KK, int QS = kThreads, bool PF = false>
-__device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uint32_t *nb,
-                                                const float4 *Lg, const float2 *lo2,
-                                                const FusedArgs &a, const float *xrow) {
-    const int k = a.k, m = k - 1;
-
-    // Step 2: scores.  Distances are Euclidean; the weights of the mean and
-    // spread are 1/i over the m scored neighbours.  exp(boost (d_1 - d_i) /
-    // sigma) differs from exp(boost (mean - d_i) / sigma) by one common
-    // factor, which cancels in the solve, and it cannot overflow.
-    // Euclidean distances by the SFU reciprocal square root (relative error
-    // ~2^-22, far below what the scores need).
     float del[KK];
 #pragma unroll
     for (int t = 0; t < KK; ++t) del[t] = sd[t] > 0.f ? sd[t] * rsqrtf(sd[t]) : 0.f;
@@ -845,9 +669,8 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
     const float sigma = sqrtf(var / wsum);
     const float dk = at<KK>(del, k - 1);
     const bool flat = sigma <= kSigmaEps * fmaxf(mean, 1e-30f);
-    const float inv_sigma = flat ? 0.f : a.boost / sigma;
+    const float inv_sigma = flat ? 0.f : boost / sigma;
     const float inv_dk = dk > 0.f ? 1.0f / dk : 0.f;
-    float ss[KK];
 #pragma unroll
     for (int t = 0; t < KK; ++t) {
         float s = 0.f;
@@ -863,17 +686,36 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
         }
         ss[t] = s;
     }
+}
 
-    // 2-D coordinates relative to the nearest neighbour's.
-    const float2 l0 = lo2[nb_at<QS>(nb, 0)];
+// Where a point whose FP32 system is too ill-conditioned goes: its row is
+// appended to a list that refine_kernel (refine_batch_kernel for the batched
+// kernel) then recomputes in FP64.  Deferring it keeps the FP64 code, and
+// the call it would need, out of the kernels' hot loops: a rare-path call
+// there made them spill registers (measured 1.3-4x slower projections).
+struct RefineSink {
+    long long *list;
+    unsigned *count;
+    __device__ __forceinline__ void operator()(long long row) const {
+        list[atomicAdd(count, 1u)] = row;
+    }
+};
+struct BatchRefineSink {
+    int2 *list;
+    unsigned *count;
+    int item;
+    __device__ __forceinline__ void operator()(long long row) const {
+        list[atomicAdd(count, 1u)] = make_int2(item, (int)row);
+    }
+};
 
-    // Step 3: pair terms, u < v < m.
-    float A00 = 0.f, A01 = 0.f, A11 = 0.f, B0 = 0.f, B1 = 0.f, rho = 0.f;
-    pair_sums<D, KK, 0, QS, PF>(sd, nb, ss, m, Lg, lo2, l0, a, 0.f, 0.f, A00, A01, A11, B0, B1,
-                                rho);
-
-    // Step 4: FP64 solve; ill-conditioned systems are recomputed in FP64.
-    const double a00 = A00, a01 = A01, a11 = A11, b0 = B0, b1 = B1;
+// Step 4: FP64 solve of the normal system (coordinates relative to l0).  A
+// system with det/trace^2 at or below kDetRefine goes to the sink (for an
+// active point) and l0 stands in until the FP64 recomputation replaces it.
+template <class SINK>
+__device__ __forceinline__ float2 point_solve(const NormalSys &S, float2 l0, long long row,
+                                              bool active, const SINK &sink) {
+    const double a00 = S.a00, a01 = S.a01, a11 = S.a11, b0 = S.b0, b1 = S.b1;
     const double det = a00 * a11 - a01 * a01;
     const double tr = a00 + a11;
     if (__builtin_expect(det > kDetRefine * tr * tr, 1)) {
@@ -882,8 +724,29 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
         const double py = (a00 * b1 - a01 * b0) * id;
         return make_float2((float)(px + (double)l0.x), (float)(py + (double)l0.y));
     }
-    const double2 r = refine_fp64<D, KK, QS>(xrow, a.center, nb, k, Lg, lo2, a.boost, a.adjust);
-    return make_float2((float)r.x, (float)r.y);
+    if (active) sink(row);
+    return l0;
+}
+
+// Steps 2-4 for one point whose landmark indices are in this thread's
+// column of shared memory (nb_at(nb, t) for rank t) and whose exact squared
+// distances are in sd (the fused and batched kernels).
+template <int D, int KK, int QS = kThreads, bool PF = false, class SINK>
+__device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uint32_t *nb,
+                                                const float4 *Lg, const float2 *lo2,
+                                                const FusedArgs &a, long long row, bool active,
+                                                const SINK &sink) {
+    const int m = a.k - 1;
+    float ss[KK];
+    point_scores<KK>(sd, a.k, a.boost, ss);
+    // 2-D coordinates relative to the nearest neighbour's.
+    const float2 l0 = lo2[nb_at<QS>(nb, 0)];
+    NormalSys S = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (a.adjust == 1.f)
+        pair_sums_regs<D, KK, true, QS, PF>(sd, ss, nb, m, Lg, lo2, l0, a, S);
+    else
+        pair_sums_regs<D, KK, false, QS, PF>(sd, ss, nb, m, Lg, lo2, l0, a, S);
+    return point_solve(S, l0, row, active, sink);
 }
 
 // ---------------------------------------------------------------------------
@@ -1145,8 +1008,8 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
 #pragma unroll
         for (int s = 0; s < KK; s += 2)
             nb[(s >> 1) * kThreads] = (uint32_t)si[s] | ((uint32_t)si[s + 1] << 16);
-        const float2 p = project_point<D, KK>(sd, nb, Lg, lo2, a,
-                                              a.X + (size_t)(active ? row0 + tid : row0) * D);
+        const float2 p = project_point<D, KK>(sd, nb, Lg, lo2, a, row0 + tid, active,
+                                              RefineSink{a.refine_list, a.refine_count});
         if (active) reinterpret_cast<float2 *>(a.out)[row0 + tid] = p;
     }
 }
@@ -1338,9 +1201,9 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchArgs B
 #pragma unroll
         for (int s2 = 0; s2 < KK; s2 += 2)
             nb[(s2 >> 1) * kThreads] = (uint32_t)si[s2] | ((uint32_t)si[s2 + 1] << 16);
-        const float2 p = project_point<D, KK>(sd, nb, Lg,
-                                              reinterpret_cast<const float2 *>(a.lo), a,
-                                              a.X + (size_t)(active ? row0 + tid : row0) * D);
+        const float2 p = project_point<D, KK>(
+            sd, nb, Lg, reinterpret_cast<const float2 *>(a.lo), a, row0 + tid, active,
+            BatchRefineSink{B.refine_list, B.refine_count, it});
         if (active) reinterpret_cast<float2 *>(a.out)[row0 + tid] = p;
     }
 }
@@ -1361,8 +1224,9 @@ __device__ __forceinline__ void project_tiles(const FusedArgs &a, const float4 *
     const long long ntiles = (a.n + kThreads - 1) / kThreads;
     const bool vec = (a.k & 3) == 0;  // rows of k entries are 16-byte aligned
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long row = tile * kThreads + tid;
-        const bool active = row < a.n;
+        const long long pos = tile * kThreads + tid;
+        const bool active = pos < a.n;
+        const long long row = active && a.perm ? (long long)__ldg(a.perm + pos) : pos;
         float sd[KK];
         int si[KK];
         if (vec) {
@@ -1395,9 +1259,8 @@ __device__ __forceinline__ void project_tiles(const FusedArgs &a, const float4 *
 #pragma unroll
         for (int t = 0; t < KK; t += 2)
             nb[(t >> 1) * kThreads] = (uint32_t)si[t] | ((uint32_t)si[t + 1] << 16);
-        const float *xrow = a.X + (size_t)(active ? row : 0) * D;
-        const float2 p = TAB ? project_point<D, KK, kThreads, true>(sd, nb, Lg, lo2, a, xrow)
-                             : project_point<D, KK>(sd, nb, Lg, lo2, a, xrow);
+        const float2 p = project_point<D, KK, kThreads, TAB>(
+            sd, nb, Lg, lo2, a, row, active, RefineSink{a.refine_list, a.refine_count});
         if (active) reinterpret_cast<float2 *>(a.out)[row] = p;
     }
 }
@@ -1454,6 +1317,111 @@ __global__ void __launch_bounds__(kThreads, MINB) project_kernel(const FusedArgs
 template <int D, int KC, int MINB>
 cudaError_t launch_project(const FusedArgs &a, int grid, size_t smem, cudaStream_t stream) {
     project_kernel<D, KC, MINB><<<grid, kThreads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Exact re-rank of the screened lists of the tensor-core k-NN kernel: one
+// thread per point (visited in the k-NN's order, a.perm, so that the
+// threads of a warp read nearby rows), its KC keys from a.cand, the FP32
+// difference-form distances of the listed landmarks from rows in shared
+// memory (copied once per block by bulk TMA when they fit, a.nchunks == 1;
+// else read from global memory), ordered by (distance, landmark index), and
+// the certificate with the screening bound M = m_dot |x| max|l| + the FP32
+// part (|x|^2 as the k-NN kernel summed it).  Certified lists go to a.idx /
+// a.dist2; the others to a.fail_list for rescan_kernel.
+
+template <int D, int KC, bool RES>
+__device__ __forceinline__ void rerank_tiles(const FusedArgs &a, const float4 *Lg, int tid) {
+    constexpr int KK = KC - 4;
+    constexpr float kGamma = (2.25f * D + 10.f) * kU * 1.25f;
+    const long long ntiles = (a.n + kThreads - 1) / kThreads;
+    const float lmax = *a.lmax;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long pos = tile * kThreads + tid;
+        const bool active = pos < a.n;
+        const long long row = !active ? 0 : (a.perm ? (long long)__ldg(a.perm + pos) : pos);
+        float4 xr[D / 4];
+        const float4 *xp = reinterpret_cast<const float4 *>(a.X) + row * (D / 4);
+        float xx = 0.f;
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) {
+            xr[e] = active ? centred(__ldg(xp + e), a.center, e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xx = fmaf(xr[e].x, xr[e].x, xx);
+            xx = fmaf(xr[e].y, xr[e].y, xx);
+            xx = fmaf(xr[e].z, xr[e].z, xx);
+            xx = fmaf(xr[e].w, xr[e].w, xx);
+        }
+        const float xn = sqrtf(xx);
+        const float sx = xn + lmax;
+        const float M = a.m_dot * xn * lmax + 2.f * kGamma * sx * sx;
+        float keys[KC];
+        const float4 *cp = reinterpret_cast<const float4 *>(a.cand + row * KC);
+#pragma unroll
+        for (int t = 0; t < KC; t += 4) {
+            const float4 v = active ? __ldg(cp + t / 4) : make_float4(INFINITY, INFINITY, INFINITY,
+                                                                     INFINITY);
+            keys[t] = v.x;
+            keys[t + 1] = v.y;
+            keys[t + 2] = v.z;
+            keys[t + 3] = v.w;
+        }
+        float sd[KK];
+        int si[KK];
+        const bool cert = rerank<D, KC, KK>(xr, keys, Lg, a.key_mask, a.L, a.k, M, a.key_quant, sd,
+                                            si, xx, a.lperm);
+        if (!active) continue;
+        if (__builtin_expect(!cert, 0)) {
+            // deferred: rescan_kernel finds this point's neighbours exactly
+            atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
+            a.fail_list[atomicAdd(a.fail_count, 1u)] = row;
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < KK; ++s2)
+            if (s2 < a.k) {
+                a.idx[row * a.k + s2] = si[s2];
+                if (a.dist2) a.dist2[row * a.k + s2] = sd[s2];
+            }
+    }
+}
+
+template <int D, int KC>
+__global__ void __launch_bounds__(kThreads) rerank_kernel(const FusedArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    float *sL = reinterpret_cast<float *>(smem + kBarrierBytes);
+    const int tid = threadIdx.x;
+    const long long ntiles = (a.n + kThreads - 1) / kThreads;
+    if ((long long)blockIdx.x >= ntiles) return;
+    if (a.nchunks == 1) {
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const uint32_t bytes = (uint32_t)((size_t)a.L * D * sizeof(float));
+            mbar_expect_tx(bar, bytes);
+            copy_pieces(sL, a.hi, bytes, bar);
+        }
+        const bool ok = mbar_wait(bar, 0);
+        if (!__syncthreads_and(ok)) {
+            // the copy did not land in time: report, drain it (bounded), leave
+            if (tid == 0) {
+                atomicOr(a.status, kErrWaitTimeout);
+                mbar_wait(bar, 0);
+            }
+            return;
+        }
+        rerank_tiles<D, KC, true>(a, reinterpret_cast<const float4 *>(sL), tid);
+    } else {
+        rerank_tiles<D, KC, false>(a, reinterpret_cast<const float4 *>(a.hi), tid);
+    }
+}
+
+template <int D, int KC>
+cudaError_t launch_rerank(const FusedArgs &a, int grid, size_t smem, cudaStream_t stream) {
+    rerank_kernel<D, KC><<<grid, kThreads, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -1585,6 +1553,413 @@ cudaError_t launch_rescan(const FusedArgs &a, int grid, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Steps 1-4 of one point again with FP64 arithmetic, all 32 lanes of a warp
+// sharing the work (the points whose FP32 normal system is ill-conditioned,
+// det/trace^2 <= kDetRefine: its terms' rounding, ~1e-7 relative, is
+// amplified by the condition number).  Called by every lane of the warp.
+//   1. the exact k nearest (FP32 difference form, ties to the lower index:
+//      the same neighbours as every k-NN path) by the warp scan of
+//      rescan_kernel; lane i keeps rank i;
+//   2. lane i: the squared distance of its neighbour in FP64 from the rows,
+//      the score of reading R2 (weights 1/i over the m = k - 1 scored
+//      neighbours, spread about the weighted mean, exp(boost (delta_1 -
+//      delta_i) / sigma) times the cut-off factor) by warp sums;
+//   3. the m (m - 1) / 2 pairs dealt to the lanes: D_uv = <X - L_u, L_v -
+//      L_u> / q as an FP64 dot product, the weight s_u s_v r^-adjust, the
+//      normal-system terms, summed over the warp;
+//   4. the solve of reading R5: Cramer's rule if det > 1e-10 trace^2, else
+//      the least-norm solution about the score-weighted centroid of the
+//      scored 2-D landmarks (the plain mean if every score is 0), or that
+//      centroid when A = 0.
+// GB300's FP64 rate is low, so all 32 lanes issue useful FP64 work.
+// Returns the coordinates on every lane.
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int D, int KK>
+__device__ __noinline__ float2 refine_warp_point(const float *X, long long row,
+                                                 const float *center, const float4 *Lg,
+                                                 const float2 *lo2, int L, int k, float boost,
+                                                 float adjust) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float4 x[D / 4];
+    const float4 *xp = reinterpret_cast<const float4 *>(X) + row * (D / 4);
+#pragma unroll
+    for (int e = 0; e < D / 4; ++e) x[e] = centred(__ldg(xp + e), center, e);
+    // 1. exact k nearest; lane r keeps rank r
+    unsigned long long best[KK];
+    rescan_scan<D, KK>(x, Lg, L, lane, 32, best);
+    int j = 0;
+    for (int r = 0; r < k; ++r) {
+        const unsigned long long m = warp_pop<KK>(best);
+        if (lane == r) j = (int)(unsigned)(m & 0xffffffffu);
+    }
+    // 2. distances and scores
+    const int m = k - 1;
+    const bool ranked = lane < k, scored = lane < m;
+    double d2 = 0.0;
+    if (ranked) {
+        const float4 *l = Lg + (size_t)j * (D / 4);
+        const int f = swz(D, j);
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) {
+            const float4 q = l[e ^ f];
+            const double t0 = (double)x[e].x - q.x, t1 = (double)x[e].y - q.y;
+            const double t2 = (double)x[e].z - q.z, t3 = (double)x[e].w - q.w;
+            d2 += t0 * t0 + t1 * t1 + t2 * t2 + t3 * t3;
+        }
+    }
+    const double del = sqrt(d2);
+    const double w = scored ? 1.0 / (double)(lane + 1) : 0.0;
+    const double wsum = warp_sum_d(w);
+    const double mean = warp_sum_d(w * del) / wsum;
+    const double sigma = sqrt(warp_sum_d(w * (del - mean) * (del - mean)) / wsum);
+    const double del0 = __shfl_sync(full, del, 0);
+    const double dk = __shfl_sync(full, del, k - 1);
+    const bool flat = sigma <= 1e-12 * fmax(mean, 1e-300);
+    double s = 0.0;
+    if (scored) {
+        const double f1 = flat ? 1.0 : exp((double)boost * (del0 - del) / sigma);
+        const double f2 = dk > 0.0 ? -expm1((double)kScoreEdge * (del / dk - 1.0)) : 1.0;
+        s = f1 * f2;
+    }
+    const float2 l0 = lo2[__shfl_sync(full, j, 0)];
+    const float2 lt = lo2[j];
+    const double px = (double)lt.x - (double)l0.x, py = (double)lt.y - (double)l0.y;
+    const double C0 = warp_sum_d(scored ? s * px : 0.0), C1 = warp_sum_d(scored ? s * py : 0.0);
+    const double Ssum = warp_sum_d(s);
+    const double M0 = warp_sum_d(scored ? px : 0.0), M1 = warp_sum_d(scored ? py : 0.0);
+    // 3. pairs u < v < m dealt to the lanes
+    double a00 = 0.0, a01 = 0.0, a11 = 0.0, b0 = 0.0, b1 = 0.0;
+    const int P = m * (m - 1) / 2;
+    for (int p0 = 0; p0 < P; p0 += 32) {
+        const int p = p0 + lane;
+        const bool valid = p < P;
+        int u = 0, rem = valid ? p : 0;
+        while (u < m - 1 && rem >= m - 1 - u) {
+            rem -= m - 1 - u;
+            ++u;
+        }
+        const int v = min(u + 1 + rem, 31);
+        const int ju = __shfl_sync(full, j, u), jv = __shfl_sync(full, j, v);
+        const double su = __shfl_sync(full, s, u), sv = __shfl_sync(full, s, v);
+        const double pxu = __shfl_sync(full, px, u), pyu = __shfl_sync(full, py, u);
+        const double pxv = __shfl_sync(full, px, v), pyv = __shfl_sync(full, py, v);
+        if (!valid) continue;
+        const float4 *Lu = Lg + (size_t)ju * (D / 4);
+        const float4 *Lv = Lg + (size_t)jv * (D / 4);
+        const int fu = swz(D, ju), fv = swz(D, jv);
+        double q = 0.0, g = 0.0;
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) {
+            const float4 cu = Lu[e ^ fu], cv = Lv[e ^ fv];
+            const double e0 = (double)cv.x - cu.x, e1 = (double)cv.y - cu.y;
+            const double e2 = (double)cv.z - cu.z, e3 = (double)cv.w - cu.w;
+            q += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3;
+            g += ((double)x[e].x - cu.x) * e0 + ((double)x[e].y - cu.y) * e1 +
+                 ((double)x[e].z - cu.z) * e2 + ((double)x[e].w - cu.w) * e3;
+        }
+        const double hx = pxv - pxu, hy = pyv - pyu;
+        const double r = hx * hx + hy * hy;
+        if (!(q > 0.0) || !(r > 0.0)) continue;
+        const double wp = su * sv / (adjust == 1.f ? r : pow(r, (double)adjust));
+        const double rhs = g / q + (hx * pxu + hy * pyu) / r;
+        a00 += wp * hx * hx / r;
+        a01 += wp * hx * hy / r;
+        a11 += wp * hy * hy / r;
+        b0 += wp * hx * rhs;
+        b1 += wp * hy * rhs;
+    }
+    a00 = warp_sum_d(a00);
+    a01 = warp_sum_d(a01);
+    a11 = warp_sum_d(a11);
+    b0 = warp_sum_d(b0);
+    b1 = warp_sum_d(b1);
+    // 4. solve
+    const double det = a00 * a11 - a01 * a01, tr = a00 + a11;
+    double rx, ry;
+    if (det > kDetEps * tr * tr) {
+        rx = (b0 * a11 - a01 * b1) / det;
+        ry = (a00 * b1 - a01 * b0) / det;
+    } else {
+        const double c0 = Ssum > 0.0 ? C0 / Ssum : M0 / (double)m;
+        const double c1 = Ssum > 0.0 ? C1 / Ssum : M1 / (double)m;
+        rx = c0;
+        ry = c1;
+        if (tr > 0.0) {
+            const double disc = sqrt((a00 - a11) * (a00 - a11) + 4.0 * a01 * a01);
+            const double lam = 0.5 * (tr + disc);
+            // major eigenvector: the better conditioned of two forms
+            const double va0 = a01, va1 = lam - a00, vb0 = lam - a11, vb1 = a01;
+            const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
+            double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
+            double nn = ga >= gb ? ga : gb;
+            if (nn == 0.0) {
+                v0 = 1.0;
+                v1 = 0.0;
+                nn = 1.0;
+            }
+            nn = sqrt(nn);
+            v0 /= nn;
+            v1 /= nn;
+            const double r0 = b0 - (a00 * c0 + a01 * c1);
+            const double r1 = b1 - (a01 * c0 + a11 * c1);
+            const double t = (v0 * r0 + v1 * r1) / lam;
+            rx = c0 + t * v0;
+            ry = c1 + t * v1;
+        }
+    }
+    return make_float2((float)(rx + (double)l0.x), (float)(ry + (double)l0.y));
+}
+
+// The same recomputation with the 256 threads of a block on one point, for
+// the refine kernels: each thread scans L/256 landmarks and the warps'
+// lists are merged by warp 0 (as rescan_kernel's block mode), warp 0 then
+// scores the neighbours (lane i = rank i), and the pairs are dealt to all
+// threads, so a point takes a few microseconds instead of one warp's long
+// chain of dependent loads and FP64 operations.  Every thread of the block
+// calls it; returns the coordinates on every thread.
+template <int D, int KK>
+__device__ __noinline__ float2 refine_block_point(const float *X, long long row,
+                                                  const float *center, const float4 *Lg,
+                                                  const float2 *lo2, int L, int k, float boost,
+                                                  float adjust) {
+    constexpr int kWarps = 256 / 32;
+    __shared__ unsigned long long s_top[kWarps][KK];
+    __shared__ int s_j[32];
+    __shared__ double s_s[32], s_px[32], s_py[32];
+    __shared__ double s_red[kWarps][5];
+    __shared__ double s_c[5];
+    __shared__ float2 s_out;
+    const unsigned full = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float4 x[D / 4];
+    const float4 *xp = reinterpret_cast<const float4 *>(X) + row * (D / 4);
+#pragma unroll
+    for (int e = 0; e < D / 4; ++e) x[e] = centred(__ldg(xp + e), center, e);
+    // 1. exact k nearest: every thread a slice, then the warps' lists merged
+    unsigned long long best[KK];
+    rescan_scan<D, KK>(x, Lg, L, tid, 256, best);
+    for (int r = 0; r < k; ++r) {
+        const unsigned long long m = warp_pop<KK>(best);
+        if (lane == 0) s_top[warp][r] = m;
+    }
+    __syncthreads();
+    const int m = k - 1;
+    if (warp == 0) {
+        int pos = 0, j = 0;
+        unsigned long long head = lane < kWarps ? s_top[lane][0] : ~0ull;
+        for (int r = 0; r < k; ++r) {
+            unsigned long long mm = head;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) mm = umin64(mm, __shfl_xor_sync(full, mm, off));
+            if (head == mm && lane < kWarps) {
+                ++pos;
+                head = pos < k ? s_top[lane][pos] : ~0ull;
+            }
+            if (lane == r) j = (int)(unsigned)(mm & 0xffffffffu);
+        }
+        // 2. distances and scores, lane i = rank i
+        const bool ranked = lane < k, scored = lane < m;
+        double d2 = 0.0;
+        if (ranked) {
+            const float4 *l = Lg + (size_t)j * (D / 4);
+            const int f = swz(D, j);
+#pragma unroll
+            for (int e = 0; e < D / 4; ++e) {
+                const float4 q = l[e ^ f];
+                const double t0 = (double)x[e].x - q.x, t1 = (double)x[e].y - q.y;
+                const double t2 = (double)x[e].z - q.z, t3 = (double)x[e].w - q.w;
+                d2 += t0 * t0 + t1 * t1 + t2 * t2 + t3 * t3;
+            }
+        }
+        const double del = sqrt(d2);
+        const double w = scored ? 1.0 / (double)(lane + 1) : 0.0;
+        const double wsum = warp_sum_d(w);
+        const double mean = warp_sum_d(w * del) / wsum;
+        const double sigma = sqrt(warp_sum_d(w * (del - mean) * (del - mean)) / wsum);
+        const double del0 = __shfl_sync(full, del, 0);
+        const double dk = __shfl_sync(full, del, k - 1);
+        const bool flat = sigma <= 1e-12 * fmax(mean, 1e-300);
+        double sc = 0.0;
+        if (scored) {
+            const double f1 = flat ? 1.0 : exp((double)boost * (del0 - del) / sigma);
+            const double f2 = dk > 0.0 ? -expm1((double)kScoreEdge * (del / dk - 1.0)) : 1.0;
+            sc = f1 * f2;
+        }
+        const float2 l0 = lo2[__shfl_sync(full, j, 0)];
+        const float2 lt = lo2[j];
+        const double px = (double)lt.x - (double)l0.x, py = (double)lt.y - (double)l0.y;
+        const double C0 = warp_sum_d(scored ? sc * px : 0.0);
+        const double C1 = warp_sum_d(scored ? sc * py : 0.0);
+        const double Ssum = warp_sum_d(sc);
+        const double M0 = warp_sum_d(scored ? px : 0.0), M1 = warp_sum_d(scored ? py : 0.0);
+        s_j[lane] = j;
+        s_s[lane] = sc;
+        s_px[lane] = px;
+        s_py[lane] = py;
+        if (lane == 0) {
+            s_c[0] = Ssum > 0.0 ? C0 / Ssum : M0 / (double)m;  // centroid (R5)
+            s_c[1] = Ssum > 0.0 ? C1 / Ssum : M1 / (double)m;
+            s_c[2] = l0.x;
+            s_c[3] = l0.y;
+        }
+    }
+    __syncthreads();
+    // 3. pairs u < v < m dealt to the threads
+    double a00 = 0.0, a01 = 0.0, a11 = 0.0, b0 = 0.0, b1 = 0.0;
+    const int P = m * (m - 1) / 2;
+    for (int p = tid; p < P; p += 256) {
+        int u = 0, rem = p;
+        while (rem >= m - 1 - u) {
+            rem -= m - 1 - u;
+            ++u;
+        }
+        const int v = u + 1 + rem;
+        const int ju = s_j[u], jv = s_j[v];
+        const float4 *Lu = Lg + (size_t)ju * (D / 4);
+        const float4 *Lv = Lg + (size_t)jv * (D / 4);
+        const int fu = swz(D, ju), fv = swz(D, jv);
+        double q = 0.0, g = 0.0;
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) {
+            const float4 cu = Lu[e ^ fu], cv = Lv[e ^ fv];
+            const double e0 = (double)cv.x - cu.x, e1 = (double)cv.y - cu.y;
+            const double e2 = (double)cv.z - cu.z, e3 = (double)cv.w - cu.w;
+            q += e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3;
+            g += ((double)x[e].x - cu.x) * e0 + ((double)x[e].y - cu.y) * e1 +
+                 ((double)x[e].z - cu.z) * e2 + ((double)x[e].w - cu.w) * e3;
+        }
+        const double pxu = s_px[u], pyu = s_py[u];
+        const double hx = s_px[v] - pxu, hy = s_py[v] - pyu;
+        const double r = hx * hx + hy * hy;
+        if (!(q > 0.0) || !(r > 0.0)) continue;
+        const double wp = s_s[u] * s_s[v] / (adjust == 1.f ? r : pow(r, (double)adjust));
+        const double rhs = g / q + (hx * pxu + hy * pyu) / r;
+        a00 += wp * hx * hx / r;
+        a01 += wp * hx * hy / r;
+        a11 += wp * hy * hy / r;
+        b0 += wp * hx * rhs;
+        b1 += wp * hy * rhs;
+    }
+    a00 = warp_sum_d(a00);
+    a01 = warp_sum_d(a01);
+    a11 = warp_sum_d(a11);
+    b0 = warp_sum_d(b0);
+    b1 = warp_sum_d(b1);
+    if (lane == 0) {
+        s_red[warp][0] = a00;
+        s_red[warp][1] = a01;
+        s_red[warp][2] = a11;
+        s_red[warp][3] = b0;
+        s_red[warp][4] = b1;
+    }
+    __syncthreads();
+    // 4. solve (reading R5)
+    if (tid == 0) {
+        double A00 = 0.0, A01 = 0.0, A11 = 0.0, B0 = 0.0, B1 = 0.0;
+        for (int w = 0; w < kWarps; ++w) {
+            A00 += s_red[w][0];
+            A01 += s_red[w][1];
+            A11 += s_red[w][2];
+            B0 += s_red[w][3];
+            B1 += s_red[w][4];
+        }
+        const double det = A00 * A11 - A01 * A01, tr = A00 + A11;
+        double rx, ry;
+        if (det > kDetEps * tr * tr) {
+            rx = (B0 * A11 - A01 * B1) / det;
+            ry = (A00 * B1 - A01 * B0) / det;
+        } else {
+            const double c0 = s_c[0], c1 = s_c[1];
+            rx = c0;
+            ry = c1;
+            if (tr > 0.0) {
+                const double disc = sqrt((A00 - A11) * (A00 - A11) + 4.0 * A01 * A01);
+                const double lam = 0.5 * (tr + disc);
+                const double va0 = A01, va1 = lam - A00, vb0 = lam - A11, vb1 = A01;
+                const double ga = va0 * va0 + va1 * va1, gb = vb0 * vb0 + vb1 * vb1;
+                double v0 = ga >= gb ? va0 : vb0, v1 = ga >= gb ? va1 : vb1;
+                double nn = ga >= gb ? ga : gb;
+                if (nn == 0.0) {
+                    v0 = 1.0;
+                    v1 = 0.0;
+                    nn = 1.0;
+                }
+                nn = sqrt(nn);
+                v0 /= nn;
+                v1 /= nn;
+                const double r0 = B0 - (A00 * c0 + A01 * c1);
+                const double r1 = B1 - (A01 * c0 + A11 * c1);
+                const double t = (v0 * r0 + v1 * r1) / lam;
+                rx = c0 + t * v0;
+                ry = c1 + t * v1;
+            }
+        }
+        s_out = make_float2((float)(rx + s_c[2]), (float)(ry + s_c[3]));
+    }
+    __syncthreads();
+    const float2 res = s_out;
+    __syncthreads();  // s_out and the other arrays may be reused by the next point
+    return res;
+}
+
+// One block per row of a.refine_list (count *a.refine_count): the FP64
+// recomputation of the point, written to a.out.
+template <int D, int KC>
+__global__ void __launch_bounds__(256) refine_kernel(const FusedArgs a) {
+    constexpr int KK = KC - 4;
+    const unsigned count = *reinterpret_cast<volatile const unsigned *>(a.refine_count);
+    for (long long w = blockIdx.x; w < (long long)count; w += gridDim.x) {
+        const long long row = a.refine_list[w];
+        const float2 p = refine_block_point<D, KK>(a.X, row, a.center,
+                                                   reinterpret_cast<const float4 *>(a.hi),
+                                                   reinterpret_cast<const float2 *>(a.lo), a.L,
+                                                   a.k, a.boost, a.adjust);
+        if (threadIdx.x == 0) {
+            reinterpret_cast<float2 *>(a.out)[row] = p;
+            atomicAdd(reinterpret_cast<unsigned *>(a.status) + 5, 1u);  // stats: refines
+        }
+    }
+}
+
+// The same for the batched kernel: entries (dataset, row).
+template <int D, int KC>
+__global__ void __launch_bounds__(256) refine_batch_kernel(const BatchArgs B) {
+    constexpr int KK = KC - 4;
+    const unsigned count = *reinterpret_cast<volatile const unsigned *>(B.refine_count);
+    for (long long w = blockIdx.x; w < (long long)count; w += gridDim.x) {
+        const int2 e = B.refine_list[w];
+        const FusedArgs &a = B.items[e.x];
+        const float2 p = refine_block_point<D, KK>(a.X, e.y, a.center,
+                                                   reinterpret_cast<const float4 *>(a.hi),
+                                                   reinterpret_cast<const float2 *>(a.lo), a.L,
+                                                   a.k, a.boost, a.adjust);
+        if (threadIdx.x == 0) {
+            reinterpret_cast<float2 *>(a.out)[e.y] = p;
+            atomicAdd(reinterpret_cast<unsigned *>(B.status) + 5, 1u);  // stats: refines
+        }
+    }
+}
+
+template <int D, int KC>
+cudaError_t launch_refine(const FusedArgs &a, int grid, cudaStream_t stream) {
+    refine_kernel<D, KC><<<grid, 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D, int KC>
+cudaError_t launch_refine_batch(const BatchArgs &b, int grid, cudaStream_t stream) {
+    refine_batch_kernel<D, KC><<<grid, 256, 0, stream>>>(b);
+    return cudaGetLastError();
+}
+
 // One thread per ordered pair (u, v): the squared distance table of the pair
 // loop, computed by the loop's own pair_q.
 template <int D>
@@ -1636,7 +2011,9 @@ const KernelOps Instance<D, KC>::ops = {
     reinterpret_cast<const void *>(&batch_kernel<D, KC, Instance<D, KC>::kMinBlocks>),
     &launch_batch<D, KC, Instance<D, KC>::kMinBlocks>, &launch_qtab<D>,
     reinterpret_cast<const void *>(&project_kernel<D, KC, Instance<D, KC>::kMinBlocks>),
-    &launch_project<D, KC, Instance<D, KC>::kMinBlocks>, &launch_rescan<D, KC>};
+    &launch_project<D, KC, Instance<D, KC>::kMinBlocks>, &launch_rescan<D, KC>,
+    reinterpret_cast<const void *>(&rerank_kernel<D, KC>), &launch_rerank<D, KC>,
+    &launch_refine<D, KC>, &launch_refine_batch<D, KC>};
 
 // Table of the list capacities instantiated for each D.
 #define ESOM_DEFINE_D(DV)                                            \

@@ -52,6 +52,24 @@ struct FusedArgs {
     // block first waits on a barrier that nothing completes and gives up
     // after this many ns (see esom_test_stall)
     unsigned long long stall_ns;
+    // tensor-core k-NN with spatial orders (all null: natural order): the
+    // visiting order of the points, each tile's home chunk, the chunks'
+    // visiting orders, and the landmark of each internal screening position
+    // (a.norms then holds the norms in the internal order)
+    const int *perm;
+    const unsigned short *tile_home;
+    const unsigned short *corder;
+    const int *lperm;
+    // tensor-core k-NN: the screened list of each point (KC keys, ascending,
+    // at row * KC), re-ranked exactly by rerank_kernel; m_dot = the
+    // tensor-core part of the screening error per unit |x| max|l|
+    // (tc_dot_bound)
+    float *cand;
+    float m_dot;
+    // projection: rows whose FP32 normal system is too ill-conditioned are
+    // appended here (count in *refine_count) for refine_kernel
+    long long *refine_list;
+    unsigned *refine_count;
 };
 
 // x - c, four at a time (c may be null: no centring).
@@ -71,6 +89,8 @@ struct BatchArgs {
     const int *tile_item;       // dataset of each global tile
     const long long *cta_begin; // grid + 1 range boundaries
     int *status;                // error bits, as for a single launch
+    int2 *refine_list;          // (dataset, row) of ill-conditioned points
+    unsigned *refine_count;
 };
 
 struct KernelOps {
@@ -91,7 +111,22 @@ struct KernelOps {
     // Exact k-NN of the rows in a.fail_list (one warp per row), written to
     // a.idx / a.dist2 like the k-NN kernels do.
     cudaError_t (*launch_rescan)(const FusedArgs &, int grid, cudaStream_t);
+    // Exact re-rank of the tensor-core k-NN's screened lists (a.cand):
+    // FP32 difference-form distances (rows in shared memory when
+    // a.nchunks == 1, rerank_smem_bytes), order by (distance, landmark), the
+    // certificate; writes a.idx / a.dist2, failed rows to a.fail_list.
+    const void *rerank_func;
+    cudaError_t (*launch_rerank)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
+    // FP64 recomputation, one block a point, of the rows in a.refine_list
+    // (B.refine_list for the batched kernel), written to the outputs.
+    cudaError_t (*launch_refine)(const FusedArgs &, int grid, cudaStream_t);
+    cudaError_t (*launch_refine_batch)(const BatchArgs &, int grid, cudaStream_t);
 };
+
+
+inline size_t rerank_smem_bytes(int D, int L, bool resident) {
+    return kBarrierBytes + (resident ? (size_t)L * D * sizeof(float) : 0);
+}
 
 // Returns the instantiation for dimension D and list capacity kc, or nullptr.
 const KernelOps *kernel_ops(int D, int kc);
@@ -141,6 +176,20 @@ __host__ __device__ constexpr int tc_minb(int D, int KC) { return D <= 16 ? (KC 
 __host__ __device__ constexpr int tc_queue(int D, int KC) { return tc_minb(D, KC) >= 4 ? 24 : 48; }
 __host__ __device__ constexpr int tc_check(int D, int KC) { return tc_minb(D, KC) >= 4 ? 16 : 32; }
 
+// Bound on the tensor-core part of the screening error per unit |X| max|L|.
+// With x_hi the rounding of x to p significant bits (p = 11 for TF32, 8 for
+// BF16) and x_lo that of x - x_hi: |x - x_hi| <= 2^-p |x| and
+// |x - x_hi - x_lo| <= 2^-2p |x|, so the dropped terms x_lo l_lo and the two
+// remainders are <= 3 2^-2p |x_i||l_i| per coordinate; the 3D products are
+// exact in FP32 and accumulated with at most 3D + 1 roundings (2^-23 each,
+// relative to the sum of |products| <= |x||l|).  Twice that in
+// v_j = |L_j|^2 - 2 T_j, and a factor 2 of margin.  (Measured on the GPU:
+// at most 0.103 of this bound, on rows spanning 2^-10 .. 2^10.)
+__host__ __device__ constexpr float tc_dot_bound(int D, int prec) {
+    return 4.f * (3.f * (prec == kTcBf16 ? 1.5258789e-5f : 2.3841858e-7f) +
+                  (float)(3 * D + 1) * 1.1920929e-7f);
+}
+
 // Bytes of one chunk image: the high parts of kTcN rows, then the low
 // parts, in the swizzled K-major order the MMA reads (see tc_image_offset).
 __host__ __device__ inline size_t tc_chunk_bytes(int D, int prec = kTcTf32) {
@@ -166,6 +215,24 @@ inline size_t tc_smem_bytes(int D, int KC, int prec = kTcTf32) {
            + (size_t)tc_queue(D, KC) * kTcRows * 4  // candidate queue
            + 256;                                // barriers, TMEM address, flags
 }
+
+// Spatial orders of the tensor-core screening (esom_order.cu), used when
+// L <= kOrderMaxL: the landmark order lperm (internal position -> landmark,
+// chunks of kTcN along principal directions), the chunk centroids (nch x D),
+// the squared norms in the internal order (NaN padding) and each chunk's
+// visiting order (corder[c * nch + r], the chunks by centroid distance).
+constexpr int kOrderMaxL = 8192;
+cudaError_t launch_landmark_order(const float *hi, const float *norms, int L, int D, int *lperm,
+                                  float *centers, float *norms_int, unsigned short *corder,
+                                  cudaStream_t stream);
+// The points of one pass grouped by home chunk (nearest centroid):
+// perm[pos] = point at visiting position pos, tile_home[t] = home chunk of
+// position kTcRows t; home (n) and counts (nblocks * nch) are scratch.
+constexpr int kOrderBlocks = 304;
+cudaError_t launch_point_order(const float *X, long long n, int D, const float *centers, int nch,
+                               const float *center, unsigned short *home, int *counts,
+                               int nblocks, int *perm, unsigned short *tile_home,
+                               cudaStream_t stream);
 
 // Points per tensor-core k-NN pass of esom_project: the pass writes their
 // neighbours (k indices and squared distances each) to the handle's scratch,
@@ -196,9 +263,10 @@ const TcOps *tc_dump_ops(int D, int prec);
 
 // Builds the split chunk images of the landmarks (precision prec) from the
 // (chunk-swizzled) rows of hi: ceil(L / kTcN) images of tc_chunk_bytes(D,
-// prec), rows beyond L zero.
+// prec), rows beyond L zero; with lperm, internal position j holds landmark
+// lperm[j].
 cudaError_t launch_tc_image(const float *hi, int L, int D, unsigned char *img, int prec,
-                            cudaStream_t stream);
+                            cudaStream_t stream, const int *lperm = nullptr);
 
 // rcp[i] = the FP64 reciprocal the 2x2 solve uses (drcp), div[i] = 1.0 / x[i]
 // by CUDA's division, for i < n (device pointers).

@@ -21,7 +21,11 @@
 namespace {
 
 constexpr size_t kScratchFloats = ESOM_NOALLOC_SCRATCH_BYTES / sizeof(float);
-constexpr size_t kStatusFloats = 64;  // first 256 bytes: the status word
+constexpr size_t kStatusFloats = 64;  // first 256 bytes: the status words
+// rows the scratch must keep for the list of ill-conditioned points of one
+// pass (recomputed in FP64 after the pass); the rest of the scratch raises
+// the pass size up to a handle's
+constexpr size_t kMinRefineRows = 8192;
 constexpr int kMaxDevices = 64;
 
 }  // namespace
@@ -64,10 +68,10 @@ extern "C" esom_status esom_project_noalloc(const float *points, int64_t n, cons
     if (k > ESOM_MAX_K) return noalloc_fail(ESOM_EUNSUPPORTED, "k above ESOM_MAX_K (32)");
     if (L > ESOM_MAX_L ||
         (size_t)L * (size_t)d + (size_t)((2 * L + 3) & ~3) + (size_t)((L + 3) & ~3) +
-                kStatusFloats > kScratchFloats)
+                kStatusFloats + 2 * kMinRefineRows > kScratchFloats)
         return noalloc_fail(ESOM_EINVAL,
                             "landmarks exceed the no-alloc scratch: need (L*(d+2) + L rounded up "
-                            "to 4)*4 + 256 bytes <= ESOM_NOALLOC_SCRATCH_BYTES");
+                            "to 4)*4 + 256 + 65536 bytes <= ESOM_NOALLOC_SCRATCH_BYTES");
     if (n < 0) return noalloc_fail(ESOM_EINVAL, "n < 0");
     if (!hi || !lo) return noalloc_fail(ESOM_EINVAL, "null landmark pointer");
     if (n > 0 && (!points || !out)) return noalloc_fail(ESOM_EINVAL, "null points or out");
@@ -103,14 +107,20 @@ extern "C" esom_status esom_project_noalloc(const float *points, int64_t n, cons
     if (e != cudaSuccess) return noalloc_fail(ESOM_ECUDA, cudaGetErrorString(e));
     if (bps < 1) return noalloc_fail(ESOM_EUNSUPPORTED, "launch does not fit on an SM");
 
-    // Scratch layout (every part 16-byte aligned): [status word, largest
-    // norm | landmarks L x d | 2-D landmarks L x 2 | squared norms, L rounded
-    // up to 4].
+    // Scratch layout (every part 16-byte aligned): [status words: error
+    // bits, largest norm, rescans, -, refine-list length | landmarks L x d |
+    // 2-D landmarks L x 2 | squared norms, L rounded up to 4 | refine list,
+    // the rest].
     int *status = reinterpret_cast<int *>(scratch);
     float *s_lmax = scratch + 1;
     float *s_hi = scratch + kStatusFloats;
     float *s_lo = s_hi + (size_t)L * d;
     float *s_norms = s_lo + (size_t)((2 * L + 3) & ~3);  // 16-byte aligned for the bulk copy
+    float *s_list = s_norms + (size_t)((L + 3) & ~3);
+    long long *refine_list = reinterpret_cast<long long *>(s_list);
+    unsigned *refine_count = reinterpret_cast<unsigned *>(status) + 4;
+    long long pass = (long long)((kScratchFloats - (size_t)(s_list - scratch)) / 2);
+    if (pass > esom::kTcPass) pass = esom::kTcPass;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     e = cudaMemsetAsync(status, 0, 2 * sizeof(int), st);  // status and max norm start at zero
     if (e == cudaSuccess)
@@ -133,15 +143,25 @@ extern "C" esom_status esom_project_noalloc(const float *points, int64_t n, cons
     a.k = k;
     a.boost = boost;
     a.adjust = adjust;
-    a.out = out;
     a.mode = esom::kProject;
     a.chunk = chunk;
     a.nchunks = nchunks;
-    a.ntiles = (n + esom::kThreads - 1) / esom::kThreads;
     a.status = status;
-    long long grid = (long long)bps * sms;
-    if (grid > a.ntiles) grid = a.ntiles;
-    e = ops->launch(a, (int)grid, smem, st);
+    a.refine_list = refine_list;
+    a.refine_count = refine_count;
+    // passes that the refine list can hold, each followed by the FP64
+    // recomputation of the points it listed
+    for (long long off = 0; off < n && e == cudaSuccess; off += pass) {
+        a.n = n - off < pass ? n - off : pass;
+        a.X = points + off * d;
+        a.out = out + off * 2;
+        a.ntiles = (a.n + esom::kThreads - 1) / esom::kThreads;
+        long long grid = (long long)bps * sms;
+        if (grid > a.ntiles) grid = a.ntiles;
+        e = cudaMemsetAsync(refine_count, 0, sizeof(unsigned), st);
+        if (e == cudaSuccess) e = ops->launch(a, (int)grid, smem, st);
+        if (e == cudaSuccess) e = ops->launch_refine(a, 2 * sms, st);
+    }
     if (e != cudaSuccess) return noalloc_fail(ESOM_ECUDA, cudaGetErrorString(e));
     return ESOM_OK;
 }

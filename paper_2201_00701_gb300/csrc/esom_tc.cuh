@@ -186,20 +186,6 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
-// Bound on the tensor-core part of the screening error per unit |X| max|L|.
-// With x_hi the rounding of x to p significant bits (p = 11 for TF32, 8 for
-// BF16) and x_lo that of x - x_hi: |x - x_hi| <= 2^-p |x| and
-// |x - x_hi - x_lo| <= 2^-2p |x|, so the dropped terms x_lo l_lo and the two
-// remainders are <= 3 2^-2p |x_i||l_i| per coordinate; the 3D products are
-// exact in FP32 and accumulated with at most 3D + 1 roundings (2^-23 each,
-// relative to the sum of |products| <= |x||l|).  Twice that in
-// v_j = |L_j|^2 - 2 T_j, and a factor 2 of margin.
-template <int D, int PREC>
-__device__ __forceinline__ float tc_dot_bound() {
-    constexpr float kSplit = PREC == kTcBf16 ? 1.5258789e-5f : 2.3841858e-7f;  // 2^-2p
-    return 4.f * (3.f * kSplit + (float)(3 * D + 1) * 1.1920929e-7f);
-}
-
 // ---------------------------------------------------------------------------
 
 // DUMP (tests of the error bound only): instead of selecting, every
@@ -209,7 +195,6 @@ template <int D, int KC, int PREC, bool DUMP = false>
 __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const FusedArgs a) {
     static_assert(D % 4 == 0 && D >= 4 && D <= 64, "D must be a multiple of 4 in [4, 64]");
     static_assert(KC >= 8 && KC <= 36 && KC % 4 == 0, "list capacity out of range");
-    constexpr int KK = KC - 4;
     constexpr int EB = tc_elem_bytes(PREC);      // bytes of an operand element
     constexpr int RB = tc_row_bytes(D, PREC);    // bytes of a row per column block
     constexpr int NB = tc_nblk(D, PREC);
@@ -275,6 +260,13 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         *s_abort = 1;
         atomicOr(a.status, kErrWaitTimeout);
     };
+    // The landmark chunk a tile visits at step r: in the order of chunk
+    // distance from the tile's home chunk when the points are grouped by
+    // home, else chunk r.
+    auto chunk_of = [&](long long tile, int r) -> int {
+        if (!a.corder) return r;
+        return (int)__ldg(a.corder + (size_t)__ldg(a.tile_home + tile) * nch + r);
+    };
 
     if (warp == 4) {
         // ------------------------------------------------------------------
@@ -284,7 +276,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
             long long issued = 0, landed = 0;
             auto issue = [&](long long g) {
                 const int s = (int)(g % S);
-                const int c = (int)(g % nch);
+                const int c = chunk_of(first + (g / nch) * gridDim.x, (int)(g % nch));
                 mbar_expect_tx(&l_full[s], kBBytes);
                 bulk_g2s(sB + (size_t)s * kBBytes, a.img + (size_t)c * kBBytes, kBBytes,
                          &l_full[s]);
@@ -351,7 +343,6 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         const uint32_t mask = a.key_mask;
         const float q = a.key_quant;
         const float lmax = *a.lmax;
-        const float4 *Lg = reinterpret_cast<const float4 *>(a.hi);
         const uint32_t my_lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         constexpr float kGamma = (2.25f * D + 10.f) * kU * 1.25f;
 
@@ -359,8 +350,9 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         // parts (TF32 or BF16, swizzled), into the point buffer and returns
         // |x|^2 (FP32, exact row).
         auto write_tile = [&](long long tile) -> float {
-            const long long row = tile * kTcRows + tid;
-            const bool act = row < a.n;
+            const long long pos = tile * kTcRows + tid;
+            const bool act = pos < a.n;
+            const long long row = act && a.perm ? (long long)__ldg(a.perm + pos) : pos;
             const float4 *xp = reinterpret_cast<const float4 *>(a.X) + (act ? row : 0) * (D / 4);
             float xx = 0.f;
 #pragma unroll
@@ -416,25 +408,45 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         // threshold test and a predicated push.  Padding columns (beyond L) have NaN
         // norms, so they never pass.  Every QI values the queue is flushed
         // when a lane may not have room for QI more.
-        auto push32 = [&](const float (&v)[32], int jbase, float (&keys)[KC], ScanState &st,
+        auto push32 = [&](float (&v)[32], int jbase, float (&keys)[KC], ScanState &st,
                           float M) {
             const float4 *N4 = reinterpret_cast<const float4 *>(a.norms + jbase);
+            // screening values two at a time on the packed FP32x2 pipe (each
+            // lane the same fma as fmaf(-2, v, |l|^2))
+#pragma unroll
+            for (int jb = 0; jb < 32; jb += 4) {
+                const float4 n4 = __ldg(N4 + jb / 4);
+                const float2 s01 = __ffma2_rn(make_float2(v[jb], v[jb + 1]),
+                                              make_float2(-2.f, -2.f), make_float2(n4.x, n4.y));
+                const float2 s23 = __ffma2_rn(make_float2(v[jb + 2], v[jb + 3]),
+                                              make_float2(-2.f, -2.f), make_float2(n4.z, n4.w));
+                v[jb] = s01.x;
+                v[jb + 1] = s01.y;
+                v[jb + 2] = s23.x;
+                v[jb + 3] = s23.y;
+            }
+            if (a.perm) {
+                // points grouped by home: skip the 32 values when no lane of
+                // the warp has one below its threshold.  A key differs from
+                // its value v by at most q|v|, and v - q|v| grows with v, so
+                // no key of the group is below the threshold either.
+                float m4[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    m4[r] = fminf(fminf(fminf(v[r], v[r + 4]), fminf(v[r + 8], v[r + 12])),
+                                  fminf(fminf(v[r + 16], v[r + 20]), fminf(v[r + 24], v[r + 28])));
+                const float vmin = fminf(fminf(m4[0], m4[1]), fminf(m4[2], m4[3]));
+                if (!__any_sync(0xffffffffu, vmin - q * fabsf(vmin) < st.thr)) return;
+            }
 #pragma unroll
             for (int hb = 0; hb < 32; hb += 16) {
                 uint32_t *qp = qk + st.qn * QS + tid;
 #pragma unroll
                 for (int jb = 0; jb < 16; jb += 4) {
-                    // screening values two at a time on the packed FP32x2
-                    // pipe (each lane the same fma as fmaf(-2, v, |l|^2))
-                    const float4 n4 = __ldg(N4 + (hb + jb) / 4);
-                    const float2 s01 = __ffma2_rn(make_float2(v[hb + jb], v[hb + jb + 1]),
-                                                  make_float2(-2.f, -2.f), make_float2(n4.x, n4.y));
-                    const float2 s23 = __ffma2_rn(make_float2(v[hb + jb + 2], v[hb + jb + 3]),
-                                                  make_float2(-2.f, -2.f), make_float2(n4.z, n4.w));
-                    const float sv[4] = {s01.x, s01.y, s23.x, s23.y};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const float key = make_key(sv[e], (uint32_t)(jbase + hb + jb + e), mask);
+                        const float key = make_key(v[hb + jb + e], (uint32_t)(jbase + hb + jb + e),
+                                                   mask);
                         if (key < st.thr) {
                             *qp = __float_as_uint(key);
                             qp += QS;
@@ -454,13 +466,14 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
         long long g = 0;
         long long tile = first;
         for (long long i = 0; i < my_tiles && ok; ++i, tile += gridDim.x) {
-            const long long row = tile * kTcRows + tid;
-            const bool active = row < a.n;
+            const long long pos = tile * kTcRows + tid;
+            const bool active = pos < a.n;
+            const long long row = active && a.perm ? (long long)__ldg(a.perm + pos) : pos;
             const float xx = xx_next;
             const float xn = sqrtf(xx);
             const float sx = xn + lmax;
             // |v_j - (exact FP32 distance - |x|^2)| <= M
-            const float M = tc_dot_bound<D, PREC>() * xn * lmax + 2.f * kGamma * sx * sx;
+            const float M = a.m_dot * xn * lmax + 2.f * kGamma * sx * sx;
 
             float keys[KC];
             ScanState st;
@@ -475,7 +488,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                     break;
                 }
                 tc_fence_after();
-                const int base = c * kTcN;
+                const int base = chunk_of(tile, c) * kTcN;  // first internal index
                 const uint32_t col = my_lane_addr + (uint32_t)(tb * kTcN);
 #pragma unroll 1
                 for (int h = 0; h < 2; ++h) {
@@ -488,13 +501,15 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                         if (lane == 0) mbar_arrive(&t_empty[tb]);
                     }
                     if (DUMP) {
+                        // at the landmark's own column (internal position
+                        // j' holds landmark lperm[j'])
                         if (active) {
-                            float4 *o = reinterpret_cast<float4 *>(
-                                a.dist2 + row * (long long)(nch * kTcN) + base + 32 * h);
+                            float *o = a.dist2 + row * (long long)(nch * kTcN);
 #pragma unroll
-                            for (int t = 0; t < 8; ++t)
-                                o[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2],
-                                                   v[4 * t + 3]);
+                            for (int t = 0; t < 32; ++t) {
+                                const int jp = base + 32 * h + t;
+                                o[a.lperm && jp < a.L ? __ldg(a.lperm + jp) : jp] = v[t];
+                            }
                         }
                     } else if (c == 0 && h == 0) {
                         // The first KF values go straight into the list (one
@@ -502,12 +517,12 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                         // beyond KC are dropped, which the certificate covers
                         // like any key pushed out.  The rest of the half is
                         // pushed.
-                        const int cnt = a.L < kTcN ? a.L : kTcN;
+                        const int cnt = a.L - base < kTcN ? a.L - base : kTcN;
                         float kv[KF];
 #pragma unroll
                         for (int t = 0; t < KF; ++t)
-                            kv[t] = t < cnt ? make_key(fmaf(-2.f, v[t], __ldg(a.norms + t)),
-                                                       (uint32_t)t, mask)
+                            kv[t] = t < cnt ? make_key(fmaf(-2.f, v[t], __ldg(a.norms + base + t)),
+                                                       (uint32_t)(base + t), mask)
                                             : INFINITY;
                         key_sort<KF>(kv);
 #pragma unroll
@@ -515,8 +530,8 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                         st.thr = push_threshold(at<KC>(keys, a.k - 1), M, q);
 #pragma unroll
                         for (int t = KF; t < 32; ++t) {
-                            const float key = make_key(fmaf(-2.f, v[t], __ldg(a.norms + t)),
-                                                       (uint32_t)t, mask);
+                            const float key = make_key(fmaf(-2.f, v[t], __ldg(a.norms + base + t)),
+                                                       (uint32_t)(base + t), mask);
                             if (key < st.thr) {
                                 qk[st.qn * QS + tid] = __float_as_uint(key);
                                 ++st.qn;
@@ -536,28 +551,15 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
             if (DUMP) continue;
             queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
 
-            // Step 1b: exact re-rank of the list, certificate, rare rescan.
-            float4 xr[D / 4];
-            const float4 *xp = reinterpret_cast<const float4 *>(a.X) + (active ? row : 0) * (D / 4);
-#pragma unroll
-            for (int e = 0; e < D / 4; ++e)
-                xr[e] = active ? centred(__ldg(xp + e), a.center, e)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-            float sd[KK];
-            int si[KK];
-            const bool cert = rerank<D, KC, KK>(xr, keys, Lg, mask, a.L, a.k, M, q, sd, si, xx);
-            if (__builtin_expect(!cert, 0) && active) {
-                // deferred: rescan_kernel finds this point's neighbours exactly
-                atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
-                a.fail_list[atomicAdd(a.fail_count, 1u)] = row;
-            }
+            // The screened list goes to the candidate buffer; rerank_kernel
+            // computes its exact distances from rows in shared memory (an
+            // in-kernel re-rank gathering the rows from L2 took 37% of this
+            // kernel's time).
             if (active) {
+                float4 *cp = reinterpret_cast<float4 *>(a.cand + row * KC);
 #pragma unroll
-                for (int s2 = 0; s2 < KK; ++s2)
-                    if (s2 < a.k) {
-                        a.idx[row * a.k + s2] = si[s2];
-                        if (a.dist2) a.dist2[row * a.k + s2] = sd[s2];
-                    }
+                for (int t = 0; t < KC; t += 4)
+                    cp[t / 4] = make_float4(keys[t], keys[t + 1], keys[t + 2], keys[t + 3]);
             }
         }
         if (!ok) raise_abort();

@@ -193,7 +193,7 @@ __device__ __forceinline__ void add_pair(PairAcc &s, float p, float q, float2 lu
 
 template <int D>
 __global__ void __launch_bounds__(kVarThreads) project_registers_kernel(const FusedArgs a) {
-    __shared__ float s_sd[kVarWarps][kVarMaxK], s_ss[kVarWarps][kVarMaxK];
+    __shared__ float s_ss[kVarWarps][kVarMaxK];
     __shared__ int s_ix[kVarWarps][kVarMaxK];
     __shared__ uint32_t s_nb[kVarWarps][kVarMaxK / 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -230,7 +230,6 @@ __global__ void __launch_bounds__(kVarThreads) project_registers_kernel(const Fu
         const float f2 = dk > 0.f ? -expm1f(z) : 1.f;
         st = f1 * f2;
     }
-    s_sd[warp][lane] = dt;
     s_ss[warp][lane] = st;
     s_ix[warp][lane] = it;
     const int inext = __shfl_down_sync(full, it, 1);
@@ -295,23 +294,20 @@ __global__ void __launch_bounds__(kVarThreads) project_registers_kernel(const Fu
     const float A00 = warp_sum(acc.a00), A01 = warp_sum(acc.a01), A11 = warp_sum(acc.a11);
     const float B0 = warp_sum(acc.b0), B1 = warp_sum(acc.b1);
 
-    // Step 4: FP64 solve on lane 0, with the library's near-singular path
-    if (lane == 0) {
-        const double a00 = A00, a01 = A01, a11 = A11, b0 = B0, b1 = B1;
-        const double det = a00 * a11 - a01 * a01;
-        const double tr = a00 + a11;
-        double rx, ry;
-        if (det > kDetRefine * tr * tr) {
-            rx = (b0 * a11 - a01 * b1) / det + (double)l0.x;
-            ry = (a00 * b1 - a01 * b0) / det + (double)l0.y;
-        } else {
-            const double2 r = refine_fp64<D, kVarMaxK, 1>(a.X + (size_t)row * D, a.center,
-                                                          s_nb[warp], a.k, Lg, lo2, a.boost,
-                                                          a.adjust);
-            rx = r.x;
-            ry = r.y;
-        }
-        reinterpret_cast<float2 *>(a.out)[row] = make_float2((float)rx, (float)ry);
+    // Step 4: FP64 solve (the sums are the same on every lane); an
+    // ill-conditioned system is recomputed in FP64 by the whole warp
+    const double a00 = A00, a01 = A01, a11 = A11, b0 = B0, b1 = B1;
+    const double det = a00 * a11 - a01 * a01;
+    const double tr = a00 + a11;
+    if (det > kDetRefine * tr * tr) {
+        if (lane == 0)
+            reinterpret_cast<float2 *>(a.out)[row] =
+                make_float2((float)((b0 * a11 - a01 * b1) / det + (double)l0.x),
+                            (float)((a00 * b1 - a01 * b0) / det + (double)l0.y));
+    } else {
+        const float2 r = refine_warp_point<D, kVarMaxK>(a.X, row, a.center, Lg, lo2, a.L, a.k,
+                                                        a.boost, a.adjust);
+        if (lane == 0) reinterpret_cast<float2 *>(a.out)[row] = r;
     }
 }
 

@@ -221,3 +221,45 @@ def test_project_host_matches_device(esom, pinned, n, plan):
         out = P.project_host(Xh, w.boost, w.adjust)
         torch.cuda.current_stream().synchronize()
         assert torch.equal(out, ref)
+
+
+def test_ill_conditioned_points_every_path(esom):
+    """With adjust = 2 on unstructured data about 4% of the points have a
+    normal system with det/trace^2 < 1e-3, which FP32 sums cannot resolve
+    (errors up to 35x the bound before); every execution plan, the batched
+    launch and the no-alloc entry point list them and recompute them in
+    FP64, one warp a point.  All return the same bits, within 1e-4 of the
+    extent of the FP64 oracle, and the handle counts the recomputed points."""
+    rng = np.random.default_rng(11)
+    w = workloads.random_case(rng, 1500, 16, 200, 12, boost=2.0, adjust=2.0)
+    X = torch.from_numpy(w.X).cuda()
+    hi, lo = torch.from_numpy(w.hi).cuda(), torch.from_numpy(w.lo).cuda()
+    outs = {}
+    with esom.Projector(w.d, w.L, w.k) as P:
+        P.set_landmarks(hi, lo)
+        for plan, name in esom.PLAN_NAMES.items():
+            P.set_plan(plan)
+            P.stats(reset=True)
+            outs[name] = P.project(X, w.boost, w.adjust).cpu().numpy()
+            assert P.device_status() == 0
+            assert P.stats()["refines"] > 0, name
+        out_b = torch.empty((w.n, 2), device="cuda")
+        P.set_plan(esom.ESOM_PLAN_FUSED)
+        item = esom.BatchItem(P.h, X.data_ptr(), w.n, out_b.data_ptr(), w.boost, w.adjust)
+        st, b = esom.esom_batch_create([item], False)
+        assert st == 0
+        assert esom.esom_batch_run(b, 0) == 0
+        torch.cuda.synchronize()
+        outs["batch"] = out_b.cpu().numpy()
+        esom.esom_batch_destroy(b)
+    out_n = torch.empty((w.n, 2), device="cuda")
+    assert esom.esom_project_noalloc(X.data_ptr(), w.n, hi.data_ptr(), lo.data_ptr(), w.d, w.L,
+                                     w.k, out_n.data_ptr(), w.boost, w.adjust, 0) == 0
+    torch.cuda.synchronize()
+    outs["noalloc"] = out_n.cpu().numpy()
+    for name, o in outs.items():
+        assert np.array_equal(o.view(np.uint32), outs["fused"].view(np.uint32)), name
+    o, ratio, _ = oracle.project(w.X, w.hi, w.lo, w.k, w.boost, w.adjust, diagnostics=True)
+    stats = coord_errors(outs["fused"], o, ratio, w.extent)
+    report(stats, "ill-conditioned, every path")
+    assert stats["ill_conditioned"] > 20
