@@ -320,6 +320,7 @@ def run_esom(args, world, rank, local):
     torch.cuda.synchronize()
     if P.device_status() != 0:
         raise RuntimeError("device status flag raised during warm-up")
+    P.stats(reset=True)  # the timed region's counters start here
 
     props = torch.cuda.get_device_properties(dev)
     uuid = getattr(props, "uuid", None)
@@ -450,10 +451,9 @@ def run_esom(args, world, rank, local):
             "phases_ms": {"knn_only": float(np.median(knn_ms)),
                           "projection_share": 1.0 - float(np.median(knn_ms))
                           / float(np.median(step_ms))},
-            # this library's kernels per step: one fused launch, or per pass
-            # of 2^19 points a k-NN, a rescan and a projection launch
-            "gpu_launches": args.steps * (1 if screen == "fused" else
-                                          3 * ((n + (1 << 19) - 1) >> 19)),
+            # this library's kernels launched in the timed region, as the
+            # handle counted them (esom_get_stats)
+            "gpu_launches": main_stats["launches"],
             "plans_ms": {screen: float(np.median(step_ms)),
                          **{o: v[0] for o, v in others.items()}},
             "rescan_fraction": {screen: main_stats["rescans"] / max(main_stats["points"], 1),

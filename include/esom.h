@@ -127,6 +127,8 @@ typedef struct {
     uint64_t refines;   /* points whose FP32 normal system was too ill-conditioned
                            (det/trace^2 <= 1e-3), so steps 1-4 were recomputed
                            in FP64 (slower path) */
+    uint64_t launches;  /* kernels this library launched for esom_project,
+                           esom_project_host and esom_knn calls of the handle */
 } esom_stats;
 
 /* Waits for `stream`, then returns the handle's counters accumulated since
@@ -174,8 +176,10 @@ esom_status esom_get_config(esom_handle h, esom_config *cfg);
  * esom_get_stats), so both modes return the same neighbours, distances and
  * coordinates, bit for bit; the mode only changes speed.
  * With TF32, esom_project runs the tensor-core k-NN kernel and then a
- * projection kernel over passes of 2^19 points, exchanging the neighbours
- * through a scratch buffer of the handle (2^19 * k * 8 bytes): projections
+ * re-rank and projection kernel over passes of 2^20 points, exchanging the
+ * screened candidate lists through scratch buffers of the handle (2^20 *
+ * (k + 4 .. 8) * 4 bytes, and 2^20 * k * 8 bytes for the neighbours of the
+ * few points whose certificate fails): projections
  * of one handle on different streams must then not overlap.
  * Switching to TF32 allocates the landmark images (2 * ceil(L/64) * 64 *
  * row bytes, row bytes = 64 for d <= 16, else 128 * ceil(d/32)) and the
@@ -191,8 +195,8 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream);
 
 /* on != 0: esom_project with FP32 screening runs as two kernels, as the
  * paper's pipeline does (Section 4.4): the k-NN kernel writes each point's
- * neighbours to the handle's scratch (2^19 * k * 8 bytes, allocated here),
- * then the projection kernel reads them, in passes of 2^19 points; on = 0:
+ * neighbours to the handle's scratch (2^20 * k * 8 bytes, allocated here),
+ * then the projection kernel reads them, in passes of 2^20 points; on = 0:
  * one fused kernel (the default).  Same results either way; projections of
  * one handle on different streams must not overlap while split (the
  * scratch is shared).  Tensor-core screening always runs split.
@@ -255,7 +259,7 @@ esom_status esom_set_centering(esom_handle h, int on);
 #define ESOM_PLAN_SPLIT 1
 #define ESOM_PLAN_TF32 2
 #define ESOM_PLAN_BF16 3
-/* Autotuner: times each plan on the first min(n, 2^19) of `points` (device,
+/* Autotuner: times each plan on the first min(n, 2^20) of `points` (device,
  * n x d) three times on `stream`, writing their coordinates to `out`
  * (n x 2 device), keeps the fastest for the handle (as if set with
  * esom_set_screening / esom_set_split) and stores it in *plan (nullable).
@@ -475,7 +479,7 @@ esom_status esom_test_stall(esom_handle h, int64_t limit_ns);
  * k-NN (Section 4.2: the distance block; here a tcgen05 contraction of split
  * TF32 or BF16 operands with FP32 accumulation), for tests of its error
  * bound.  Needs tensor-core screening on (esom_set_screening).  For each of
- * the n points (n <= 2^19; device, as for esom_project) writes
+ * the n points (n <= 2^20; device, as for esom_project) writes
  * T[i * Lc + j] = the accumulated x_i . L_j for j < Lc = 64 ceil(L / 64)
  * (landmarks beyond L are zero rows) to T (device, n * Lc floats, 16-byte
  * aligned).  Errors: ESOM_EINVAL, ESOM_EALIGN, ESOM_ENOLANDMARKS,

@@ -50,7 +50,7 @@ class EsomError(RuntimeError):
 
 class _Stats(ctypes.Structure):
     _fields_ = [("points", ctypes.c_uint64), ("rescans", ctypes.c_uint64),
-                ("refines", ctypes.c_uint64)]
+                ("refines", ctypes.c_uint64), ("launches", ctypes.c_uint64)]
 
 
 class BatchItem(ctypes.Structure):
@@ -220,7 +220,7 @@ def esom_get_stats(h, stream: int = 0, reset: bool = False):
     st_ = _Stats()
     st = load().esom_get_stats(h, stream, ctypes.byref(st_), int(reset))
     return st, {"points": int(st_.points), "rescans": int(st_.rescans),
-                "refines": int(st_.refines)}
+                "refines": int(st_.refines), "launches": int(st_.launches)}
 
 
 def esom_set_screening(h, mode: int, stream: int = 0) -> int:

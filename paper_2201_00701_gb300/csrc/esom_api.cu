@@ -74,10 +74,9 @@ void fill_args(const esom_ctx *h, const float *points, long long n, float *out, 
     a->ntiles = (n + kThreads - 1) / kThreads;
     a->status = h->status;
     a->img = h->img;
-    // The pair loop reads the distance table when its landmark rows are not
-    // in shared memory (streamed chunks); with resident rows recomputing from
-    // shared memory is faster than the L2 gathers.
-    a->qtab = h->nchunks > 1 ? h->qtab : nullptr;
+    // the pair constants from the handle's table (whichever it keeps)
+    a->ptab = h->ptab;
+    a->qtab = h->qtab;
     a->center = h->centered ? h->center : nullptr;
     a->tc_chunks = (h->L + kTcN - 1) / kTcN;
     a->refine_list = h->refine_list;
@@ -259,9 +258,14 @@ esom_status configure(esom_ctx *h) {
 // the spatial order (when on), then the split chunk images in that order.
 cudaError_t build_screening(esom_ctx *h, int prec, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
-    if (h->order_on)
+    if (h->order_on) {
+        // a handle that keeps its order (the frame server's sessions, whose
+        // landmarks move a little per frame) recomputes it only the first time
+        const bool reorder = !h->keep_order || !h->order_valid;
         e = esom::launch_landmark_order(h->hi, h->norms, h->L, h->d, h->lperm, h->centers,
-                                        h->norms_int, h->corder, st);
+                                        h->norms_int, h->corder, st, reorder);
+        if (e == cudaSuccess) h->order_valid = 1;
+    }
     if (e == cudaSuccess)
         e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, prec, st,
                                   h->order_on ? h->lperm : nullptr);
@@ -281,6 +285,10 @@ esom_status check_device(const esom_ctx *h) {
     return ESOM_OK;
 }
 
+// Which projection kernel the handle's tables call for (PairMode: 0 pair
+// table, 1 squared-distance table, 2 neither).
+int proj_mode(const esom_ctx *h) { return h->ptab ? 0 : h->qtab ? 1 : 2; }
+
 // Projection from given neighbours by the library's kernel (one thread per
 // point, distance table), the launch the split path makes after its k-NN.
 // The FP64 recomputation of the rows the projection just listed (one warp a
@@ -290,8 +298,10 @@ cudaError_t launch_refine(esom_ctx *h, const FusedArgs &p, cudaStream_t stream) 
 }
 
 esom_status launch_projection(esom_ctx *h, FusedArgs p0, cudaStream_t stream) {
+    p0.ptab = h->ptab;
     p0.qtab = h->qtab;
     p0.mode = esom::kProject;
+    const int pm = proj_mode(h);
     unsigned *rcount = reinterpret_cast<unsigned *>(h->status) + 4;
     // passes of at most kTcPass points: the refine list holds one pass
     for (long long off = 0; off < p0.n; off += esom::kTcPass) {
@@ -304,15 +314,13 @@ esom_status launch_projection(esom_ctx *h, FusedArgs p0, cudaStream_t stream) {
         if (off > 0) p.perm = nullptr;  // a visiting order covers one pass
         cudaError_t e = cudaMemsetAsync(rcount, 0, sizeof(unsigned), stream);
         if (e == cudaSuccess) {
-            const bool res =
-                h->nchunks == 1 && esom::project_smem_bytes(h->d, h->L, true) <= h->proj_smem;
-            p.nchunks = res ? 1 : 2;
-            p.ntiles = (p.n + esom::kThreads - 1) / esom::kThreads;
+            p.ntiles = (p.n + esom::proj_threads(pm) - 1) / esom::proj_threads(pm);
             long long grid = (long long)h->proj_blocks_per_sm * h->num_sms;
             if (grid > p.ntiles) grid = p.ntiles;
-            e = h->ops->launch_proj(p, (int)grid, h->proj_smem, stream);
+            e = h->ops->launch_proj[pm](p, (int)grid, h->proj_smem, stream);
         }
         if (e == cudaSuccess) e = launch_refine(h, p, stream);
+        h->launches += 2;
         if (e != cudaSuccess) return cuda_fail(e, "projection kernel launch");
     }
     return ESOM_OK;
@@ -334,11 +342,15 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
         // count lives in status word 3) and are resolved by the warp-per-point
         // rescan kernel after the pass; a pass holds at most kTcPass points.
         unsigned *fail_count = reinterpret_cast<unsigned *>(h->status) + 3;
-        auto knn = [&](FusedArgs k, long long cnt) -> cudaError_t {
+        // proj_out (tensor-core plans, projection): the exact re-rank and the
+        // projection run as one kernel writing proj_out, and the points whose
+        // certificate failed are projected after their rescan
+        auto knn = [&](FusedArgs k, long long cnt, float *proj_out) -> cudaError_t {
             k.mode = esom::kKnn;
             k.fail_list = h->fail_list;
             k.fail_count = fail_count;
-            cudaError_t r = cudaMemsetAsync(fail_count, 0, sizeof(unsigned), stream);
+            // status words 3 and 4: the fail count and the refine count
+            cudaError_t r = cudaMemsetAsync(fail_count, 0, 2 * sizeof(unsigned), stream);
             if (r != cudaSuccess) return r;
             if (h->screening) {
                 // points grouped by home chunk; the tensor-core k-NN writes
@@ -352,6 +364,7 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                                                  h->home, h->counts, esom::kOrderBlocks, h->perm,
                                                  h->tile_home, stream);
                     if (r != cudaSuccess) return r;
+                    h->launches += 2;
                     t.perm = h->perm;
                     t.tile_home = h->tile_home;
                     t.corder = h->corder;
@@ -363,6 +376,33 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                 if (grid > tiles) grid = tiles;
                 r = h->tc->launch(t, (int)grid, h->tc_smem, stream);
                 if (r != cudaSuccess) return r;
+                ++h->launches;
+                if (proj_out) {
+                    const int pm = proj_mode(h);
+                    FusedArgs rp = t;
+                    rp.mode = esom::kProject;
+                    rp.out = proj_out;
+                    rp.norms = h->norms;
+                    const long long ptiles =
+                        (cnt + esom::proj_threads(pm) - 1) / esom::proj_threads(pm);
+                    long long pgrid = (long long)h->rproj_blocks_per_sm * h->num_sms;
+                    if (pgrid > ptiles) pgrid = ptiles;
+                    r = h->ops->launch_rproj[pm](rp, (int)pgrid, h->proj_smem, stream);
+                    if (r != cudaSuccess) return r;
+                    r = h->ops->launch_rescan(k, 2 * h->num_sms, stream);
+                    if (r != cudaSuccess) return r;
+                    // the failed points, from their rescanned neighbours
+                    FusedArgs pf = k;
+                    pf.mode = esom::kProject;
+                    pf.out = proj_out;
+                    pf.perm = nullptr;
+                    pf.rows_list = h->fail_list;
+                    pf.rows_count = fail_count;
+                    r = h->ops->launch_proj[pm](pf, h->num_sms, h->proj_smem, stream);
+                    if (r != cudaSuccess) return r;
+                    h->launches += 4;  // re-rank + projection, rescan, projection, refine
+                    return launch_refine(h, pf, stream);
+                }
                 FusedArgs rr = t;
                 rr.norms = h->norms;
                 rr.nchunks = h->rerank_smem > esom::rerank_smem_bytes(h->d, h->L, false) ? 1 : 2;
@@ -370,13 +410,16 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                 long long rgrid = (long long)h->rerank_blocks_per_sm * h->num_sms;
                 if (rgrid > rtiles) rgrid = rtiles;
                 r = h->ops->launch_rerank(rr, (int)rgrid, h->rerank_smem, stream);
+                ++h->launches;
             } else {
                 k.ntiles = (cnt + esom::kThreads - 1) / esom::kThreads;
                 long long grid = (long long)h->blocks_per_sm * h->num_sms;
                 if (grid > k.ntiles) grid = k.ntiles;
                 r = h->ops->launch(k, (int)grid, h->smem, stream);
+                ++h->launches;
             }
             if (r != cudaSuccess) return r;
+            ++h->launches;
             return h->ops->launch_rescan(k, 2 * h->num_sms, stream);
         };
         if (mode == esom::kKnn) {
@@ -387,7 +430,7 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                 k.n = cnt;
                 k.idx = idx + off * h->k;
                 k.dist2 = dist2 ? dist2 + off * h->k : nullptr;
-                e = knn(k, cnt);
+                e = knn(k, cnt, nullptr);
             }
         } else {
             for (long long off = 0; off < n && e == cudaSuccess; off += esom::kTcPass) {
@@ -397,7 +440,11 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                 k.n = cnt;
                 k.idx = h->tc_idx;
                 k.dist2 = h->tc_d2;
-                e = knn(k, cnt);
+                if (h->screening) {
+                    e = knn(k, cnt, out + off * 2);
+                    continue;
+                }
+                e = knn(k, cnt, nullptr);
                 if (e != cudaSuccess) break;
                 FusedArgs p = k;
                 p.out = out + off * 2;
@@ -435,6 +482,7 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
             if (mode == esom::kProject) e = cudaMemsetAsync(rcount, 0, sizeof(unsigned), stream);
             if (e == cudaSuccess) e = h->ops->launch(f, (int)grid, h->smem, stream);
             if (e == cudaSuccess && mode == esom::kProject) e = launch_refine(h, f, stream);
+            h->launches += mode == esom::kProject ? 2 : 1;
         }
     }
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
@@ -487,7 +535,9 @@ esom_status esom_create(int d, int L, int k, esom_handle *out) {
     if (e == cudaSuccess)
         e = cudaMalloc(&h->norms, (size_t)((L + esom::kTcN - 1) / esom::kTcN * esom::kTcN) *
                                       sizeof(float));
-    if (e == cudaSuccess && L <= esom::kQtabMaxL)
+    if (e == cudaSuccess && L <= esom::kPtabMaxL)
+        e = cudaMalloc(&h->ptab, (size_t)L * L * sizeof(float2));
+    else if (e == cudaSuccess && L <= esom::kQtabMaxL)
         e = cudaMalloc(&h->qtab, (size_t)L * L * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->refine_list, (size_t)esom::kTcPass * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->status, 256);
@@ -526,7 +576,8 @@ esom_status esom_set_landmarks(esom_handle h, const float *hi, const float *lo,
                                                          reinterpret_cast<float *>(h->status + 1), st,
                                                          esom::kTcN,
                                                          h->centered ? h->center : nullptr);
-    if (e == cudaSuccess && h->qtab) e = h->ops->launch_qtab(h->hi, h->L, h->qtab, st);
+    if (e == cudaSuccess && (h->ptab || h->qtab))
+        e = h->ops->launch_pair_table(h->hi, h->lo, h->L, h->ptab, h->qtab, st);
     if (e == cudaSuccess && h->screening) e = build_screening(h, tc_prec(h->screening), st);
     if (e != cudaSuccess) return cuda_fail(e, "landmark copy");
     ++h->version;
@@ -664,7 +715,9 @@ esom_status esom_get_stats(esom_handle h, esom_stream_t stream, esom_stats *out,
     out->points = h->points;
     out->rescans = words[2];
     out->refines = words[5];
+    out->launches = h->launches;
     if (reset) {
+        h->launches = 0;
         e = cudaMemset(h->status + 2, 0, sizeof(unsigned));
         if (e == cudaSuccess) e = cudaMemset(h->status + 5, 0, sizeof(unsigned));
         if (e != cudaSuccess) return cuda_fail(e, "stats reset");
@@ -724,18 +777,29 @@ esom_status prepare_projection(esom_ctx *h) {
     int optin = 0;
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(shared memory opt-in)");
-    const bool resident = h->nchunks == 1;
-    const size_t psmem = esom::project_smem_bytes(h->d, h->L, resident);
+    const int pm = proj_mode(h);
+    const size_t psmem = esom::project_smem_bytes(h->L, h->kc, pm);
     if (psmem > (size_t)optin)
         return fail(ESOM_EUNSUPPORTED, "projection needs %zu bytes of shared memory", psmem);
-    e = cudaFuncSetAttribute(h->ops->proj_func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    const void *fn = h->ops->proj_func[pm];
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(projection shared memory)");
-    int pbps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pbps, h->ops->proj_func, esom::kThreads, psmem);
+    int pbps = 0, rbps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pbps, fn, esom::proj_threads(pm), psmem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (pbps < 1) return fail(ESOM_EUNSUPPORTED, "projection launch does not fit on an SM");
+    // the re-rank + projection kernel of the tensor-core plans (same shared
+    // memory layout)
+    const void *rfn = h->ops->rproj_func[pm];
+    e = cudaFuncSetAttribute(rfn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rbps, rfn, esom::proj_threads(pm),
+                                                          psmem);
+    if (e != cudaSuccess) return cuda_fail(e, "re-rank projection kernel configuration");
+    if (rbps < 1) return fail(ESOM_EUNSUPPORTED, "re-rank projection launch does not fit on an SM");
     h->proj_smem = psmem;
     h->proj_blocks_per_sm = pbps;
+    h->rproj_blocks_per_sm = rbps;
     return ESOM_OK;
 }
 
@@ -1039,6 +1103,7 @@ esom_status esom_destroy(esom_handle h) {
     cudaFree(h->refine_list);
     cudaFree(h->img);
     cudaFree(h->qtab);
+    cudaFree(h->ptab);
     cudaFree(h->tc_idx);
     cudaFree(h->tc_d2);
     cudaFree(h->fail_list);

@@ -64,6 +64,11 @@ struct Group {
 
 }  // namespace
 
+// Status words of a batch: [0] error bits, [2] rescans, then one
+// refine-list count per group from kGroupCountWord on.
+constexpr int kGroupCountWord = 16;
+constexpr int kStatusWords = 1024;
+
 struct esom_batch_ctx {
     int dev = 0, num_sms = 0, optin = 0;
     std::vector<esom_batch_item> items;
@@ -94,7 +99,8 @@ esom_status apply_shape(esom_batch_ctx *b, Group &g, const Shape &sh) {
             FusedArgs &a = g.args[i];
             a.chunk = h->chunk;
             a.nchunks = h->nchunks;
-            a.qtab = h->nchunks > 1 ? h->qtab : nullptr;
+            a.ptab = h->ptab;
+            a.qtab = h->qtab;
         }
         g.shape = Shape{0, 0, 1};
         g.grid = 0;
@@ -110,7 +116,8 @@ esom_status apply_shape(esom_batch_ctx *b, Group &g, const Shape &sh) {
             chunk = esom::landmark_chunk(h->L, h->d, sh.forced_chunk);
         a.chunk = chunk;
         a.nchunks = (h->L + chunk - 1) / chunk;
-        a.qtab = a.nchunks > 1 ? h->qtab : nullptr;
+        a.ptab = h->ptab;
+        a.qtab = h->qtab;
         cap = std::max(cap, chunk);
     }
     const size_t smem = esom::batch_smem_bytes(g.D, cap);
@@ -156,6 +163,7 @@ esom_status apply_shape(esom_batch_ctx *b, Group &g, const Shape &sh) {
 
 esom_status launch_group(esom_batch_ctx *b, const Group &g, cudaStream_t st) {
     if (g.tiles == 0) return ESOM_OK;
+    const int gi = (int)(&g - b->groups.data());
     if (g.shape.separate) {
         // each dataset through its handle's own execution plan (fused,
         // split or tensor-core, as set on the handle or chosen by esom_tune)
@@ -177,7 +185,8 @@ esom_status launch_group(esom_batch_ctx *b, const Group &g, cudaStream_t st) {
     // points whose FP32 system is too ill-conditioned: listed by the group's
     // launch, recomputed in FP64 right after it
     a.refine_list = g.d_refine;
-    a.refine_count = reinterpret_cast<unsigned *>(b->status) + 4;
+    // each group its own count (groups may run concurrently in a graph)
+    a.refine_count = reinterpret_cast<unsigned *>(b->status) + kGroupCountWord + gi;
     cudaError_t e = cudaMemsetAsync(a.refine_count, 0, sizeof(unsigned), st);
     if (e == cudaSuccess) e = g.ops->launch_batch(a, g.grid, g.smem, st);
     if (e == cudaSuccess) e = g.ops->launch_refine_batch(a, 2 * b->num_sms, st);
@@ -283,8 +292,8 @@ esom_status esom_batch_create(const esom_batch_item *items, int count, int autot
         }
         b->groups[(size_t)gidx[key]].items.push_back(i);
     }
-    e = cudaMalloc(&b->status, 256);
-    if (e == cudaSuccess) e = cudaMemset(b->status, 0, 256);
+    e = cudaMalloc(&b->status, kStatusWords * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->status, 0, kStatusWords * sizeof(int));
     esom_status s = e == cudaSuccess ? ESOM_OK : bcuda(e, "batch status");
     for (Group &g : b->groups) {
         if (s != ESOM_OK) break;
@@ -344,6 +353,70 @@ esom_status esom_batch_run(esom_batch b, esom_stream_t stream) {
     return ESOM_OK;
 }
 
+// Launches the batch's work as independent branches forked from and joined
+// back into the capture stream: each group's batched launch on a branch of
+// its own, and the datasets that run through their own handles (separate
+// shapes) on one branch per handle (datasets sharing a handle share its
+// scratch, so they stay in order on that branch).  The branches have no
+// data in common, so the graph lets their kernels overlap on the GPU.
+esom_status capture_branches(esom_batch_ctx *b, cudaStream_t cap) {
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    std::map<const esom_ctx *, size_t> by_handle;
+    cudaEvent_t fork = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, cap);
+    auto branch = [&](size_t *idx) -> cudaError_t {
+        cudaStream_t bs;
+        cudaError_t r = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+        if (r != cudaSuccess) return r;
+        streams.push_back(bs);
+        *idx = streams.size() - 1;
+        return cudaStreamWaitEvent(bs, fork, 0);
+    };
+    esom_status s = e == cudaSuccess ? ESOM_OK : bcuda(e, "batch graph fork");
+    for (const Group &g : b->groups) {
+        if (s != ESOM_OK || g.tiles == 0) continue;
+        if (!g.shape.separate) {
+            size_t bi = 0;
+            e = branch(&bi);
+            s = e == cudaSuccess ? launch_group(b, g, streams[bi]) : bcuda(e, "batch branch");
+            continue;
+        }
+        for (int idx : g.items) {
+            const esom_batch_item &it = b->items[(size_t)idx];
+            if (it.n == 0 || s != ESOM_OK) continue;
+            auto f = by_handle.find(it.landmarks);
+            size_t bi = 0;
+            if (f == by_handle.end()) {
+                e = branch(&bi);
+                if (e != cudaSuccess) {
+                    s = bcuda(e, "batch branch");
+                    break;
+                }
+                by_handle[it.landmarks] = bi;
+            } else {
+                bi = f->second;
+            }
+            s = esom_project(it.landmarks, it.points, it.n, it.out, it.boost, it.adjust,
+                             reinterpret_cast<esom_stream_t>(streams[bi]));
+        }
+    }
+    // join every branch back into the capture stream
+    for (cudaStream_t bs : streams) {
+        cudaEvent_t j = nullptr;
+        cudaError_t r = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+        if (r == cudaSuccess) r = cudaEventRecord(j, bs);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(cap, j, 0);
+        if (j) events.push_back(j);
+        if (r != cudaSuccess && s == ESOM_OK) s = bcuda(r, "batch graph join");
+    }
+    for (cudaEvent_t j : events) cudaEventDestroy(j);
+    for (cudaStream_t bs : streams) cudaStreamDestroy(bs);
+    if (fork) cudaEventDestroy(fork);
+    return s;
+}
+
 esom_status esom_batch_run_graph(esom_batch b, esom_stream_t stream) {
     if (!b) return bfail(ESOM_EINVAL, "null batch");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -352,8 +425,7 @@ esom_status esom_batch_run_graph(esom_batch b, esom_stream_t stream) {
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         if (e != cudaSuccess) return bcuda(e, "capture stream");
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        esom_status s = e == cudaSuccess ? esom_batch_run(b, reinterpret_cast<esom_stream_t>(cap))
-                                          : bcuda(e, "begin capture");
+        esom_status s = e == cudaSuccess ? capture_branches(b, cap) : bcuda(e, "begin capture");
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
         cudaStreamDestroy(cap);

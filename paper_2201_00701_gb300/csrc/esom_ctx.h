@@ -18,7 +18,10 @@ struct esom_ctx {
     // current pass, [4] refine-list length of the current pass
     int *status = nullptr;
     long long *refine_list = nullptr;  // rows of one pass for the FP64 recomputation
-    float *qtab = nullptr; // L x L squared landmark distances (L <= kQtabMaxL)
+    // pair constants of the projection per landmark pair: the pair table
+    // (L <= kPtabMaxL), else the squared landmark distances (L <= kQtabMaxL)
+    float2 *ptab = nullptr;
+    float *qtab = nullptr;
     uint64_t version = 0;
     const esom::KernelOps *ops = nullptr;
     int num_sms = 0;
@@ -27,6 +30,7 @@ struct esom_ctx {
     // launch; 0 = none (the launch consumes it)
     unsigned long long stall_ns = 0;
     uint64_t points = 0;   // points handed to the kernels since the last stats reset
+    uint64_t launches = 0; // kernels launched for esom_project / esom_knn since then
     // launch configuration (derived from L, d and the chunk choice)
     int chunk = 0, nchunks = 0, blocks_per_sm = 0;
     size_t smem = 0;
@@ -46,7 +50,7 @@ struct esom_ctx {
     int *tc_idx = nullptr;
     float *tc_d2 = nullptr;
     long long *fail_list = nullptr;  // rows whose certificate failed (kTcPass)
-    int proj_blocks_per_sm = 0;
+    int proj_blocks_per_sm = 0, rproj_blocks_per_sm = 0;
     size_t proj_smem = 0;
     // tensor-core k-NN: screened lists of one pass (kTcPass x kc keys) and
     // the exact re-rank kernel's configuration
@@ -58,6 +62,9 @@ struct esom_ctx {
     // visiting orders; per pass: point homes, block counts, visiting order
     // of the points, home chunk of each tile
     int order_on = 0;
+    // keep_order: reuse the landmark order on later landmark sets (set by the
+    // frame server); order_valid: lperm holds an order of this handle
+    int keep_order = 0, order_valid = 0;
     int *lperm = nullptr;
     float *centers = nullptr;
     float *norms_int = nullptr;

@@ -146,6 +146,17 @@ __device__ __forceinline__ void copy_pieces(void *dst, const void *src, uint32_t
     }
 }
 
+// Read-only global load that does not allocate in L1: for data read once
+// (points, screened lists), so that it does not evict the landmark rows and
+// pair-table entries other loads keep there.
+__device__ __forceinline__ float4 ldg_stream(const float4 *p) {
+    float4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "l"(p));
+    return r;
+}
+
 // Reciprocal by the SFU (one instruction, relative error ~2^-23); used
 // where a correctly rounded division is not needed.
 __device__ __forceinline__ float rcp_fast(float x) {
@@ -527,108 +538,199 @@ __device__ __forceinline__ int nb_at(const uint32_t *col, int t) {
 // Step 3: pair terms over u < v < m, accumulated into the normal system
 // (A, b).  D_uv uses the law of cosines on the exact squared distances:
 // <X - L_u, L_v - L_u> = (|X - L_u|^2 + |L_v - L_u|^2 - |X - L_v|^2) / 2.
+// The constants of a landmark pair (pair_entry) depend only on the two
+// landmarks; the handle tabulates them per landmark set (the pair table,
+// built with pair_entry itself, or the table of |L_v - L_u|^2 alone for
+// large L), and kernels without a table compute them from the rows.
 // Every kernel that projects adds the same terms in the same order (u
 // ascending, then v ascending) with pair_add, so all execution plans give
 // the same bits whatever layout their neighbour data has.
 
+// Where the pair constants come from.
+enum PairMode : int {
+    kPairTab2 = 0,  // a.ptab: the pair table, (1/q, 1/r) per landmark pair
+    kPairTab1 = 1,  // a.qtab: q = |L_v - L_u|^2 per landmark pair
+    kPairRows = 2,  // neither: q from the landmark rows in global memory
+};
+
 // |L_v - L_u|^2 in the FP32 difference form with four partial sums; the
-// table of squared landmark distances (landmark_dist_kernel) holds exactly
-// these values.
+// tables hold exactly these values (or values computed from them).  nlu is
+// -L_u (so each difference is one packed add); the sums run two at a time on
+// the packed FP32x2 pipe, each lane the same operation as the scalar form.
 template <int D>
-__device__ __forceinline__ float pair_q(const float4 (&lu)[D / 4], const float4 *Lv, int fv) {
-    float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+__device__ __forceinline__ float pair_q_neg(const float4 (&nlu)[D / 4], const float4 *Lv, int fv) {
+    float2 q01 = make_float2(0.f, 0.f), q23 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int e = 0; e < D / 4; ++e) {
         const float4 lv = Lv[e ^ fv];
-        const float ex = lv.x - lu[e].x, ey = lv.y - lu[e].y;
-        const float ez = lv.z - lu[e].z, ew = lv.w - lu[e].w;
-        q0 = fmaf(ex, ex, q0);
-        q1 = fmaf(ey, ey, q1);
-        q2 = fmaf(ez, ez, q2);
-        q3 = fmaf(ew, ew, q3);
+        const float2 exy = __fadd2_rn(make_float2(lv.x, lv.y), make_float2(nlu[e].x, nlu[e].y));
+        const float2 ezw = __fadd2_rn(make_float2(lv.z, lv.w), make_float2(nlu[e].z, nlu[e].w));
+        q01 = __ffma2_rn(exy, exy, q01);
+        q23 = __ffma2_rn(ezw, ezw, q23);
     }
-    return (q0 + q1) + (q2 + q3);
+    return (q01.x + q01.y) + (q23.x + q23.y);
+}
+
+template <int D>
+__device__ __forceinline__ float pair_q(const float4 (&lu)[D / 4], const float4 *Lv, int fv) {
+    float4 nlu[D / 4];
+#pragma unroll
+    for (int e = 0; e < D / 4; ++e) nlu[e] = make_float4(-lu[e].x, -lu[e].y, -lu[e].z, -lu[e].w);
+    return pair_q_neg<D>(nlu, Lv, fv);
+}
+
+// The constants of landmark pair (u, v) from q = |L_v - L_u|^2 and the 2-D
+// operator h = l_v - l_u (absolute 2-D coordinates): (1/q, 1/|h|^2) by the
+// SFU (relative error ~2^-23).  A pair that does not count (L_u = L_v, or
+// l_u = l_v) gets 1/|h|^2 = 0, which zeroes its weight and so every term it
+// adds; 1/q = 0 when q = 0 keeps its intermediates finite.
+__device__ __forceinline__ float2 pair_entry(float qq, float hx, float hy) {
+    const float r = fmaf(hx, hx, hy * hy);
+    const float iq = qq > 0.f ? rcp_fast(qq) : 0.f;
+    return make_float2(iq, (qq > 0.f && r > 0.f) ? rcp_fast(r) : 0.f);
 }
 
 struct NormalSys {
     float a00, a01, a11, b0, b1;
 };
 
-// One pair's terms: the 2-D operator h = l_v - l_u (positions relative to
-// the nearest neighbour's), r = |h|^2, the weight w = s_u s_v r^-adjust
-// (1/r itself for adjust = 1, else by the SFU, relative error ~1e-6), D_uv,
-// and w h h^T / r and w h (D_uv + <h, l_u>/r) added to the system.  A pair
-// that does not count (use false: outside u < v < m; or L_u = L_v, qq = 0;
-// or l_u = l_v, r = 0) gets weight 0 with finite intermediates, so it adds
-// exact zeros.
+// One pair's terms, with u = l_u - l_0 (positions relative to the nearest
+// neighbour's), h = l_v - l_u, hd = half the exact squared distances and
+// e = pair_entry(...): the weight w = s_u s_v r^-adjust (1/r itself for
+// adjust = 1, else by the SFU, relative error ~1e-6), D_uv, and
+// w h h^T / r and w h (D_uv + <h, u>/r) added to the system.
 template <bool ADJ1>
-__device__ __forceinline__ void pair_add(float ux, float uy, float su, float du, float vx,
-                                         float vy, float sv, float dv, float qq, bool use,
-                                         float adjust, NormalSys &S) {
-    const float hx = vx - ux, hy = vy - uy;
-    const float r = fmaf(hx, hx, hy * hy);
-    const bool ok = use && qq > 0.f && r > 0.f;
-    const float ir = r > 0.f ? rcp_fast(r) : 0.f;
-    const float wr0 = ADJ1 ? ir : exp2f_fast(-adjust * log2f_fast(r));
-    const float w = ok ? su * sv * wr0 : 0.f;
+__device__ __forceinline__ void pair_add(float ux, float uy, float su, float hdu, float hx,
+                                         float hy, float sv, float hdv, float2 e, float adjust,
+                                         NormalSys &S) {
+    const float ir = e.y;
+    const float wr0 = ADJ1 ? ir : (ir > 0.f ? exp2f_fast(adjust * log2f_fast(ir)) : 0.f);
+    const float w = su * sv * wr0;
     const float wr = w * ir;
-    const float Duv = fmaf(0.5f * (du - dv), qq > 0.f ? rcp_fast(qq) : 0.f, 0.5f);
+    const float Duv = fmaf(hdu - hdv, e.x, 0.5f);
     const float rhs = fmaf(fmaf(hx, ux, hy * uy), ir, Duv);
-    const float th = wr * hx;
-    S.a00 = fmaf(th, hx, S.a00);
-    S.a01 = fmaf(th, hy, S.a01);
-    S.a11 = fmaf(wr * hy, hy, S.a11);
+    // the updates two at a time on the packed FP32x2 pipe
+    const float2 h2 = make_float2(hx, hy);
+    const float2 th = __fmul2_rn(make_float2(wr, wr), h2);  // (wr hx, wr hy)
+    const float2 a0 = __ffma2_rn(make_float2(th.x, th.x), h2, make_float2(S.a00, S.a01));
+    S.a00 = a0.x;
+    S.a01 = a0.y;
+    S.a11 = fmaf(th.y, hy, S.a11);
     const float wrhs = w * rhs;
-    S.b0 = fmaf(wrhs, hx, S.b0);
-    S.b1 = fmaf(wrhs, hy, S.b1);
+    const float2 b = __ffma2_rn(make_float2(wrhs, wrhs), h2, make_float2(S.b0, S.b1));
+    S.b0 = b.x;
+    S.b1 = b.y;
 }
 
 // The pairs of one point whose neighbour indices sit in this thread's column
-// of shared memory (nb_at) and whose scores and distances are in registers;
-// 2-D positions gathered from lo2, |L_v - L_u|^2 from the table when given,
-// else from the rows.  PF (the projection kernel, which always has the
-// table): row u's table entries are gathered up front, predicated and
-// independent, so their L2 latencies overlap.
-template <int D, int KK, bool ADJ1, int QS = kThreads, bool PF = false>
-__device__ __forceinline__ void pair_sums_regs(const float (&sd)[KK], const float (&ss)[KK],
+// of shared memory (nb_at) and whose scores and half distances are in
+// registers (the fused and batched kernels); 2-D positions gathered from
+// lo2; the pair constants from whichever table the arguments carry, else
+// from the rows Lg.
+template <int D, int KK, bool ADJ1, int QS = kThreads>
+__device__ __forceinline__ void pair_sums_regs(const float (&hd)[KK], const float (&ss)[KK],
                                                const uint32_t *nb, int m, const float4 *Lg,
                                                const float2 *lo2, float2 l0, const FusedArgs &a,
                                                NormalSys &S) {
 #pragma unroll 1
     for (int u = 0; u < m - 1; ++u) {
         const int iu = nb_at<QS>(nb, u);
-        float su = ss[0], du = sd[0];
+        float su = ss[0], hdu = hd[0];
 #pragma unroll
         for (int t = 1; t < KK; ++t)
             if (t == u) {
                 su = ss[t];
-                du = sd[t];
+                hdu = hd[t];
             }
+        const float2 pu = lo2[iu];
+        const float ux = pu.x - l0.x, uy = pu.y - l0.y;
+        const float2 *trow = a.ptab ? a.ptab + (size_t)iu * a.L : nullptr;
         const float *qrow = a.qtab ? a.qtab + (size_t)iu * a.L : nullptr;
         const float4 *Lu = Lg + (size_t)iu * (D / 4);
         const int fu = swz(D, iu);
         float4 lu[D / 4];
 #pragma unroll
         for (int e = 0; e < D / 4; ++e)
-            lu[e] = qrow ? make_float4(0.f, 0.f, 0.f, 0.f) : Lu[e ^ fu];
-        const float2 lut = lo2[iu];
-        const float ux = lut.x - l0.x, uy = lut.y - l0.y;
-        float qv[PF ? KK : 1];
+            lu[e] = (trow || qrow) ? make_float4(0.f, 0.f, 0.f, 0.f) : Lu[e ^ fu];
 #pragma unroll
-        for (int v = 0; v < (PF ? KK : 1); ++v)
-            qv[v] = (PF && v > u && v < m) ? __ldg(qrow + nb_at<QS>(nb, v)) : 1.f;
+        for (int v = 1; v < KK; ++v) {
+            if (v > u && v < m) {
+                const int iv = nb_at<QS>(nb, v);
+                const float2 pv = lo2[iv];
+                const float hx = pv.x - pu.x, hy = pv.y - pu.y;
+                const float2 e =
+                    trow ? __ldg(trow + iv)
+                         : pair_entry(qrow ? __ldg(qrow + iv)
+                                           : pair_q<D>(lu, Lg + (size_t)iv * (D / 4), swz(D, iv)),
+                                      hx, hy);
+                pair_add<ADJ1>(ux, uy, su, hdu, hx, hy, ss[v], hd[v], e, a.adjust, S);
+            }
+        }
+    }
+}
+
+// The same pairs for the projection kernels, both loops at run time: each
+// neighbour's score and half distance (sst, float2) and landmark index (sti)
+// sit in this thread's columns of shared memory (stride NT), the 2-D
+// positions in lo2; the pair constants of u's row come from the table in
+// groups of 8 whose loads are issued before their pairs are summed (MODE
+// kPairTab2 / kPairTab1), or are computed from the rows (kPairRows).  Only
+// the pairs u < v < m are visited.
+template <int D, bool ADJ1, int MODE, int NT>
+__device__ __forceinline__ void pair_sums_stash(const float2 *sst, const int *sti, int m,
+                                                const float2 *lo2, float2 l0, const FusedArgs &a,
+                                                NormalSys &S) {
+    constexpr int G = 8;
+#pragma unroll 1
+    for (int u = 0; u < m - 1; ++u) {
+        const float2 uh = sst[u * NT];  // (s_u, hd_u)
+        const int iu = sti[u * NT];
+        const float2 pu = lo2[iu];
+        const float ux = pu.x - l0.x, uy = pu.y - l0.y;
+        if constexpr (MODE == kPairRows) {
+            const float4 *Lg = reinterpret_cast<const float4 *>(a.hi);
+            const float4 *Lu = Lg + (size_t)iu * (D / 4);
+            const int fu = swz(D, iu);
+            float4 lu[D / 4];
 #pragma unroll
-        for (int v0 = 1; v0 < KK; v0 += 2) {
-            if (v0 + 1 > u && v0 < m) {
+            for (int e = 0; e < D / 4; ++e) lu[e] = __ldg(Lu + (e ^ fu));
+#pragma unroll 1
+            for (int v = u + 1; v < m; ++v) {
+                const int iv = sti[v * NT];
+                const float2 vh = sst[v * NT];
+                const float2 pv = lo2[iv];
+                const float hx = pv.x - pu.x, hy = pv.y - pu.y;
+                const float qq = pair_q<D>(lu, Lg + (size_t)iv * (D / 4), swz(D, iv));
+                pair_add<ADJ1>(ux, uy, uh.x, uh.y, hx, hy, vh.x, vh.y, pair_entry(qq, hx, hy),
+                               a.adjust, S);
+            }
+        } else {
+            const float2 *trow = MODE == kPairTab2 ? a.ptab + (size_t)iu * a.L : nullptr;
+            const float *qrow = MODE == kPairTab1 ? a.qtab + (size_t)iu * a.L : nullptr;
+#pragma unroll 1
+            for (int v0 = u + 1; v0 < m; v0 += G) {
+                int iv[G];
+                float2 ev[G];
 #pragma unroll
-                for (int v = v0; v < v0 + 2 && v < KK; ++v) {
-                    const int iv = nb_at<QS>(nb, v);
-                    const float2 lvt = lo2[iv];
-                    const float qq = PF     ? qv[v < (PF ? KK : 1) ? v : 0]
-                                     : qrow ? __ldg(qrow + iv)
-                                            : pair_q<D>(lu, Lg + (size_t)iv * (D / 4), swz(D, iv));
-                    pair_add<ADJ1>(ux, uy, su, du, lvt.x - l0.x, lvt.y - l0.y, ss[v], sd[v], qq,
-                                   v > u && v < m, a.adjust, S);
+                for (int j = 0; j < G; ++j) iv[j] = v0 + j < m ? sti[(v0 + j) * NT] : iu;
+#pragma unroll
+                // (cached in L1: the spatially ordered points of a warp share
+                // most of their neighbours, so they reread the same entries)
+                for (int j = 0; j < G; ++j) {
+                    if (MODE == kPairTab2)
+                        ev[j] = __ldg(trow + iv[j]);
+                    else
+                        ev[j].x = __ldg(qrow + iv[j]);
+                }
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    if (v0 + j < m) {
+                        const float2 vh = sst[(v0 + j) * NT];
+                        const float2 pv = lo2[iv[j]];
+                        const float hx = pv.x - pu.x, hy = pv.y - pu.y;
+                        const float2 e = MODE == kPairTab2 ? ev[j] : pair_entry(ev[j].x, hx, hy);
+                        pair_add<ADJ1>(ux, uy, uh.x, uh.y, hx, hy, vh.x, vh.y, e, a.adjust, S);
+                    }
                 }
             }
         }
@@ -731,21 +833,50 @@ __device__ __forceinline__ float2 point_solve(const NormalSys &S, float2 l0, lon
 // Steps 2-4 for one point whose landmark indices are in this thread's
 // column of shared memory (nb_at(nb, t) for rank t) and whose exact squared
 // distances are in sd (the fused and batched kernels).
-template <int D, int KK, int QS = kThreads, bool PF = false, class SINK>
+template <int D, int KK, int QS = kThreads, class SINK>
 __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uint32_t *nb,
                                                 const float4 *Lg, const float2 *lo2,
                                                 const FusedArgs &a, long long row, bool active,
                                                 const SINK &sink) {
     const int m = a.k - 1;
-    float ss[KK];
+    float ss[KK], hd[KK];
     point_scores<KK>(sd, a.k, a.boost, ss);
+#pragma unroll
+    for (int t = 0; t < KK; ++t) hd[t] = 0.5f * sd[t];
     // 2-D coordinates relative to the nearest neighbour's.
     const float2 l0 = lo2[nb_at<QS>(nb, 0)];
     NormalSys S = {0.f, 0.f, 0.f, 0.f, 0.f};
     if (a.adjust == 1.f)
-        pair_sums_regs<D, KK, true, QS, PF>(sd, ss, nb, m, Lg, lo2, l0, a, S);
+        pair_sums_regs<D, KK, true, QS>(hd, ss, nb, m, Lg, lo2, l0, a, S);
     else
-        pair_sums_regs<D, KK, false, QS, PF>(sd, ss, nb, m, Lg, lo2, l0, a, S);
+        pair_sums_regs<D, KK, false, QS>(hd, ss, nb, m, Lg, lo2, l0, a, S);
+    return point_solve(S, l0, row, active, sink);
+}
+
+// Steps 2-4 for one point of the projection kernels: neighbour indices and
+// exact squared distances in registers (si, sd); each neighbour's score and
+// half distance and its index go to this thread's stash columns sst / sti
+// (stride NT) for the pair loop.
+template <int D, int KK, int MODE, int NT, class SINK>
+__device__ __forceinline__ float2 project_point_stash(const float (&sd)[KK], const int (&si)[KK],
+                                                      float2 *sst, int *sti, const float2 *lo2,
+                                                      const FusedArgs &a, long long row,
+                                                      bool active, const SINK &sink) {
+    const int m = a.k - 1;
+    float ss[KK];
+    point_scores<KK>(sd, a.k, a.boost, ss);
+    const float2 l0 = lo2[si[0]];
+#pragma unroll
+    for (int t = 0; t < KK; ++t)
+        if (t < m) {
+            sst[t * NT] = make_float2(ss[t], 0.5f * sd[t]);
+            sti[t * NT] = si[t];
+        }
+    NormalSys S = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (a.adjust == 1.f)
+        pair_sums_stash<D, true, MODE, NT>(sst, sti, m, lo2, l0, a, S);
+    else
+        pair_sums_stash<D, false, MODE, NT>(sst, sti, m, lo2, l0, a, S);
     return point_solve(S, l0, row, active, sink);
 }
 
@@ -1211,22 +1342,69 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchArgs B
 // ---------------------------------------------------------------------------
 // Steps 2-4 from given neighbours: one thread per point reads its k indices
 // and exact squared distances (ascending, as a k-NN kernel wrote them) and
-// runs the fused kernel's projection.  Landmark rows are copied into shared
-// memory once per block when they fit (a.nchunks == 1), else read from
-// global memory; the pair loop uses the distance table when a.qtab is set.
+// projects.  Blocks of proj_threads(MODE); each thread keeps its
+// neighbours' scores, half distances and indices in stash columns of shared
+// memory for the pair loop (pair_sums_stash), with the pair constants from a
+// table (the 2-D positions then copied into shared memory once per block) or
+// computed from the rows in global memory (L above the tables' limit).
 
-// The projection loop over this block's tiles.  Instantiated once with the
-// rows and 2-D positions in shared memory and once in global memory, so the
-// compiler knows each pointer's space (shared loads instead of generic ones).
-template <int D, int KK, bool TAB>
-__device__ __forceinline__ void project_tiles(const FusedArgs &a, const float4 *Lg,
-                                              const float2 *lo2, uint32_t *nb, int tid) {
-    const long long ntiles = (a.n + kThreads - 1) / kThreads;
+// Shared memory of the projection kernels: the stash columns and, with a
+// table, the 2-D positions.
+template <int KK, int MODE>
+__device__ __forceinline__ void proj_smem_layout(unsigned char *smem, float2 **sst, int **sti,
+                                                 float2 **lo) {
+    constexpr int NT = proj_threads(MODE);
+    unsigned char *p = smem + kBarrierBytes;
+    *sst = reinterpret_cast<float2 *>(p);
+    p += (size_t)KK * NT * sizeof(float2);
+    *sti = reinterpret_cast<int *>(p);
+    p += (size_t)KK * NT * sizeof(int);
+    *lo = reinterpret_cast<float2 *>(p);
+}
+
+// Copies the 2-D positions into shared memory by bulk copies (every mode but
+// kPairRows); false if the copy did not land in time (reported, drained).
+template <int MODE>
+__device__ __forceinline__ bool proj_stage(const FusedArgs &a, uint64_t *bar, float2 *lo) {
+    if (MODE == kPairRows) return true;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // (the handle's 2-D position buffer is padded to 16 bytes)
+        const uint32_t lbytes = (uint32_t)(((size_t)a.L * 2 * sizeof(float) + 15) & ~(size_t)15);
+        mbar_expect_tx(bar, lbytes);
+        copy_pieces(lo, a.lo, lbytes, bar);
+    }
+    const bool ok = mbar_wait(bar, 0);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+            atomicOr(a.status, kErrWaitTimeout);
+            mbar_wait(bar, 0);
+        }
+        return false;
+    }
+    return true;
+}
+
+template <int D, int KK, int MODE>
+__device__ __forceinline__ void project_tiles(const FusedArgs &a, const float2 *lo2, float2 *sst,
+                                              int *sti, int tid) {
+    constexpr int NT = proj_threads(MODE);
+    const long long ntiles = (a.n + NT - 1) / NT;
     const bool vec = (a.k & 3) == 0;  // rows of k entries are 16-byte aligned
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long long pos = tile * kThreads + tid;
-        const bool active = pos < a.n;
-        const long long row = active && a.perm ? (long long)__ldg(a.perm + pos) : pos;
+    const long long nlist = a.rows_list ? (long long)*a.rows_count : 0;
+    const long long ntl = a.rows_list ? (nlist + NT - 1) / NT : ntiles;
+    for (long long tile = blockIdx.x; tile < ntl; tile += gridDim.x) {
+        const long long pos = tile * NT + tid;
+        const bool active = pos < (a.rows_list ? nlist : a.n);
+        const long long row = !active       ? 0
+                              : a.rows_list ? __ldg(a.rows_list + pos)
+                              : a.perm      ? (long long)__ldg(a.perm + pos)
+                                            : pos;
         float sd[KK];
         int si[KK];
         if (vec) {
@@ -1256,67 +1434,34 @@ __device__ __forceinline__ void project_tiles(const FusedArgs &a, const float4 *
                 sd[t] = have ? a.dist2[row * a.k + t] : 0.f;
             }
         }
-#pragma unroll
-        for (int t = 0; t < KK; t += 2)
-            nb[(t >> 1) * kThreads] = (uint32_t)si[t] | ((uint32_t)si[t + 1] << 16);
-        const float2 p = project_point<D, KK, kThreads, TAB>(
-            sd, nb, Lg, lo2, a, row, active, RefineSink{a.refine_list, a.refine_count});
+        const float2 p = project_point_stash<D, KK, MODE, NT>(
+            sd, si, sst + tid, sti + tid, lo2, a, row, active,
+            RefineSink{a.refine_list, a.refine_count});
         if (active) reinterpret_cast<float2 *>(a.out)[row] = p;
     }
 }
 
-template <int D, int KC, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) project_kernel(const FusedArgs a) {
+template <int D, int KC, int MODE>
+__global__ void __launch_bounds__(proj_threads(MODE), proj_min_blocks(MODE)) project_kernel(const FusedArgs a) {
     constexpr int KK = KC - 4;
+    constexpr int NT = proj_threads(MODE);
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    float *sL = reinterpret_cast<float *>(smem + kBarrierBytes);
-    const bool resident = a.nchunks == 1;
-    float2 *sLo = reinterpret_cast<float2 *>(sL + (resident ? (size_t)a.L * D : 0));
-    uint32_t *qk = reinterpret_cast<uint32_t *>(sLo + (resident ? (a.L + 1) & ~1 : 0));
+    float2 *sst, *sLo;
+    int *sti;
+    proj_smem_layout<KK, MODE>(smem, &sst, &sti, &sLo);
     const int tid = threadIdx.x;
-    const long long ntiles = (a.n + kThreads - 1) / kThreads;
+    const long long ntiles =
+        a.rows_list ? ((long long)*a.rows_count + NT - 1) / NT : (a.n + NT - 1) / NT;
     if ((long long)blockIdx.x >= ntiles) return;
-    if (resident) {
-        if (tid == 0) {
-            mbar_init(bar, 1);
-            fence_mbar_init();
-        }
-        __syncthreads();
-        if (tid == 0) {
-            const uint32_t bytes = (uint32_t)((size_t)a.L * D * sizeof(float));
-            // (the handle's 2-D position buffer is padded to 16 bytes)
-            const uint32_t lbytes = (uint32_t)(((size_t)a.L * 2 * sizeof(float) + 15) & ~(size_t)15);
-            mbar_expect_tx(bar, bytes + lbytes);
-            copy_pieces(sL, a.hi, bytes, bar);
-            copy_pieces(sLo, a.lo, lbytes, bar);
-        }
-        const bool ok = mbar_wait(bar, 0);
-        if (!__syncthreads_and(ok)) {
-            // the copy did not land in time: report, drain it (bounded), leave
-            if (tid == 0) {
-                atomicOr(a.status, kErrWaitTimeout);
-                mbar_wait(bar, 0);
-            }
-            return;
-        }
-        if (a.qtab)
-            project_tiles<D, KK, true>(a, reinterpret_cast<const float4 *>(sL), sLo, qk + tid, tid);
-        else
-            project_tiles<D, KK, false>(a, reinterpret_cast<const float4 *>(sL), sLo, qk + tid,
-                                        tid);
-    } else if (a.qtab) {
-        project_tiles<D, KK, true>(a, reinterpret_cast<const float4 *>(a.hi),
-                                   reinterpret_cast<const float2 *>(a.lo), qk + tid, tid);
-    } else {
-        project_tiles<D, KK, false>(a, reinterpret_cast<const float4 *>(a.hi),
-                                    reinterpret_cast<const float2 *>(a.lo), qk + tid, tid);
-    }
+    if (!proj_stage<MODE>(a, bar, sLo)) return;
+    project_tiles<D, KK, MODE>(
+        a, MODE == kPairRows ? reinterpret_cast<const float2 *>(a.lo) : sLo, sst, sti, tid);
 }
 
-template <int D, int KC, int MINB>
+template <int D, int KC, int MODE>
 cudaError_t launch_project(const FusedArgs &a, int grid, size_t smem, cudaStream_t stream) {
-    project_kernel<D, KC, MINB><<<grid, kThreads, smem, stream>>>(a);
+    project_kernel<D, KC, MODE><<<grid, proj_threads(MODE), smem, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -1356,7 +1501,8 @@ __device__ __forceinline__ void rerank_tiles(const FusedArgs &a, const float4 *L
         const float sx = xn + lmax;
         const float M = a.m_dot * xn * lmax + 2.f * kGamma * sx * sx;
         float keys[KC];
-        const float4 *cp = reinterpret_cast<const float4 *>(a.cand + row * KC);
+        // (the screened lists are stored in the k-NN's visiting order)
+        const float4 *cp = reinterpret_cast<const float4 *>(a.cand + (active ? pos : 0) * KC);
 #pragma unroll
         for (int t = 0; t < KC; t += 4) {
             const float4 v = active ? __ldg(cp + t / 4) : make_float4(INFINITY, INFINITY, INFINITY,
@@ -1422,6 +1568,86 @@ __global__ void __launch_bounds__(kThreads) rerank_kernel(const FusedArgs a) {
 template <int D, int KC>
 cudaError_t launch_rerank(const FusedArgs &a, int grid, size_t smem, cudaStream_t stream) {
     rerank_kernel<D, KC><<<grid, kThreads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+// Exact re-rank and projection of the tensor-core k-NN's screened lists in
+// one pass (the tensor-core plan of esom_project): one thread per point, in
+// the k-NN's visiting order; the re-rank of rerank_tiles, then, for a
+// certified list, steps 2-4 of the projection kernel with the neighbours
+// still in registers, so no neighbour exchange buffer is written or read.
+// The re-rank reads the landmark rows through the L1 cache.  A point whose
+// certificate
+// fails goes to a.fail_list; rescan_kernel and the projection kernel over
+// that list finish it.
+template <int D, int KC, int MODE>
+__global__ void __launch_bounds__(proj_threads(MODE), proj_min_blocks(MODE))
+    rerank_project_kernel(const FusedArgs a) {
+    constexpr int KK = KC - 4;
+    constexpr int NT = proj_threads(MODE);
+    constexpr float kGamma = (2.25f * D + 10.f) * kU * 1.25f;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    float2 *sst, *sLo;
+    int *sti;
+    proj_smem_layout<KK, MODE>(smem, &sst, &sti, &sLo);
+    const int tid = threadIdx.x;
+    const long long ntiles = (a.n + NT - 1) / NT;
+    if ((long long)blockIdx.x >= ntiles) return;
+    if (!proj_stage<MODE>(a, bar, sLo)) return;
+    const float2 *lo2 = MODE == kPairRows ? reinterpret_cast<const float2 *>(a.lo) : sLo;
+    const float4 *Lg = reinterpret_cast<const float4 *>(a.hi);
+    const float lmax = *a.lmax;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long pos = tile * NT + tid;
+        const bool active = pos < a.n;
+        const long long row = !active ? 0 : (a.perm ? (long long)__ldg(a.perm + pos) : pos);
+        float4 xr[D / 4];
+        const float4 *xp = reinterpret_cast<const float4 *>(a.X) + row * (D / 4);
+        float xx = 0.f;
+#pragma unroll
+        for (int e = 0; e < D / 4; ++e) {
+            xr[e] = active ? centred(ldg_stream(xp + e), a.center, e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xx = fmaf(xr[e].x, xr[e].x, xx);
+            xx = fmaf(xr[e].y, xr[e].y, xx);
+            xx = fmaf(xr[e].z, xr[e].z, xx);
+            xx = fmaf(xr[e].w, xr[e].w, xx);
+        }
+        const float xn = sqrtf(xx);
+        const float sx = xn + lmax;
+        const float M = a.m_dot * xn * lmax + 2.f * kGamma * sx * sx;
+        float keys[KC];
+        const float4 *cp = reinterpret_cast<const float4 *>(a.cand + (active ? pos : 0) * KC);
+#pragma unroll
+        for (int t = 0; t < KC; t += 4) {
+            const float4 v = active ? ldg_stream(cp + t / 4)
+                                    : make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+            keys[t] = v.x;
+            keys[t + 1] = v.y;
+            keys[t + 2] = v.z;
+            keys[t + 3] = v.w;
+        }
+        float sd[KK];
+        int si[KK];
+        const bool cert = rerank<D, KC, KK>(xr, keys, Lg, a.key_mask, a.L, a.k, M, a.key_quant,
+                                            sd, si, xx, a.lperm);
+        if (active && __builtin_expect(!cert, 0)) {
+            atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
+            a.fail_list[atomicAdd(a.fail_count, 1u)] = row;
+        }
+        const bool proj = active && cert;
+#pragma unroll
+        for (int t = 0; t < KK; ++t) si[t] = min(max(si[t], 0), a.L - 1);
+        const float2 p = project_point_stash<D, KK, MODE, NT>(
+            sd, si, sst + tid, sti + tid, lo2, a, row, proj,
+            RefineSink{a.refine_list, a.refine_count});
+        if (proj) reinterpret_cast<float2 *>(a.out)[row] = p;
+    }
+}
+
+template <int D, int KC, int MODE>
+cudaError_t launch_rerank_project(const FusedArgs &a, int grid, size_t smem, cudaStream_t stream) {
+    rerank_project_kernel<D, KC, MODE><<<grid, proj_threads(MODE), smem, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -1960,11 +2186,12 @@ cudaError_t launch_refine_batch(const BatchArgs &b, int grid, cudaStream_t strea
     return cudaGetLastError();
 }
 
-// One thread per ordered pair (u, v): the squared distance table of the pair
-// loop, computed by the loop's own pair_q.
+// One thread per ordered pair (u, v) of landmarks: the pair table
+// (pair_entry of the loop's own pair_q and the 2-D operator) when ptab is
+// given, else the table of squared landmark distances (pair_q alone).
 template <int D>
-__global__ void landmark_dist_kernel(const float *__restrict__ hi, int L,
-                                     float *__restrict__ qtab) {
+__global__ void landmark_pair_kernel(const float *__restrict__ hi, const float *__restrict__ lo,
+                                     int L, float2 *__restrict__ ptab, float *__restrict__ qtab) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)L * L) return;
     const int u = (int)(t / L), v = (int)(t - (long long)u * L);
@@ -1974,13 +2201,22 @@ __global__ void landmark_dist_kernel(const float *__restrict__ hi, int L,
     float4 lu[D / 4];
 #pragma unroll
     for (int e = 0; e < D / 4; ++e) lu[e] = __ldg(Lu + (e ^ fu));
-    qtab[t] = pair_q<D>(lu, Lg + (size_t)v * (D / 4), swz(D, v));
+    const float qq = pair_q<D>(lu, Lg + (size_t)v * (D / 4), swz(D, v));
+    if (ptab) {
+        const float2 pu = reinterpret_cast<const float2 *>(lo)[u];
+        const float2 pv = reinterpret_cast<const float2 *>(lo)[v];
+        ptab[t] = pair_entry(qq, pv.x - pu.x, pv.y - pu.y);
+    } else {
+        qtab[t] = qq;
+    }
 }
 
 template <int D>
-cudaError_t launch_qtab(const float *hi, int L, float *qtab, cudaStream_t stream) {
+cudaError_t launch_pair_table(const float *hi, const float *lo, int L, float2 *ptab, float *qtab,
+                              cudaStream_t stream) {
     const long long pairs = (long long)L * L;
-    landmark_dist_kernel<D><<<(unsigned)((pairs + 255) / 256), 256, 0, stream>>>(hi, L, qtab);
+    landmark_pair_kernel<D><<<(unsigned)((pairs + 255) / 256), 256, 0, stream>>>(hi, lo, L, ptab,
+                                                                                qtab);
     return cudaGetLastError();
 }
 
@@ -2009,10 +2245,19 @@ const KernelOps Instance<D, KC>::ops = {
     reinterpret_cast<const void *>(&fused_kernel<D, KC, Instance<D, KC>::kMinBlocks>), KC,
     &launch_fused<D, KC, Instance<D, KC>::kMinBlocks>,
     reinterpret_cast<const void *>(&batch_kernel<D, KC, Instance<D, KC>::kMinBlocks>),
-    &launch_batch<D, KC, Instance<D, KC>::kMinBlocks>, &launch_qtab<D>,
-    reinterpret_cast<const void *>(&project_kernel<D, KC, Instance<D, KC>::kMinBlocks>),
-    &launch_project<D, KC, Instance<D, KC>::kMinBlocks>, &launch_rescan<D, KC>,
+    &launch_batch<D, KC, Instance<D, KC>::kMinBlocks>, &launch_pair_table<D>,
+    {reinterpret_cast<const void *>(&project_kernel<D, KC, kPairTab2>),
+     reinterpret_cast<const void *>(&project_kernel<D, KC, kPairTab1>),
+     reinterpret_cast<const void *>(&project_kernel<D, KC, kPairRows>)},
+    {&launch_project<D, KC, kPairTab2>, &launch_project<D, KC, kPairTab1>,
+     &launch_project<D, KC, kPairRows>},
+    &launch_rescan<D, KC>,
     reinterpret_cast<const void *>(&rerank_kernel<D, KC>), &launch_rerank<D, KC>,
+    {reinterpret_cast<const void *>(&rerank_project_kernel<D, KC, kPairTab2>),
+     reinterpret_cast<const void *>(&rerank_project_kernel<D, KC, kPairTab1>),
+     reinterpret_cast<const void *>(&rerank_project_kernel<D, KC, kPairRows>)},
+    {&launch_rerank_project<D, KC, kPairTab2>, &launch_rerank_project<D, KC, kPairTab1>,
+     &launch_rerank_project<D, KC, kPairRows>},
     &launch_refine<D, KC>, &launch_refine_batch<D, KC>};
 
 // Table of the list capacities instantiated for each D.

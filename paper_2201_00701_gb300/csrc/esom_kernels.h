@@ -39,7 +39,11 @@ struct FusedArgs {
     int *status;          // device status words: [0] error bits, [2] rescan count
     const unsigned char *img;  // tensor-core screening: landmark chunk images
     int tc_chunks;        // ceil(L / kTcN) chunks in img
-    const float *qtab;    // L x L squared landmark distances (pair_q values), or null
+    // pair constants of the projection (pair_entry): the pair table of
+    // (1/q, 1/r) per landmark pair, or the L x L table of q = |L_v - L_u|^2
+    // (pair_q values) for larger L; both null: computed from the rows
+    const float2 *ptab;
+    const float *qtab;
     // k-NN mode: when set, a point whose screening certificate fails is not
     // rescanned in line but appended (row index) to fail_list, counted in
     // *fail_count; rescan_kernel then finds its neighbours exactly
@@ -70,6 +74,10 @@ struct FusedArgs {
     // appended here (count in *refine_count) for refine_kernel
     long long *refine_list;
     unsigned *refine_count;
+    // projection kernel: when set, it projects only the rows listed here
+    // (*rows_count of them; e.g. the points whose certificate failed)
+    const long long *rows_list;
+    const unsigned *rows_count;
 };
 
 // x - c, four at a time (c may be null: no centring).
@@ -99,15 +107,18 @@ struct KernelOps {
     cudaError_t (*launch)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
     const void *batch_func;
     cudaError_t (*launch_batch)(const BatchArgs &, int grid, size_t smem, cudaStream_t);
-    // Fills qtab[u * L + v] = |L_v - L_u|^2 from the (chunk-swizzled) rows
-    // of hi with the pair loop's own arithmetic (pair_q), so the table holds
-    // exactly the values the loop would compute.
-    cudaError_t (*launch_qtab)(const float *hi, int L, float *qtab, cudaStream_t);
+    // Fills the pair table ptab[u * L + v] = pair_entry(q, l_v - l_u) when
+    // ptab is given, else qtab[u * L + v] = q, with q = |L_v - L_u|^2 from
+    // the (chunk-swizzled) rows of hi by the pair loop's own arithmetic
+    // (pair_q), so the tables hold exactly the values the loop would compute.
+    cudaError_t (*launch_pair_table)(const float *hi, const float *lo, int L, float2 *ptab,
+                                     float *qtab, cudaStream_t);
     // Projection from given neighbours (FusedArgs idx / dist2, k per point):
-    // steps 2-4 of the fused kernel, landmark rows and 2-D positions
-    // resident in shared memory when a.nchunks == 1 (project_smem_bytes).
-    const void *proj_func;
-    cudaError_t (*launch_proj)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
+    // steps 2-4 of the fused kernel in blocks of kProjThreads, one kernel per
+    // source of the pair constants (index: PairMode of esom_fused.cuh;
+    // shared memory: project_smem_bytes).
+    const void *proj_func[3];
+    cudaError_t (*launch_proj[3])(const FusedArgs &, int grid, size_t smem, cudaStream_t);
     // Exact k-NN of the rows in a.fail_list (one warp per row), written to
     // a.idx / a.dist2 like the k-NN kernels do.
     cudaError_t (*launch_rescan)(const FusedArgs &, int grid, cudaStream_t);
@@ -117,6 +128,12 @@ struct KernelOps {
     // certificate; writes a.idx / a.dist2, failed rows to a.fail_list.
     const void *rerank_func;
     cudaError_t (*launch_rerank)(const FusedArgs &, int grid, size_t smem, cudaStream_t);
+    // Exact re-rank and projection in one kernel (the tensor-core plan's
+    // projection, blocks of kProjThreads, one kernel per PairMode, shared
+    // memory project_smem_bytes): certified points are projected at once,
+    // the others go to a.fail_list.
+    const void *rproj_func[3];
+    cudaError_t (*launch_rproj[3])(const FusedArgs &, int grid, size_t smem, cudaStream_t);
     // FP64 recomputation, one block a point, of the rows in a.refine_list
     // (B.refine_list for the batched kernel), written to the outputs.
     cudaError_t (*launch_refine)(const FusedArgs &, int grid, cudaStream_t);
@@ -131,9 +148,17 @@ inline size_t rerank_smem_bytes(int D, int L, bool resident) {
 // Returns the instantiation for dimension D and list capacity kc, or nullptr.
 const KernelOps *kernel_ops(int D, int kc);
 
-// Largest L for which a handle keeps the L x L table of squared landmark
-// distances (64 MiB at 4096); above it the pair loop computes them.
+// Largest L for which a handle keeps the pair table (8 bytes a landmark
+// pair: 32 MiB at 2048), and the L x L table of squared landmark distances
+// (64 MiB at 4096); above both the pair loop computes its constants.
+constexpr int kPtabMaxL = 2048;
 constexpr int kQtabMaxL = 4096;
+
+// Threads (= points) per block of the projection kernels, and the resident
+// blocks per SM they are compiled for.
+constexpr int kProjThreads = 128;
+__host__ __device__ constexpr int proj_threads(int) { return kProjThreads; }
+__host__ __device__ constexpr int proj_min_blocks(int) { return 4; }
 
 
 // ---------------------------------------------------------------------------
@@ -222,9 +247,12 @@ inline size_t tc_smem_bytes(int D, int KC, int prec = kTcTf32) {
 // the squared norms in the internal order (NaN padding) and each chunk's
 // visiting order (corder[c * nch + r], the chunks by centroid distance).
 constexpr int kOrderMaxL = 8192;
+// With reorder false the landmark order lperm is kept (it only sets the
+// speed of the screening, never its result) and only the centroids, the
+// internal-order norms and the visiting orders are recomputed.
 cudaError_t launch_landmark_order(const float *hi, const float *norms, int L, int D, int *lperm,
                                   float *centers, float *norms_int, unsigned short *corder,
-                                  cudaStream_t stream);
+                                  cudaStream_t stream, bool reorder = true);
 // The points of one pass grouped by home chunk (nearest centroid):
 // perm[pos] = point at visiting position pos, tile_home[t] = home chunk of
 // position kTcRows t; home (n) and counts (nblocks * nch) are scratch.
@@ -237,7 +265,7 @@ cudaError_t launch_point_order(const float *X, long long n, int D, const float *
 // Points per tensor-core k-NN pass of esom_project: the pass writes their
 // neighbours (k indices and squared distances each) to the handle's scratch,
 // the projection kernel reads them.
-constexpr long long kTcPass = 1 << 19;
+constexpr long long kTcPass = 1 << 20;
 
 struct TcOps {
     const void *func;
@@ -246,10 +274,14 @@ struct TcOps {
 };
 
 
-inline size_t project_smem_bytes(int D, int L, bool resident) {
-    return kBarrierBytes +
-           (resident ? (size_t)L * D * sizeof(float) + (size_t)((L + 1) & ~1) * 8 : 0) +
-           (size_t)kQueue * kThreads * sizeof(unsigned);
+// Shared memory of the projection kernels (pair mode `mode`, PairMode of
+// esom_fused.cuh) for list capacity kc: the stash columns (a float2 and an
+// index per neighbour and thread) and, with a table (modes 0, 1), the 2-D
+// positions.
+inline size_t project_smem_bytes(int L, int kc, int mode) {
+    const size_t lo = ((size_t)L * 2 * sizeof(float) + 15) & ~(size_t)15;
+    const size_t kk = (size_t)(kc - 4);
+    return kBarrierBytes + kk * kProjThreads * (8 + 4) + (mode != 2 ? lo : 0);
 }
 
 // Tensor-core instantiation for D, list capacity kc and precision, or

@@ -285,18 +285,21 @@ __global__ void chunk_visit_order_kernel(const float *__restrict__ centers, int 
 
 cudaError_t launch_landmark_order(const float *hi, const float *norms, int L, int D, int *lperm,
                                   float *centers, float *norms_int, unsigned short *corder,
-                                  cudaStream_t stream) {
+                                  cudaStream_t stream, bool reorder) {
     if (L > kOrderMaxL || L < 1) return cudaErrorInvalidValue;
-    int Lp = 1;
-    while (Lp < L) Lp <<= 1;
-    if (Lp < 2) Lp = 2;
-    const size_t smem = (size_t)Lp * sizeof(unsigned long long);
-    cudaError_t e = cudaFuncSetAttribute(landmark_order_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    landmark_order_kernel<<<1, kOrderThreads, smem, stream>>>(hi, L, D, Lp, lperm);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (reorder) {
+        int Lp = 1;
+        while (Lp < L) Lp <<= 1;
+        if (Lp < 2) Lp = 2;
+        const size_t smem = (size_t)Lp * sizeof(unsigned long long);
+        e = cudaFuncSetAttribute(landmark_order_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        landmark_order_kernel<<<1, kOrderThreads, smem, stream>>>(hi, L, D, Lp, lperm);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     const int nch = (L + kTcN - 1) / kTcN;
     chunk_center_kernel<<<nch, kTcN, 0, stream>>>(hi, norms, lperm, L, D, centers, norms_int);
     e = cudaGetLastError();

@@ -309,12 +309,14 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
     // resident points and output, the session's landmark copy and the
     // handle's (rows, 2-D positions, norms, squared-distance table), the
     // minibatch k-NN indices
-    const size_t qtab = d.L <= esom::kQtabMaxL ? (size_t)d.L * d.L * 4 : 0;
+    const size_t qtab = d.L <= esom::kPtabMaxL   ? (size_t)d.L * d.L * 8
+                        : d.L <= esom::kQtabMaxL ? (size_t)d.L * d.L * 4
+                                                 : 0;
     // tensor-core screening: landmark images and the neighbour scratch
     const size_t img = s->screening != ESOM_SCREEN_FP32
                            ? (size_t)((d.L + esom::kTcN - 1) / esom::kTcN) *
                                      esom::tc_chunk_bytes(d.d, esom::kTcTf32) +
-                                 (size_t)esom::kTcPass * d.k * 8
+                                 (size_t)esom::kTcPass * (d.k * 8 + (d.k + 8) * 4)
                            : 0;
     const size_t bytes = (size_t)d.n * d.d * 4 + (size_t)d.n * 8 + (size_t)d.L * (d.d + 2) * 4 * 2 +
                          (size_t)((d.L + 63) & ~63) * 4 + qtab + img +
@@ -350,6 +352,10 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
         if (e == cudaSuccess && r == ESOM_OK && s->screening == ESOM_SCREEN_AUTO)
             r = esom_tune(ss->h, ss->points, d.n, ss->out, d.boost, d.adjust,
                           reinterpret_cast<esom_stream_t>(ss->stream), &ss->plan);
+        // a frame's SOM step moves the landmarks a little: the spatial order
+        // of the tensor-core screening (computed at admission) is kept, so a
+        // frame's landmark refresh does not pay for a new one
+        if (r == ESOM_OK) ss->h->keep_order = 1;
     }
     if (r != ESOM_OK || e != cudaSuccess) {
         free_session(ss);

@@ -179,6 +179,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Smallest of three floats in one instruction (a NaN operand is ignored).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // FP32 -> TF32, round to nearest (ties away from zero); low 13 bits zero.
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;
@@ -425,39 +432,39 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
                 v[jb + 2] = s23.x;
                 v[jb + 3] = s23.y;
             }
-            if (a.perm) {
-                // points grouped by home: skip the 32 values when no lane of
-                // the warp has one below its threshold.  A key differs from
-                // its value v by at most q|v|, and v - q|v| grows with v, so
-                // no key of the group is below the threshold either.
-                float m4[4];
+            // In groups of 8 landmarks: a group is skipped when no lane of
+            // the warp can queue one of its values.  A key differs from its
+            // value v by at most q|v|, and v - q|v| grows with v, so the
+            // group's smallest key is at least vmin - q|vmin|; with the
+            // points grouped by home (a.perm) the lanes of a warp are near
+            // each other and most groups are skipped.
+            float thr = st.thr;
+            uint32_t *qp = qk + st.qn * QS + tid;
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    m4[r] = fminf(fminf(fminf(v[r], v[r + 4]), fminf(v[r + 8], v[r + 12])),
-                                  fminf(fminf(v[r + 16], v[r + 20]), fminf(v[r + 24], v[r + 28])));
-                const float vmin = fminf(fminf(m4[0], m4[1]), fminf(m4[2], m4[3]));
-                if (!__any_sync(0xffffffffu, vmin - q * fabsf(vmin) < st.thr)) return;
-            }
+            for (int g8 = 0; g8 < 32; g8 += 8) {
+                const float vmin = fminf(fmin3(fmin3(v[g8], v[g8 + 1], v[g8 + 2]),
+                                               fmin3(v[g8 + 3], v[g8 + 4], v[g8 + 5]), v[g8 + 6]),
+                                         v[g8 + 7]);
+                if (__any_sync(0xffffffffu, fmaf(-q, fabsf(vmin), vmin) < thr)) {
 #pragma unroll
-            for (int hb = 0; hb < 32; hb += 16) {
-                uint32_t *qp = qk + st.qn * QS + tid;
-#pragma unroll
-                for (int jb = 0; jb < 16; jb += 4) {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float key = make_key(v[hb + jb + e], (uint32_t)(jbase + hb + jb + e),
-                                                   mask);
-                        if (key < st.thr) {
+                    for (int e = 0; e < 8; ++e) {
+                        const float key =
+                            make_key(v[g8 + e], (uint32_t)(jbase + g8 + e), mask);
+                        if (key < thr) {
                             *qp = __float_as_uint(key);
                             qp += QS;
                         }
                     }
                 }
-                st.qn = (int)((qp - (qk + tid)) / QS);
                 // after the check no lane holds more than QC - QI keys, so
                 // the next QI values fit
-                if ((QI == 16 || hb == 16) && __any_sync(0xffffffffu, st.qn > QC - QI))
-                    queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
+                if ((QI == 16 && g8 == 8) || g8 == 24) {
+                    st.qn = (int)((qp - (qk + tid)) / QS);
+                    if (__any_sync(0xffffffffu, st.qn > QC - QI))
+                        queue_flush<KC, QS>(keys, st, qk, tid, a.k, M, q);
+                    qp = qk + st.qn * QS + tid;
+                    thr = st.thr;
+                }
             }
         };
 
@@ -556,7 +563,8 @@ __global__ void __launch_bounds__(kTcThreads, tc_minb(D, KC)) tc_kernel(const Fu
             // in-kernel re-rank gathering the rows from L2 took 37% of this
             // kernel's time).
             if (active) {
-                float4 *cp = reinterpret_cast<float4 *>(a.cand + row * KC);
+                // stored in the visiting order: a warp's lists are contiguous
+                float4 *cp = reinterpret_cast<float4 *>(a.cand + pos * KC);
 #pragma unroll
                 for (int t = 0; t < KC; t += 4)
                     cp[t / 4] = make_float4(keys[t], keys[t + 1], keys[t + 2], keys[t + 3]);

@@ -207,7 +207,7 @@ def test_landmark_update_and_version(esom):
                                            (True, (1 << 20) + 12345, 2)])
 def test_project_host_matches_device(esom, pinned, n, plan):
     """Host-buffer entry point (chunked H2D / kernel / D2H pipeline: a first
-    and a last chunk of one k-NN wave, passes of 2^19 between) gives the same
+    and a last chunk of one k-NN wave, chunks of 2^19 between) gives the same
     bits as the device entry point; n spans one, two, three and several
     chunks."""
     w = workloads.mixture30_d16(n=n)

@@ -60,9 +60,9 @@ def same_as_fp32(esom, w, label, max_rescans=0.02, mode=None):
     return got
 
 
-@pytest.mark.parametrize("n", [1, 127, 128, 129, 20_000 + 77, (1 << 19) + 1000])
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 20_000 + 77, (1 << 20) + 1000])
 def test_mixture30_d16_equals_fp32(esom, n):
-    """Tile edges, a ragged tail, and two k-NN passes (n above 2^19)."""
+    """Tile edges, a ragged tail, and two k-NN passes (n above 2^20)."""
     w = workloads.mixture30_d16(n=n)
     same_as_fp32(esom, w, f"mixture30_d16 n={n}")
 
@@ -190,10 +190,10 @@ def test_side_stream_and_repeat(esom):
 def test_split_equals_fused(esom, case):
     """FP32 screening as two kernels (k-NN, then projection from the
     neighbours) gives the fused kernel's bits, also across pass boundaries
-    (n above 2^19) and with streamed landmark chunks."""
+    (n above 2^20) and with streamed landmark chunks."""
     chunk = None
     if case == "mixture30_d16":
-        w = workloads.mixture30_d16(n=600_000)
+        w = workloads.mixture30_d16(n=(1 << 20) + 70_000)
     elif case == "mixture10_d8":
         w = workloads.mixture10_d8()
     elif case == "uniform_d32":
