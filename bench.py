@@ -34,9 +34,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "mixture30_d16"
-PROFILES = {"fused": os.path.join(ROOT, "profiles", "fused_kernel_mixture30_d16.txt"),
-            "tf32": os.path.join(ROOT, "profiles", "tc_knn_kernel_mixture30_d16.txt"),
-            "bf16": os.path.join(ROOT, "profiles", "tc_knn_kernel_bf16_mixture30_d16.txt")}
+# Committed ncu summaries, by (execution plan, kernel kind): the DRAM traffic
+# of that kernel in one step of the mixture30_d16 benchmark.
+PROFILES = {
+    ("bf16", "tc_knn"): os.path.join(ROOT, "profiles", "tc_knn_kernel_bf16_mixture30_d16.txt"),
+    ("bf16", "rerank_project"): os.path.join(ROOT, "profiles",
+                                             "rerank_project_kernel_mixture30_d16.txt"),
+}
 
 
 # The headline metric of the EmbedSOM projection benchmark.
@@ -47,9 +51,9 @@ def baseline_metric():
     return METRIC
 
 
-# The sources that define the profiled kernels (fused_kernel, tc_kernel,
-# project_kernel, rescan_kernel at d = 16): a change to any of them makes the
-# committed DRAM counters stale.
+# The sources that define the profiled kernels (tc_kernel, rerank_project_kernel
+# and the kernels they share code with, at d = 16): a change to any of them
+# makes the committed DRAM counters stale.
 KERNEL_SOURCES = ("esom_kernels.h", "esom_fused.cuh", "esom_tc.cuh", "esom_k_d16.cu",
                   "esom_tc_d16.cu")
 
@@ -64,13 +68,12 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profile_traffic(screen: str):
-    """DRAM bytes of the dominant kernel in one step, from the committed ncu
-    summary of the screening mode, if it was taken on the current kernel
-    sources."""
+def profile_traffic(plan: str, kernel: str):
+    """DRAM bytes of one kernel in one step, from the committed ncu summary of
+    that (plan, kernel), if it was taken on the current kernel sources."""
     try:
         kv = {}
-        with open(PROFILES[screen]) as f:
+        with open(PROFILES[(plan, kernel)]) as f:
             for line in f:
                 if ":" in line and not line.startswith("#"):
                     key, val = line.split(":", 1)
@@ -366,6 +369,21 @@ def run_esom(args, world, rank, local):
         others[other] = (float(np.median(other_ms)), P.stats(reset=True))
     P.set_plan(plans[screen])
 
+    # per-kernel durations: CUDA events the library records around each of
+    # its launches on the launching stream (esom_set_timing), over steps
+    # like the timed ones (L2 flushed before each)
+    P.set_timing(True)
+    nsteps_t = min(args.steps, 20)
+    for i in range(args.warmup + nsteps_t):
+        if i == args.warmup:
+            P.timing(reset=True)
+        flush.zero_()
+        P.project(X, w.boost, w.adjust, out=out)
+    ktimes = P.timing(reset=True)
+    P.set_timing(False)
+    kernel_ms = {name: ms / nsteps_t for name, (cnt, ms) in ktimes.items() if cnt}
+    kernel_launches = {name: cnt / nsteps_t for name, (cnt, ms) in ktimes.items() if cnt}
+
     # the k-NN step alone (same kernel, no projection phase): splits the step
     # time into k-NN and scores + pair sums + solve
     idx_buf = torch.empty((n, k), dtype=torch.int32, device=dev)
@@ -403,25 +421,47 @@ def run_esom(args, world, rank, local):
 
     if rank == 0:
         value = sharding.job_throughput(n, world, args.steps, total_s)
-        fmas = n * (L * d + k * k * d)              # algorithmic FMAs per launch
+        fmas = n * (L * d + k * k * d)              # algorithmic FMAs of a step
         t_launch = float(np.mean(step_ms)) / 1e3
-        achieved = 2.0 * fmas / t_launch / 1e12     # TFLOP/s (FMA = 2 flops)
         clocks = sampler.summary()
         max_mhz = clocks.get("sm_max_mhz") or 2070
         alu_peak = 2.0 * 128 * props.multi_processor_count * max_mhz * 1e6 / 1e12
-        peak = alu_peak
-        roof_note = f"128 FP32 lanes x {props.multi_processor_count} SMs x {max_mhz} MHz x 2"
+        tensor_peak = tensor_peak_tflops() / (2.0 if screen == "tf32" else 1.0)
+        # per-kernel rooflines: the work each kernel's part of the method
+        # counts (n L d distance FMAs on the tensor pipe for the screened
+        # k-NN; n k^2 d pair FMAs on the FP32 lanes for the projection; both
+        # for the fused kernel), over its own CUDA-event time
+        work = {"tc_knn": (2.0 * n * L * d, tensor_peak, "tensor",
+                           f"2 n L d flops on the {screen.upper()} tensor pipe"),
+                "rerank_project": (2.0 * n * k * k * d, alu_peak, "alu",
+                                   "2 n k^2 d pair flops on the FP32 lanes"),
+                # (the projection kernel projects every point only in the split
+                # plan; in the tensor-core plans just the few that failed)
+                **({"project": (2.0 * n * k * k * d, alu_peak, "alu",
+                                "2 n k^2 d pair flops on the FP32 lanes")}
+                   if screen == "split" else {}),
+                "fused": (2.0 * fmas, alu_peak, "alu",
+                          "2 n (L d + k^2 d) flops on the FP32 lanes")}
+        kernels = {}
+        for name, ms in kernel_ms.items():
+            entry = {"ms_per_step": ms, "launches_per_step": kernel_launches[name],
+                     "share_of_step": ms / float(np.median(step_ms))}
+            if name in work:
+                flops, pk, bound, what = work[name]
+                entry.update({"bound": bound, "achieved_tflops": flops / (ms / 1e3) / 1e12,
+                              "peak_tflops": pk, "frac": flops / (ms / 1e3) / 1e12 / pk,
+                              "algorithmic": what})
+            kernels[name] = entry
+        dom = max((nm for nm in kernels if nm in work), key=lambda nm: kernels[nm]["ms_per_step"])
+        dk = kernels[dom]
+        # the whole step against the mixed peak of its two parts
         if screen in ("tf32", "bf16"):
-            # L*d on the tensor pipe (TF32 = half the measured sustained BF16
-            # rate), k^2*d on the FP32 lanes: the effective peak of the mix
-            tf32_peak = tensor_peak_tflops() / (2.0 if screen == "tf32" else 1.0)
-            t_roof = 2.0 * n * L * d / (tf32_peak * 1e12) + 2.0 * n * k * k * d / (alu_peak * 1e12)
-            peak = 2.0 * fmas / t_roof / 1e12
-            roof_note = (f"n*L*d on {screen.upper()} tensor cores at {tf32_peak:.0f} TFLOP/s "
-                         f"(the measured sustained BF16 rate{', halved' if screen == 'tf32' else ''}"
-                         f") + n*k^2*d on the FP32 lanes at {alu_peak:.1f} TFLOP/s")
-        traffic = (profile_traffic(screen)
-                   if args.workload == WORKLOAD and screen in PROFILES else None)
+            t_roof = 2.0 * n * L * d / (tensor_peak * 1e12) + 2.0 * n * k * k * d / (alu_peak * 1e12)
+            step_peak = 2.0 * fmas / t_roof / 1e12
+        else:
+            step_peak = alu_peak
+        achieved = 2.0 * fmas / t_launch / 1e12
+        traffic = (profile_traffic(screen, dom) if args.workload == WORKLOAD else None)
         line = {
             "metric": baseline_metric(), "value": value, "unit": "points/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -459,28 +499,30 @@ def run_esom(args, world, rank, local):
             "rescan_fraction": {screen: main_stats["rescans"] / max(main_stats["points"], 1),
                                 **{o: v[1]["rescans"] / max(v[1]["points"], 1)
                                    for o, v in others.items()}},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "algorithmic": "2 * n * (L*d + k^2*d) flops per step",
-                         "peak_from": roof_note,
-                         "frac_of_fp32_alu_peak": achieved / alu_peak,
-                         "frac_at_sampled_clock": (achieved / peak * max_mhz / clocks["sm_mhz"])
+            "roofline": {"bound": dk["bound"], "achieved": dk["achieved_tflops"],
+                         "peak": dk["peak_tflops"], "unit": "TFLOP/s", "frac": dk["frac"],
+                         "traffic": traffic, "kernel": dom,
+                         "algorithmic": dk["algorithmic"] + " per launch",
+                         "ms_per_launch": dk["ms_per_step"] / dk["launches_per_step"],
+                         "peak_from": ("MEASURED_PEAKS.json bf16_tflops_sustained"
+                                       + (" halved (TF32)" if screen == "tf32" else "")
+                                       if dk["bound"] == "tensor" else
+                                       f"128 FP32 lanes x {props.multi_processor_count} SMs x "
+                                       f"{max_mhz} MHz x 2"),
+                         "timed": "CUDA events recorded by the library around each launch "
+                                  "on the launching stream (esom_set_timing)",
+                         "kernels": kernels,
+                         "step": {"achieved": achieved, "peak": step_peak,
+                                  "frac": achieved / step_peak,
+                                  "frac_of_fp32_alu_peak": achieved / alu_peak,
+                                  "algorithmic": "2 n (L d + k^2 d) flops per step"},
+                         "frac_at_sampled_clock": (dk["frac"] * max_mhz / clocks["sm_mhz"])
                          if clocks.get("sm_mhz") else None,
                          # work the FMA count omits: one screening compare per
                          # (point, landmark), the pairs u < v of the scored
                          # neighbours
                          "selection_compares_per_step": n * L,
-                         "pairs_per_step": n * (k - 1) * (k - 2) // 2,
-                         # the k-NN passes alone (CUDA events on the launching
-                         # stream): the dominant kernels of a split plan
-                         "dominant": ({"kernel": "fused_kernel", "ms": float(np.mean(step_ms)),
-                                       "share_of_step": 1.0} if screen == "fused" else
-                                      {"kernel": ("tc_kernel + rescan_kernel (k-NN passes)"
-                                                  if screen in ("tf32", "bf16") else
-                                                  "fused_kernel in k-NN mode + rescan_kernel"),
-                                       "ms": float(np.median(knn_ms)),
-                                       "share_of_step": float(np.median(knn_ms))
-                                       / float(np.median(step_ms))})},
+                         "pairs_per_step": n * (k - 1) * (k - 2) // 2},
             "clocks": clocks,
             "e2e": {"value": sharding.job_throughput(n, world, args.steps, e2e_s),
                     "unit": "points/s",
@@ -489,10 +531,66 @@ def run_esom(args, world, rank, local):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_seconds)
-        print(json.dumps(line), flush=True)
     P.close()
+    if rank == 0:
+        if world == 1 and args.workload == WORKLOAD and not args.no_secondary:
+            # the other named workloads in the same run: the screened path
+            # against plain FP32 at n = 1e7, d = 32, and the frame server
+            del X, out, flush
+            torch.cuda.empty_cache()
+            line["secondary"] = {"student50_d32": secondary_student50(args, dev),
+                                 "serve8": run_serve(args, emit=False)}
+        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def secondary_student50(args, dev):
+    """student50_d32 (n = 1e7, d = 32, L = 4096, k = 30): the autotuned
+    screened plan against the plain FP32 plans on the same points (same
+    bits), CUDA events, L2 flushed between steps."""
+    import torch
+
+    from paper_2201_00701_gb300 import binding, workloads
+
+    w = workloads.student50_d32(n=10_000_000)
+    X = torch.from_numpy(w.X).to(dev)
+    out = torch.empty((w.n, 2), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    res = {"n": w.n, "d": w.d, "L": w.L, "k": w.k, "plans_ms": {}, "rescan_fraction": {}}
+    with binding.Projector(w.d, w.L, w.k) as P:
+        P.set_landmarks(torch.from_numpy(w.hi).to(dev), torch.from_numpy(w.lo).to(dev))
+        best = binding.PLAN_NAMES[P.tune(X, w.boost, w.adjust)]
+        for plan in dict.fromkeys([best, "tf32", "bf16", "fused", "split"]):
+            P.set_plan({"fused": binding.ESOM_PLAN_FUSED, "split": binding.ESOM_PLAN_SPLIT,
+                        "tf32": binding.ESOM_PLAN_TF32, "bf16": binding.ESOM_PLAN_BF16}[plan])
+            ts = []
+            for i in range(3 + 3):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                P.project(X, w.boost, w.adjust, out=out)
+                e1.record()
+                e1.synchronize()
+                if i == 2:
+                    P.stats(reset=True)
+                if i >= 3:
+                    ts.append(e0.elapsed_time(e1))
+            st = P.stats(reset=True)
+            res["plans_ms"][plan] = float(np.median(ts))
+            res["rescan_fraction"][plan] = st["rescans"] / max(st["points"], 1)
+            if P.device_status() != 0:
+                raise RuntimeError("device status flag raised (student50_d32)")
+    fp32 = min(res["plans_ms"]["fused"], res["plans_ms"]["split"])
+    res["plan"] = best
+    res["points_per_s"] = w.n / (res["plans_ms"][best] / 1e3)
+    res["screened_speedup_vs_fp32"] = fp32 / res["plans_ms"][best]
+    # 2 n (L d + k^2 d) flops against the FP32 lanes' peak
+    alu = 2.0 * 128 * torch.cuda.get_device_properties(dev).multi_processor_count * 2070e6
+    res["frac_of_fp32_alu_peak"] = (2.0 * w.n * (w.L * w.d + w.k * w.k * w.d)
+                                    / (res["plans_ms"][best] / 1e3) / alu)
+    return res
 
 
 def run_batch64(args):
@@ -572,7 +670,7 @@ def run_batch64(args):
         P.close()
 
 
-def run_serve(args):
+def run_serve(args, emit=True):
     """--workload serve8: the frame server with 8 resident sessions (d=24,
     k=20, n in {2e5, 1e6, 5e6}, L in {256, 1024}); each frame is one SOM step
     on a 4096-point minibatch plus a reprojection of the session's points.
@@ -666,8 +764,12 @@ def run_serve(args):
         "clocks": sampler.summary(),
         "gpu_launches": 4 * len(recs),
     }
-    print(json.dumps(line), flush=True)
     srv.close()
+    if emit:
+        print(json.dumps(line), flush=True)
+    return {key: line[key] for key in ("value", "unit", "latency_ms", "offered_points_per_s",
+                                       "frames", "projections", "frames_per_s", "sessions",
+                                       "clocks")} | {"config": line["config"]}
 
 
 def main():
@@ -684,6 +786,8 @@ def main():
     ap.add_argument("--ref-points", type=int, default=4000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the student50_d32 and serve8 summaries of the default run")
     ap.add_argument("--no-ablations", action="store_true",
                     help="skip timing the paper's alternative kernels")
     ap.add_argument("--workload", default=WORKLOAD,

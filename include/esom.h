@@ -135,6 +135,32 @@ typedef struct {
  * esom_create or the last reset; reset != 0 zeroes them afterwards. */
 esom_status esom_get_stats(esom_handle h, esom_stream_t stream, esom_stats *out, int reset);
 
+/* Kernel timing, for measurement (no counterpart in the paper).  With
+ * esom_set_timing(h, 1) the handle brackets every kernel it launches for
+ * esom_project, esom_project_host and esom_knn with CUDA events on the
+ * launching stream (allocated on the first call: 2 x 256 events) and adds
+ * each kernel's duration to the total of its kind; esom_get_timing waits for
+ * `stream` and returns the totals (reset != 0 zeroes them).  Timing adds one
+ * event record on each side of every kernel; it is off by default.
+ * Errors: ESOM_EINVAL, ESOM_ECUDA. */
+#define ESOM_KERNEL_ORDER 0          /* spatial order of the points (two kernels) */
+#define ESOM_KERNEL_TC_KNN 1         /* tensor-core screened k-NN */
+#define ESOM_KERNEL_RERANK_PROJECT 2 /* exact re-rank + projection (tensor-core plans) */
+#define ESOM_KERNEL_RERANK 3         /* exact re-rank alone (esom_knn, tensor-core plans) */
+#define ESOM_KERNEL_RESCAN 4         /* exact rescan of points whose certificate failed */
+#define ESOM_KERNEL_PROJECT 5        /* projection from given neighbours */
+#define ESOM_KERNEL_REFINE 6         /* FP64 recomputation of ill-conditioned points */
+#define ESOM_KERNEL_FUSED 7          /* plain FP32 kernel (fused plan, or the split
+                                        plan's k-NN) */
+#define ESOM_KERNEL_KINDS 8
+typedef struct {
+    uint64_t launches[ESOM_KERNEL_KINDS];
+    double ms[ESOM_KERNEL_KINDS];
+} esom_kernel_times;
+esom_status esom_set_timing(esom_handle h, int on);
+esom_status esom_get_timing(esom_handle h, esom_stream_t stream, esom_kernel_times *out,
+                            int reset);
+
 /* Forces the number of landmarks per shared-memory chunk (0 restores the
  * automatic choice: all landmarks resident when L*d*4 <= 64 KiB, otherwise
  * 32 KiB chunks streamed through two buffers).  Lets tests drive the

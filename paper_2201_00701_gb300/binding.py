@@ -53,6 +53,16 @@ class _Stats(ctypes.Structure):
                 ("refines", ctypes.c_uint64), ("launches", ctypes.c_uint64)]
 
 
+ESOM_KERNEL_KINDS = 8
+KERNEL_NAMES = ["order", "tc_knn", "rerank_project", "rerank", "rescan", "project", "refine",
+                "fused"]
+
+
+class _KernelTimes(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * ESOM_KERNEL_KINDS),
+                ("ms", ctypes.c_double * ESOM_KERNEL_KINDS)]
+
+
 class BatchItem(ctypes.Structure):
     _fields_ = [("landmarks", ctypes.c_void_p), ("points", ctypes.c_void_p),
                 ("n", ctypes.c_int64), ("out", ctypes.c_void_p),
@@ -111,6 +121,8 @@ def load(build_if_missing: bool = False):
         "esom_get_config": ([P, ctypes.POINTER(_Config)], I),
         "esom_project_noalloc": ([P, I64, P, P, I, I, I, P, F, F, P], I),
         "esom_get_stats": ([P, P, ctypes.POINTER(_Stats), I], I),
+        "esom_set_timing": ([P, I], I),
+        "esom_get_timing": ([P, P, ctypes.POINTER(_KernelTimes), I], I),
         "esom_set_screening": ([P, I, P], I),
         "esom_set_split": ([P, I], I),
         "esom_set_centering": ([P, I], I),
@@ -221,6 +233,18 @@ def esom_get_stats(h, stream: int = 0, reset: bool = False):
     st = load().esom_get_stats(h, stream, ctypes.byref(st_), int(reset))
     return st, {"points": int(st_.points), "rescans": int(st_.rescans),
                 "refines": int(st_.refines), "launches": int(st_.launches)}
+
+
+def esom_set_timing(h, on: bool) -> int:
+    return load().esom_set_timing(h, int(on))
+
+
+def esom_get_timing(h, stream: int = 0, reset: bool = False):
+    """Returns (status, {kernel kind: (launches, total ms)})."""
+    t = _KernelTimes()
+    st = load().esom_get_timing(h, stream, ctypes.byref(t), int(reset))
+    return st, {name: (int(t.launches[i]), float(t.ms[i]))
+                for i, name in enumerate(KERNEL_NAMES)}
 
 
 def esom_set_screening(h, mode: int, stream: int = 0) -> int:
@@ -485,6 +509,16 @@ class Projector:
         check(st)
         return out
 
+    def set_timing(self, on: bool):
+        """Per-kernel CUDA-event timing of this handle's launches (off by default)."""
+        check(esom_set_timing(self.h, on))
+
+    def timing(self, reset: bool = False) -> dict:
+        """{kernel kind: (launches, total ms)} since the last reset."""
+        st, out = esom_get_timing(self.h, self._stream(), reset)
+        check(st)
+        return out
+
     def set_screening(self, mode: int):
         """ESOM_SCREEN_FP32 or ESOM_SCREEN_TF32; same results, different speed."""
         check(esom_set_screening(self.h, mode, self._stream()))
@@ -571,6 +605,16 @@ class Server:
 
     def set_coalescing(self, on: bool):
         check(esom_server_set_coalescing(self.s, on))
+
+    def set_timing(self, on: bool):
+        """Per-kernel CUDA-event timing of this handle's launches (off by default)."""
+        check(esom_set_timing(self.h, on))
+
+    def timing(self, reset: bool = False) -> dict:
+        """{kernel kind: (launches, total ms)} since the last reset."""
+        st, out = esom_get_timing(self.h, self._stream(), reset)
+        check(st)
+        return out
 
     def set_screening(self, mode: int):
         check(esom_server_set_screening(self.s, mode))

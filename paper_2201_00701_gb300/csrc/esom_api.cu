@@ -289,6 +289,37 @@ esom_status check_device(const esom_ctx *h) {
 // table, 1 squared-distance table, 2 neither).
 int proj_mode(const esom_ctx *h) { return h->ptab ? 0 : h->qtab ? 1 : 2; }
 
+// Kernel timing (esom_set_timing): CUDA events on the launching stream
+// around each kernel, folded into per-kind totals when the ring of event
+// pairs fills or when the totals are read.
+void time_fold(esom_ctx *h) {
+    for (int i = 0; i < h->tcount; ++i) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(h->tev[i][1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, h->tev[i][0], h->tev[i][1]) == cudaSuccess) {
+            h->tms[h->tkind[i]] += ms;
+            h->tlaunch[h->tkind[i]] += 1;
+        }
+    }
+    h->tcount = 0;
+}
+
+struct KernelTimer {
+    esom_ctx *h;
+    cudaStream_t st;
+    int slot = -1;
+    KernelTimer(esom_ctx *h_, int kind, cudaStream_t s) : h(h_), st(s) {
+        if (!h->timing) return;
+        if (h->tcount == esom_ctx::kTimed) time_fold(h);
+        slot = h->tcount++;
+        h->tkind[slot] = kind;
+        cudaEventRecord(h->tev[slot][0], st);
+    }
+    ~KernelTimer() {
+        if (slot >= 0) cudaEventRecord(h->tev[slot][1], st);
+    }
+};
+
 // Projection from given neighbours by the library's kernel (one thread per
 // point, distance table), the launch the split path makes after its k-NN.
 // The FP64 recomputation of the rows the projection just listed (one warp a
@@ -317,9 +348,13 @@ esom_status launch_projection(esom_ctx *h, FusedArgs p0, cudaStream_t stream) {
             p.ntiles = (p.n + esom::proj_threads(pm) - 1) / esom::proj_threads(pm);
             long long grid = (long long)h->proj_blocks_per_sm * h->num_sms;
             if (grid > p.ntiles) grid = p.ntiles;
+            KernelTimer kt(h, ESOM_KERNEL_PROJECT, stream);
             e = h->ops->launch_proj[pm](p, (int)grid, h->proj_smem, stream);
         }
-        if (e == cudaSuccess) e = launch_refine(h, p, stream);
+        if (e == cudaSuccess) {
+            KernelTimer kt(h, ESOM_KERNEL_REFINE, stream);
+            e = launch_refine(h, p, stream);
+        }
         h->launches += 2;
         if (e != cudaSuccess) return cuda_fail(e, "projection kernel launch");
     }
@@ -359,6 +394,7 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                 t.m_dot = esom::tc_dot_bound(h->d, tc_prec(h->screening));
                 t.cand = h->cand;
                 if (h->order_on) {
+                    KernelTimer kt(h, ESOM_KERNEL_ORDER, stream);
                     r = esom::launch_point_order(k.X, cnt, h->d, h->centers,
                                                  (h->L + esom::kTcN - 1) / esom::kTcN, k.center,
                                                  h->home, h->counts, esom::kOrderBlocks, h->perm,
@@ -374,7 +410,10 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                 const long long tiles = (cnt + esom::kTcRows - 1) / esom::kTcRows;
                 long long grid = (long long)h->tc_blocks_per_sm * h->num_sms;
                 if (grid > tiles) grid = tiles;
-                r = h->tc->launch(t, (int)grid, h->tc_smem, stream);
+                {
+                    KernelTimer kt(h, ESOM_KERNEL_TC_KNN, stream);
+                    r = h->tc->launch(t, (int)grid, h->tc_smem, stream);
+                }
                 if (r != cudaSuccess) return r;
                 ++h->launches;
                 if (proj_out) {
@@ -387,9 +426,15 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                         (cnt + esom::proj_threads(pm) - 1) / esom::proj_threads(pm);
                     long long pgrid = (long long)h->rproj_blocks_per_sm * h->num_sms;
                     if (pgrid > ptiles) pgrid = ptiles;
-                    r = h->ops->launch_rproj[pm](rp, (int)pgrid, h->proj_smem, stream);
+                    {
+                        KernelTimer kt(h, ESOM_KERNEL_RERANK_PROJECT, stream);
+                        r = h->ops->launch_rproj[pm](rp, (int)pgrid, h->proj_smem, stream);
+                    }
                     if (r != cudaSuccess) return r;
-                    r = h->ops->launch_rescan(k, 2 * h->num_sms, stream);
+                    {
+                        KernelTimer kt(h, ESOM_KERNEL_RESCAN, stream);
+                        r = h->ops->launch_rescan(k, 2 * h->num_sms, stream);
+                    }
                     if (r != cudaSuccess) return r;
                     // the failed points, from their rescanned neighbours
                     FusedArgs pf = k;
@@ -398,9 +443,13 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                     pf.perm = nullptr;
                     pf.rows_list = h->fail_list;
                     pf.rows_count = fail_count;
-                    r = h->ops->launch_proj[pm](pf, h->num_sms, h->proj_smem, stream);
+                    {
+                        KernelTimer kt(h, ESOM_KERNEL_PROJECT, stream);
+                        r = h->ops->launch_proj[pm](pf, h->num_sms, h->proj_smem, stream);
+                    }
                     if (r != cudaSuccess) return r;
                     h->launches += 4;  // re-rank + projection, rescan, projection, refine
+                    KernelTimer kt(h, ESOM_KERNEL_REFINE, stream);
                     return launch_refine(h, pf, stream);
                 }
                 FusedArgs rr = t;
@@ -409,17 +458,20 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
                 const long long rtiles = (cnt + esom::kThreads - 1) / esom::kThreads;
                 long long rgrid = (long long)h->rerank_blocks_per_sm * h->num_sms;
                 if (rgrid > rtiles) rgrid = rtiles;
+                KernelTimer kt(h, ESOM_KERNEL_RERANK, stream);
                 r = h->ops->launch_rerank(rr, (int)rgrid, h->rerank_smem, stream);
                 ++h->launches;
             } else {
                 k.ntiles = (cnt + esom::kThreads - 1) / esom::kThreads;
                 long long grid = (long long)h->blocks_per_sm * h->num_sms;
                 if (grid > k.ntiles) grid = k.ntiles;
+                KernelTimer kt(h, ESOM_KERNEL_FUSED, stream);
                 r = h->ops->launch(k, (int)grid, h->smem, stream);
                 ++h->launches;
             }
             if (r != cudaSuccess) return r;
             ++h->launches;
+            KernelTimer kt(h, ESOM_KERNEL_RESCAN, stream);
             return h->ops->launch_rescan(k, 2 * h->num_sms, stream);
         };
         if (mode == esom::kKnn) {
@@ -480,8 +532,14 @@ esom_status launch(esom_ctx *h, const float *points, long long n, float *out, in
             f.stall_ns = h->stall_ns;
             h->stall_ns = 0;
             if (mode == esom::kProject) e = cudaMemsetAsync(rcount, 0, sizeof(unsigned), stream);
-            if (e == cudaSuccess) e = h->ops->launch(f, (int)grid, h->smem, stream);
-            if (e == cudaSuccess && mode == esom::kProject) e = launch_refine(h, f, stream);
+            if (e == cudaSuccess) {
+                KernelTimer kt(h, ESOM_KERNEL_FUSED, stream);
+                e = h->ops->launch(f, (int)grid, h->smem, stream);
+            }
+            if (e == cudaSuccess && mode == esom::kProject) {
+                KernelTimer kt(h, ESOM_KERNEL_REFINE, stream);
+                e = launch_refine(h, f, stream);
+            }
             h->launches += mode == esom::kProject ? 2 : 1;
         }
     }
@@ -722,6 +780,40 @@ esom_status esom_get_stats(esom_handle h, esom_stream_t stream, esom_stats *out,
         if (e == cudaSuccess) e = cudaMemset(h->status + 5, 0, sizeof(unsigned));
         if (e != cudaSuccess) return cuda_fail(e, "stats reset");
         h->points = 0;
+    }
+    return ESOM_OK;
+}
+
+esom_status esom_set_timing(esom_handle h, int on) {
+    if (!h) return fail(ESOM_EINVAL, "null handle");
+    esom_status s = check_device(h);
+    if (s != ESOM_OK) return s;
+    if (on && !h->tev[0][0]) {
+        for (int i = 0; i < esom_ctx::kTimed; ++i)
+            for (int j = 0; j < 2; ++j) {
+                const cudaError_t e = cudaEventCreate(&h->tev[i][j]);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate (kernel timing)");
+            }
+    }
+    h->timing = on ? 1 : 0;
+    return ESOM_OK;
+}
+
+esom_status esom_get_timing(esom_handle h, esom_stream_t stream, esom_kernel_times *out,
+                            int reset) {
+    if (!h || !out) return fail(ESOM_EINVAL, "null argument");
+    esom_status s = check_device(h);
+    if (s != ESOM_OK) return s;
+    const cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    time_fold(h);
+    for (int i = 0; i < ESOM_KERNEL_KINDS; ++i) {
+        out->launches[i] = h->tlaunch[i];
+        out->ms[i] = h->tms[i];
+        if (reset) {
+            h->tlaunch[i] = 0;
+            h->tms[i] = 0.0;
+        }
     }
     return ESOM_OK;
 }
@@ -1104,6 +1196,9 @@ esom_status esom_destroy(esom_handle h) {
     cudaFree(h->img);
     cudaFree(h->qtab);
     cudaFree(h->ptab);
+    for (int i = 0; i < esom_ctx::kTimed; ++i)
+        for (int j = 0; j < 2; ++j)
+            if (h->tev[i][j]) cudaEventDestroy(h->tev[i][j]);
     cudaFree(h->tc_idx);
     cudaFree(h->tc_d2);
     cudaFree(h->fail_list);

@@ -6,6 +6,7 @@
 
 #include <mutex>
 
+#include "esom.h"
 #include "esom_kernels.h"
 
 struct esom_ctx {
@@ -31,6 +32,14 @@ struct esom_ctx {
     unsigned long long stall_ns = 0;
     uint64_t points = 0;   // points handed to the kernels since the last stats reset
     uint64_t launches = 0; // kernels launched for esom_project / esom_knn since then
+    // kernel timing (esom_set_timing): a ring of event pairs on the launching
+    // stream, the kind of kernel of each, per-kind totals
+    static constexpr int kTimed = 256;
+    int timing = 0, tcount = 0;
+    cudaEvent_t tev[kTimed][2] = {};
+    int tkind[kTimed] = {};
+    double tms[ESOM_KERNEL_KINDS] = {};
+    uint64_t tlaunch[ESOM_KERNEL_KINDS] = {};
     // launch configuration (derived from L, d and the chunk choice)
     int chunk = 0, nchunks = 0, blocks_per_sm = 0;
     size_t smem = 0;

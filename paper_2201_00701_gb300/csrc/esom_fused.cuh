@@ -1442,7 +1442,7 @@ __device__ __forceinline__ void project_tiles(const FusedArgs &a, const float2 *
 }
 
 template <int D, int KC, int MODE>
-__global__ void __launch_bounds__(proj_threads(MODE), proj_min_blocks(MODE)) project_kernel(const FusedArgs a) {
+__global__ void __launch_bounds__(proj_threads(MODE), proj_min_blocks(KC)) project_kernel(const FusedArgs a) {
     constexpr int KK = KC - 4;
     constexpr int NT = proj_threads(MODE);
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1581,7 +1581,7 @@ cudaError_t launch_rerank(const FusedArgs &a, int grid, size_t smem, cudaStream_
 // fails goes to a.fail_list; rescan_kernel and the projection kernel over
 // that list finish it.
 template <int D, int KC, int MODE>
-__global__ void __launch_bounds__(proj_threads(MODE), proj_min_blocks(MODE))
+__global__ void __launch_bounds__(proj_threads(MODE), proj_min_blocks(KC))
     rerank_project_kernel(const FusedArgs a) {
     constexpr int KK = KC - 4;
     constexpr int NT = proj_threads(MODE);

@@ -155,10 +155,12 @@ constexpr int kPtabMaxL = 2048;
 constexpr int kQtabMaxL = 4096;
 
 // Threads (= points) per block of the projection kernels, and the resident
-// blocks per SM they are compiled for.
+// blocks per SM they are compiled for (list capacity kc: five blocks, at most
+// 102 registers a thread, up to k = 20; four above, where the lists need
+// more registers).
 constexpr int kProjThreads = 128;
 __host__ __device__ constexpr int proj_threads(int) { return kProjThreads; }
-__host__ __device__ constexpr int proj_min_blocks(int) { return 4; }
+__host__ __device__ constexpr int proj_min_blocks(int kc) { return kc <= 24 ? 5 : 4; }
 
 
 // ---------------------------------------------------------------------------

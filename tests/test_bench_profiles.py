@@ -21,9 +21,9 @@ def read_kv(path):
     return kv
 
 
-@pytest.mark.parametrize("plan", sorted(bench.PROFILES))
-def test_profiles_parse_and_scale(plan):
-    kv = read_kv(bench.PROFILES[plan])
+@pytest.mark.parametrize("key", sorted(bench.PROFILES))
+def test_profiles_parse_and_scale(key):
+    kv = read_kv(bench.PROFILES[key])
     per_capture = float(kv["dram_bytes_per_launch_capture"])
     capture_n = float(kv["capture_n"])
     full = float(kv["dram_bytes_per_launch_full"])
@@ -34,13 +34,13 @@ def test_profiles_parse_and_scale(plan):
 
 def test_traffic_only_on_the_captured_sources(monkeypatch):
     h = bench.kernel_source_hash()
-    fresh = {p: read_kv(path)["source_hash"] == h for p, path in bench.PROFILES.items()}
-    for plan, ok in fresh.items():
-        got = bench.profile_traffic(plan)
+    fresh = {key: read_kv(path)["source_hash"] == h for key, path in bench.PROFILES.items()}
+    for key, ok in fresh.items():
+        got = bench.profile_traffic(*key)
         assert (got is not None) == ok
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
-    for plan in bench.PROFILES:
-        assert bench.profile_traffic(plan) is None
+    for key in bench.PROFILES:
+        assert bench.profile_traffic(*key) is None
 
 
 def test_hash_covers_the_profiled_kernel_sources():
