@@ -474,21 +474,32 @@ __device__ __noinline__ void repair_order(float *cdp, int *cip) {
 // Exact re-rank of the screened list.  On return ed/ei hold the KK nearest
 // listed candidates by (FP32 difference-form distance, index); returns false
 // if the screening certificate fails (then the caller rescans).
-template <int D, int KC, int KK>
-__device__ __forceinline__ bool rerank(const float4 (&x)[D / 4], const float (&keys)[KC],
-                                       const float4 *Lg, uint32_t mask, int L, int k, float M,
-                                       float q, float (&ed)[KK], int (&ei)[KK],
-                                       float koff = 0.f, const int *lperm = nullptr) {
+// The keys come four at a time from key4(g) (keys 4g .. 4g + 3, ascending),
+// so a caller can stream them from memory instead of holding all KC.
+template <int D, int KC, int KK, class KEY4>
+__device__ __forceinline__ bool rerank_keys(const float4 (&x)[D / 4], const KEY4 &key4,
+                                            const float4 *Lg, uint32_t mask, int L, int k,
+                                            float M, float q, float (&ed)[KK], int (&ei)[KK],
+                                            float koff = 0.f, const int *lperm = nullptr) {
+    static_assert(KC % 4 == 0, "list capacity is a multiple of 4");
     float cd[KC];
     int ci[KC];
+    float last = INFINITY;
 #pragma unroll
-    for (int t = 0; t < KC; ++t) {
-        const bool valid = keys[t] < INFINITY;
-        // (the min() only guards the row read; listed keys carry indices < L)
-        const int j = valid ? min((int)(__float_as_uint(keys[t]) & mask), L - 1) : 0;
-        // keys of a reordered screening carry internal positions
-        ci[t] = lperm ? __ldg(lperm + j) : j;
-        cd[t] = valid ? dist2_row<D>(x, Lg, ci[t]) : INFINITY;
+    for (int g = 0; g < KC / 4; ++g) {
+        const float4 k4 = key4(g);
+        const float kk[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int t = 4 * g + e;
+            const bool valid = kk[e] < INFINITY;
+            // (the min() only guards the row read; listed keys carry indices < L)
+            const int j = valid ? min((int)(__float_as_uint(kk[e]) & mask), L - 1) : 0;
+            // keys of a reordered screening carry internal positions
+            ci[t] = lperm ? __ldg(lperm + j) : j;
+            cd[t] = valid ? dist2_row<D>(x, Lg, ci[t]) : INFINITY;
+        }
+        if (g == KC / 4 - 1) last = k4.w;
     }
     // The screened order is the exact order except near ties; when it is
     // not, repair it (rare, out of line).
@@ -520,10 +531,22 @@ __device__ __forceinline__ bool rerank(const float4 (&x)[D / 4], const float (&k
     // never queued, which push_threshold covers), so its exact distance is at
     // least last - 2q|last| - M.  Keys may be offset from distances by a
     // constant koff of the point (key = distance - koff, up to M).
-    const float last = keys[KC - 1];
     if (!(last < INFINITY)) return true;
     const float exact_k = at<KC>(cd, k - 1);
     return last - 2.f * q * fabsf(last) - M > exact_k - koff;
+}
+
+template <int D, int KC, int KK>
+__device__ __forceinline__ bool rerank(const float4 (&x)[D / 4], const float (&keys)[KC],
+                                       const float4 *Lg, uint32_t mask, int L, int k, float M,
+                                       float q, float (&ed)[KK], int (&ei)[KK],
+                                       float koff = 0.f, const int *lperm = nullptr) {
+    return rerank_keys<D, KC, KK>(
+        x,
+        [&](int g) {
+            return make_float4(keys[4 * g], keys[4 * g + 1], keys[4 * g + 2], keys[4 * g + 3]);
+        },
+        Lg, mask, L, k, M, q, ed, ei, koff, lperm);
 }
 
 // Neighbour indices parked in this thread's own column of the queue buffer
@@ -1616,21 +1639,17 @@ __global__ void __launch_bounds__(proj_threads(MODE), proj_min_blocks(KC))
         const float xn = sqrtf(xx);
         const float sx = xn + lmax;
         const float M = a.m_dot * xn * lmax + 2.f * kGamma * sx * sx;
-        float keys[KC];
+        // the screened keys streamed four at a time (not all KC live at once)
         const float4 *cp = reinterpret_cast<const float4 *>(a.cand + (active ? pos : 0) * KC);
-#pragma unroll
-        for (int t = 0; t < KC; t += 4) {
-            const float4 v = active ? ldg_stream(cp + t / 4)
-                                    : make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
-            keys[t] = v.x;
-            keys[t + 1] = v.y;
-            keys[t + 2] = v.z;
-            keys[t + 3] = v.w;
-        }
         float sd[KK];
         int si[KK];
-        const bool cert = rerank<D, KC, KK>(xr, keys, Lg, a.key_mask, a.L, a.k, M, a.key_quant,
-                                            sd, si, xx, a.lperm);
+        const bool cert = rerank_keys<D, KC, KK>(
+            xr,
+            [&](int g) {
+                return active ? ldg_stream(cp + g)
+                              : make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+            },
+            Lg, a.key_mask, a.L, a.k, M, a.key_quant, sd, si, xx, a.lperm);
         if (active && __builtin_expect(!cert, 0)) {
             atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
             a.fail_list[atomicAdd(a.fail_count, 1u)] = row;
@@ -1710,6 +1729,10 @@ __device__ __forceinline__ unsigned long long warp_pop(unsigned long long (&best
     return m;
 }
 
+// Landmarks per shared-memory chunk of the rescan kernel's warp-per-point
+// mode (a multiple of 8: rows keep their chunk swizzle).
+constexpr int kRescanChunk = 64;
+
 template <int D, int KC>
 __global__ void __launch_bounds__(256) rescan_kernel(const FusedArgs a) {
     constexpr int KK = KC - 4;
@@ -1754,15 +1777,48 @@ __global__ void __launch_bounds__(256) rescan_kernel(const FusedArgs a) {
         }
         return;
     }
-    // warp per point
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < (long long)count;
-         w += nwarps) {
-        const long long row = a.fail_list[w];
+    // warp per point, the block's eight points at a time sharing each chunk
+    // of landmark rows staged in shared memory (eight times fewer row reads
+    // from L2 than each warp reading all L rows itself)
+    __shared__ __align__(16) float4 s_rows[kRescanChunk * D / 4];
+    const long long ngroups = ((long long)count + kWarps - 1) / kWarps;
+    for (long long gq = blockIdx.x; gq < ngroups; gq += gridDim.x) {
+        const long long w = gq * kWarps + warp;
+        const bool act = w < (long long)count;
+        const long long row = act ? a.fail_list[w] : 0;
         const float4 *xp = reinterpret_cast<const float4 *>(a.X) + row * (D / 4);
 #pragma unroll
-        for (int e = 0; e < D / 4; ++e) x[e] = centred(__ldg(xp + e), a.center, e);
-        rescan_scan<D, KK>(x, Lg, a.L, lane, 32, best);
+        for (int e = 0; e < D / 4; ++e)
+            x[e] = act ? centred(__ldg(xp + e), a.center, e) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int t = 0; t < KK; ++t) best[t] = ~0ull;
+        for (int c0 = 0; c0 < a.L; c0 += kRescanChunk) {
+            const int cnt = a.L - c0 < kRescanChunk ? a.L - c0 : kRescanChunk;
+            __syncthreads();  // the previous chunk is consumed
+            for (int i = threadIdx.x; i < cnt * (D / 4); i += blockDim.x)
+                s_rows[i] = __ldg(Lg + (size_t)c0 * (D / 4) + i);
+            __syncthreads();
+            // c0 is a multiple of 8, so a row keeps its chunk swizzle (swz
+            // depends on the landmark index mod 8) and dist2_row gives the
+            // same distance as from the global rows
+            if (act)
+                for (int j = lane; j < cnt; j += 32) {
+                    const float d2 = dist2_row<D>(x, s_rows, j);
+                    const unsigned long long key =
+                        ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)(c0 + j);
+                    if (key < best[KK - 1]) {
+                        unsigned long long prev = best[0];
+                        best[0] = umin64(key, best[0]);
+#pragma unroll
+                        for (int t = 1; t < KK; ++t) {
+                            const unsigned long long cur = best[t];
+                            best[t] = umax64(prev, umin64(key, cur));
+                            prev = cur;
+                        }
+                    }
+                }
+        }
+        if (!act) continue;
         for (int r = 0; r < a.k; ++r) {
             const unsigned long long m = warp_pop<KK>(best);
             if (lane == 0) {
