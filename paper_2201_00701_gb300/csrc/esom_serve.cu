@@ -26,6 +26,7 @@
 
 #include "esom.h"
 #include "esom_ctx.h"
+#include "esom_fused.cuh"
 #include "esom_kernels.h"
 
 namespace {
@@ -114,6 +115,64 @@ cudaError_t som_dispatch(int d, float *hi, const float *lo, int L, const float *
     }
 }
 
+// Best-matching landmark of each minibatch point: the nearest landmark by
+// the exact FP32 difference-form distance of the projection kernels
+// (dist2_row on the handle's rows, centred like theirs), ties to the lower
+// index -- the first column esom_knn returns, in one launch instead of a
+// k-NN pass.  One thread per point; the block streams the rows through
+// shared memory in chunks of 64 (a multiple of 8, so each row keeps its
+// chunk swizzle).
+constexpr int kBmuThreads = 256;
+constexpr int kBmuChunk = 64;
+
+template <int D>
+__global__ void __launch_bounds__(kBmuThreads) bmu_kernel(const float *__restrict__ X, int b,
+                                                          const float *__restrict__ hi, int L,
+                                                          const float *__restrict__ center,
+                                                          int *__restrict__ bmu) {
+    __shared__ __align__(16) float4 rows[kBmuChunk * D / 4];
+    const int p = blockIdx.x * kBmuThreads + threadIdx.x;
+    const bool act = p < b;
+    float4 x[D / 4];
+    const float4 *xp = reinterpret_cast<const float4 *>(X) + (size_t)(act ? p : 0) * (D / 4);
+#pragma unroll
+    for (int e = 0; e < D / 4; ++e) x[e] = esom::centred(__ldg(xp + e), center, e);
+    const float4 *Lg = reinterpret_cast<const float4 *>(hi);
+    float best = INFINITY;
+    int bi = 0;
+    for (int c0 = 0; c0 < L; c0 += kBmuChunk) {
+        const int cnt = L - c0 < kBmuChunk ? L - c0 : kBmuChunk;
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt * (D / 4); i += kBmuThreads)
+            rows[i] = __ldg(Lg + (size_t)c0 * (D / 4) + i);
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            const float d2 = esom::dist2_row<D>(x, rows, j);
+            if (d2 < best) {
+                best = d2;
+                bi = c0 + j;
+            }
+        }
+    }
+    if (act) bmu[p] = bi;
+}
+
+cudaError_t bmu_dispatch(int d, const float *X, int b, const float *hi, int L, const float *center,
+                         int *bmu, cudaStream_t st) {
+    const int blocks = (b + kBmuThreads - 1) / kBmuThreads;
+    switch (d) {
+#define ESOM_BMU_CASE(DV) \
+    case DV: bmu_kernel<DV><<<blocks, kBmuThreads, 0, st>>>(X, b, hi, L, center, bmu); break;
+        ESOM_BMU_CASE(4) ESOM_BMU_CASE(8) ESOM_BMU_CASE(12) ESOM_BMU_CASE(16)
+        ESOM_BMU_CASE(20) ESOM_BMU_CASE(24) ESOM_BMU_CASE(28) ESOM_BMU_CASE(32)
+        ESOM_BMU_CASE(36) ESOM_BMU_CASE(40) ESOM_BMU_CASE(44) ESOM_BMU_CASE(48)
+        ESOM_BMU_CASE(52) ESOM_BMU_CASE(56) ESOM_BMU_CASE(60) ESOM_BMU_CASE(64)
+#undef ESOM_BMU_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // Counter-based choice of the minibatch window of frame f (splitmix64).
 uint64_t mix64(uint64_t z) {
     z += 0x9e3779b97f4a7c15ull;
@@ -174,10 +233,12 @@ esom_status som_frame_step(Session &ss, const Frame &f) {
         const int64_t b = d.minibatch < d.n ? d.minibatch : d.n;
         const uint64_t span = (uint64_t)(d.n - b) + 1;
         const int64_t off = (int64_t)(mix64(d.seed ^ (f.id * 0x100000001b3ull)) % span);
-        r = esom_knn(ss.h, ss.points + off * d.d, b, ss.bmu, nullptr, est);
-        if (r != ESOM_OK) return r;
-        cudaError_t e = som_dispatch(d.d, ss.hi, ss.lo, d.L, ss.points + off * d.d, ss.bmu, d.k,
-                                     (int)b, d.alpha, d.sigma, st);
+        // best-matching landmarks of the window (esom_knn's first column)
+        cudaError_t e = bmu_dispatch(d.d, ss.points + off * d.d, (int)b, ss.h->hi, d.L,
+                                     ss.h->centered ? ss.h->center : nullptr, ss.bmu, st);
+        if (e != cudaSuccess) return scuda(e, "best-matching landmarks");
+        e = som_dispatch(d.d, ss.hi, ss.lo, d.L, ss.points + off * d.d, ss.bmu, 1, (int)b,
+                         d.alpha, d.sigma, st);
         if (e != cudaSuccess) return scuda(e, "SOM update");
         r = esom_set_landmarks(ss.h, ss.hi, ss.lo, est);
         if (r != ESOM_OK) return r;

@@ -215,6 +215,31 @@ def test_served_frames_equal_manual_steps_and_oracle(esom):
     report(stats, f"served frame {frames}")
 
 
+def test_served_trajectory_against_oracle_only(esom):
+    """Three served frames against a trajectory computed by the oracle alone
+    (its exact best-matching landmarks, its FP64 SOM step, its projection of
+    the final landmarks), with nothing taken from the GPU: the coordinates
+    after the last frame agree within the projection's parity bar."""
+    p = dict(workloads.serve8(n_scale=0.01)[2])  # L=256, n=2,000
+    w, X, h, l = _session_arrays(p)
+    frames, alpha, sigma = 3, 0.05, 1.5
+    with esom.Server(1 << 30, 1) as srv:
+        s = srv.add_session(X, h, l, w.k, w.boost, w.adjust, alpha, sigma, minibatch=w.n)
+        for _ in range(frames):
+            srv.submit(s)
+        srv.poll(wait_all=True)
+        got, done = srv.output(s)
+        assert done == frames
+    hi = w.hi.astype(np.float64)
+    for _ in range(frames):
+        idx, _ = oracle.knn(w.X, hi.astype(np.float32), 1)
+        hi = oracle.som_step(hi, w.lo, w.X, idx[:, 0].astype(np.int32), alpha, sigma)
+    ref, ratio, _ = oracle.project(w.X, hi.astype(np.float32), w.lo, w.k, w.boost, w.adjust,
+                                   diagnostics=True)
+    stats = coord_errors(got.cpu().numpy(), ref, ratio, w.extent)
+    report(stats, f"served {frames} frames vs the oracle's own trajectory")
+
+
 def test_session_alone_equals_in_mix(esom):
     """Session 0's outputs after four frames (SOM window from the seed and the
     frame number) are bitwise the same served alone and served concurrently
