@@ -549,6 +549,33 @@ __device__ __forceinline__ bool rerank(const float4 (&x)[D / 4], const float (&k
         Lg, mask, L, k, M, q, ed, ei, koff, lperm);
 }
 
+// Writes one point's k neighbours (indices, and distances when dist2 is
+// set) at row * k: 16-byte stores when k is a multiple of 4 and both arrays
+// are 16-byte aligned (then every row is), else one value at a time.
+template <int KK>
+__device__ __forceinline__ void store_neighbours(int *idx, float *dist2, long long row, int k,
+                                                 const int (&si)[KK], const float (&sd)[KK]) {
+    const bool vec = (k & 3) == 0 && ((uintptr_t)idx & 15u) == 0 &&
+                     ((uintptr_t)dist2 & 15u) == 0;
+    if (vec) {
+        int4 *ip = reinterpret_cast<int4 *>(idx + row * k);
+        float4 *dp = reinterpret_cast<float4 *>(dist2 + row * k);
+#pragma unroll
+        for (int s = 0; s + 3 < KK; s += 4)
+            if (s < k) {
+                ip[s / 4] = make_int4(si[s], si[s + 1], si[s + 2], si[s + 3]);
+                if (dist2) dp[s / 4] = make_float4(sd[s], sd[s + 1], sd[s + 2], sd[s + 3]);
+            }
+        return;
+    }
+#pragma unroll
+    for (int s = 0; s < KK; ++s)
+        if (s < k) {
+            idx[row * k + s] = si[s];
+            if (dist2) dist2[row * k + s] = sd[s];
+        }
+}
+
 // Neighbour indices parked in this thread's own column of the queue buffer
 // (32-bit words col[i * QS], QS = threads of the tile; word i holds ranks 2i
 // and 2i+1 as 16-bit halves), so no other thread's words are touched.
@@ -1144,15 +1171,7 @@ __global__ void __launch_bounds__(kThreads, MINB) fused_kernel(const FusedArgs a
         }
 
         if (a.mode == kKnn) {
-            if (active) {
-                const long long row = row0 + tid;
-#pragma unroll
-                for (int s = 0; s < KK; ++s)
-                    if (s < a.k) {
-                        a.idx[row * a.k + s] = si[s];
-                        if (a.dist2) a.dist2[row * a.k + s] = sd[s];
-                    }
-            }
+            if (active) store_neighbours<KK>(a.idx, a.dist2, row0 + tid, a.k, si, sd);
             continue;
         }
         // The queue is empty now: park the neighbour indices in this thread's
@@ -1545,12 +1564,7 @@ __device__ __forceinline__ void rerank_tiles(const FusedArgs &a, const float4 *L
             atomicAdd(reinterpret_cast<unsigned *>(a.status) + 2, 1u);
             a.fail_list[atomicAdd(a.fail_count, 1u)] = row;
         }
-#pragma unroll
-        for (int s2 = 0; s2 < KK; ++s2)
-            if (s2 < a.k) {
-                a.idx[row * a.k + s2] = si[s2];
-                if (a.dist2) a.dist2[row * a.k + s2] = sd[s2];
-            }
+        store_neighbours<KK>(a.idx, a.dist2, row, a.k, si, sd);
     }
 }
 

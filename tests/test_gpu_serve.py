@@ -232,7 +232,7 @@ def test_served_trajectory_against_oracle_only(esom):
         assert done == frames
     hi = w.hi.astype(np.float64)
     for _ in range(frames):
-        idx, _ = oracle.knn(w.X, hi.astype(np.float32), 1)
+        idx, _ = oracle.knn(w.X, hi.astype(np.float32), 2)  # the oracle's k-NN wants k >= 2
         hi = oracle.som_step(hi, w.lo, w.X, idx[:, 0].astype(np.int32), alpha, sigma)
     ref, ratio, _ = oracle.project(w.X, hi.astype(np.float32), w.lo, w.k, w.boost, w.adjust,
                                    diagnostics=True)
