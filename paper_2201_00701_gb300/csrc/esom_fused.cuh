@@ -719,13 +719,44 @@ __device__ __forceinline__ void pair_sums_regs(const float (&hd)[KK], const floa
     }
 }
 
+// NG consecutive pairs (u, v0) .. (u, v0 + NG - 1) of the projection
+// kernels' pair loop (all of them exist): the landmark indices from the
+// stash column, then every table load of the group, then the pair terms.
+template <int NG, bool ADJ1, int MODE, int NT>
+__device__ __forceinline__ void pair_group(const float2 *sst, const int *sti, int v0,
+                                           const float2 *trow, const float *qrow,
+                                           const float2 *lo2, float2 pu, float ux, float uy,
+                                           float2 uh, float adjust, NormalSys &S) {
+    int iv[NG];
+    float2 ev[NG];
+#pragma unroll
+    for (int j = 0; j < NG; ++j) iv[j] = sti[(v0 + j) * NT];
+    // (cached in L1: the spatially ordered points of a warp share most of
+    // their neighbours, so they reread the same entries)
+#pragma unroll
+    for (int j = 0; j < NG; ++j) {
+        if (MODE == kPairTab2)
+            ev[j] = __ldg(trow + iv[j]);
+        else
+            ev[j].x = __ldg(qrow + iv[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NG; ++j) {
+        const float2 vh = sst[(v0 + j) * NT];
+        const float2 pv = lo2[iv[j]];
+        const float hx = pv.x - pu.x, hy = pv.y - pu.y;
+        const float2 e = MODE == kPairTab2 ? ev[j] : pair_entry(ev[j].x, hx, hy);
+        pair_add<ADJ1>(ux, uy, uh.x, uh.y, hx, hy, vh.x, vh.y, e, adjust, S);
+    }
+}
+
 // The same pairs for the projection kernels, both loops at run time: each
 // neighbour's score and half distance (sst, float2) and landmark index (sti)
 // sit in this thread's columns of shared memory (stride NT), the 2-D
 // positions in lo2; the pair constants of u's row come from the table in
-// groups of 8 whose loads are issued before their pairs are summed (MODE
-// kPairTab2 / kPairTab1), or are computed from the rows (kPairRows).  Only
-// the pairs u < v < m are visited.
+// groups (pair_group) whose loads are issued before their pairs are summed
+// (MODE kPairTab2 / kPairTab1), or are computed from the rows (kPairRows).
+// Only the pairs u < v < m are visited, in ascending v.
 template <int D, bool ADJ1, int MODE, int NT>
 __device__ __forceinline__ void pair_sums_stash(const float2 *sst, const int *sti, int m,
                                                 const float2 *lo2, float2 l0, const FusedArgs &a,
@@ -757,32 +788,26 @@ __device__ __forceinline__ void pair_sums_stash(const float2 *sst, const int *st
         } else {
             const float2 *trow = MODE == kPairTab2 ? a.ptab + (size_t)iu * a.L : nullptr;
             const float *qrow = MODE == kPairTab1 ? a.qtab + (size_t)iu * a.L : nullptr;
+            // whole groups of G, then one group each of 4, 2 and 1 as the
+            // row's remainder asks: no slot runs past the row's last pair
+            int v0 = u + 1;
 #pragma unroll 1
-            for (int v0 = u + 1; v0 < m; v0 += G) {
-                int iv[G];
-                float2 ev[G];
-#pragma unroll
-                for (int j = 0; j < G; ++j) iv[j] = v0 + j < m ? sti[(v0 + j) * NT] : iu;
-#pragma unroll
-                // (cached in L1: the spatially ordered points of a warp share
-                // most of their neighbours, so they reread the same entries)
-                for (int j = 0; j < G; ++j) {
-                    if (MODE == kPairTab2)
-                        ev[j] = __ldg(trow + iv[j]);
-                    else
-                        ev[j].x = __ldg(qrow + iv[j]);
-                }
-#pragma unroll
-                for (int j = 0; j < G; ++j) {
-                    if (v0 + j < m) {
-                        const float2 vh = sst[(v0 + j) * NT];
-                        const float2 pv = lo2[iv[j]];
-                        const float hx = pv.x - pu.x, hy = pv.y - pu.y;
-                        const float2 e = MODE == kPairTab2 ? ev[j] : pair_entry(ev[j].x, hx, hy);
-                        pair_add<ADJ1>(ux, uy, uh.x, uh.y, hx, hy, vh.x, vh.y, e, a.adjust, S);
-                    }
-                }
+            for (; v0 + G <= m; v0 += G)
+                pair_group<G, ADJ1, MODE, NT>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
+                                              a.adjust, S);
+            if (v0 + 4 <= m) {
+                pair_group<4, ADJ1, MODE, NT>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
+                                              a.adjust, S);
+                v0 += 4;
             }
+            if (v0 + 2 <= m) {
+                pair_group<2, ADJ1, MODE, NT>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
+                                              a.adjust, S);
+                v0 += 2;
+            }
+            if (v0 < m)
+                pair_group<1, ADJ1, MODE, NT>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
+                                              a.adjust, S);
         }
     }
 }
