@@ -672,6 +672,8 @@ __device__ __forceinline__ void pair_add(float ux, float uy, float su, float hdu
     S.b1 = b.y;
 }
 
+template <int V> struct IntConst { static constexpr int value = V; };
+
 // The pairs of one point whose neighbour indices sit in this thread's column
 // of shared memory (nb_at) and whose scores and half distances are in
 // registers (the fused and batched kernels); 2-D positions gathered from
@@ -702,19 +704,43 @@ __device__ __forceinline__ void pair_sums_regs(const float (&hd)[KK], const floa
 #pragma unroll
         for (int e = 0; e < D / 4; ++e)
             lu[e] = (trow || qrow) ? make_float4(0.f, 0.f, 0.f, 0.f) : Lu[e ^ fu];
-#pragma unroll
-        for (int v = 1; v < KK; ++v) {
-            if (v > u && v < m) {
-                const int iv = nb_at<QS>(nb, v);
-                const float2 pv = lo2[iv];
-                const float hx = pv.x - pu.x, hy = pv.y - pu.y;
-                const float2 e =
-                    trow ? __ldg(trow + iv)
-                         : pair_entry(qrow ? __ldg(qrow + iv)
-                                           : pair_q<D>(lu, Lg + (size_t)iv * (D / 4), swz(D, iv)),
-                                      hx, hy);
-                pair_add<ADJ1>(ux, uy, su, hdu, hx, hy, ss[v], hd[v], e, a.adjust, S);
+        // pair (u, v) for a compile-time v, so ss[v] and hd[v] stay registers
+        const auto pair_v = [&](auto vc) {
+            constexpr int v = decltype(vc)::value;
+            if constexpr (v < KK) {
+                if (v < m) {
+                    const int iv = nb_at<QS>(nb, v);
+                    const float2 pv = lo2[iv];
+                    const float hx = pv.x - pu.x, hy = pv.y - pu.y;
+                    const float2 e =
+                        trow ? __ldg(trow + iv)
+                             : pair_entry(qrow ? __ldg(qrow + iv)
+                                               : pair_q<D>(lu, Lg + (size_t)iv * (D / 4),
+                                                           swz(D, iv)),
+                                          hx, hy);
+                    pair_add<ADJ1>(ux, uy, su, hdu, hx, hy, ss[v], hd[v], e, a.adjust, S);
+                }
             }
+        };
+        // v = u + 1, ..., m - 1 in ascending order: one jump to the first
+        // pair of the row, then straight through (no per-slot v > u test)
+        static_assert(KK <= 32, "list capacity above the pair cases");
+        switch (u + 1) {
+#define ESOM_PAIR_CASE(V) \
+    case V:               \
+        pair_v(IntConst<V>{}); \
+        [[fallthrough]];
+            ESOM_PAIR_CASE(1) ESOM_PAIR_CASE(2) ESOM_PAIR_CASE(3) ESOM_PAIR_CASE(4)
+            ESOM_PAIR_CASE(5) ESOM_PAIR_CASE(6) ESOM_PAIR_CASE(7) ESOM_PAIR_CASE(8)
+            ESOM_PAIR_CASE(9) ESOM_PAIR_CASE(10) ESOM_PAIR_CASE(11) ESOM_PAIR_CASE(12)
+            ESOM_PAIR_CASE(13) ESOM_PAIR_CASE(14) ESOM_PAIR_CASE(15) ESOM_PAIR_CASE(16)
+            ESOM_PAIR_CASE(17) ESOM_PAIR_CASE(18) ESOM_PAIR_CASE(19) ESOM_PAIR_CASE(20)
+            ESOM_PAIR_CASE(21) ESOM_PAIR_CASE(22) ESOM_PAIR_CASE(23) ESOM_PAIR_CASE(24)
+            ESOM_PAIR_CASE(25) ESOM_PAIR_CASE(26) ESOM_PAIR_CASE(27) ESOM_PAIR_CASE(28)
+            ESOM_PAIR_CASE(29) ESOM_PAIR_CASE(30) ESOM_PAIR_CASE(31)
+#undef ESOM_PAIR_CASE
+            default:
+                break;
         }
     }
 }
