@@ -77,6 +77,9 @@ void fill_args(const esom_ctx *h, const float *points, long long n, float *out, 
     // the pair constants from the handle's table (whichever it keeps)
     a->ptab = h->ptab;
     a->qtab = h->qtab;
+    // (current whenever screening is on: build_screening refreshes it)
+    a->ptab_pos = h->screening && h->order_on ? h->ptab_pos : nullptr;
+    a->ipos = a->ptab_pos ? h->ipos : nullptr;
     a->center = h->centered ? h->center : nullptr;
     a->tc_chunks = (h->L + kTcN - 1) / kTcN;
     a->refine_list = h->refine_list;
@@ -269,6 +272,9 @@ cudaError_t build_screening(esom_ctx *h, int prec, cudaStream_t st) {
     if (e == cudaSuccess)
         e = esom::launch_tc_image(h->hi, h->L, h->d, h->img, prec, st,
                                   h->order_on ? h->lperm : nullptr);
+    // the pair table of the current landmarks, moved into the same order
+    if (e == cudaSuccess && h->order_on && h->ptab_pos)
+        e = esom::launch_pair_table_positions(h->ptab, h->lperm, h->L, h->ptab_pos, h->ipos, st);
     return e;
 }
 
@@ -1157,7 +1163,14 @@ esom_status esom_set_screening(esom_handle h, int mode, esom_stream_t stream) {
         if (e == cudaSuccess)
             e = cudaMalloc(&h->tile_home,
                            (size_t)(esom::kTcPass / esom::kTcRows) * sizeof(unsigned short));
+        if (e == cudaSuccess && h->ptab)
+            e = cudaMalloc(&h->ptab_pos, (size_t)h->L * h->L * sizeof(float2));
+        if (e == cudaSuccess && h->ptab) e = cudaMalloc(&h->ipos, (size_t)h->L * sizeof(int));
         if (e != cudaSuccess) {
+            cudaFree(h->ptab_pos);
+            cudaFree(h->ipos);
+            h->ptab_pos = nullptr;
+            h->ipos = nullptr;
             cudaFree(h->lperm);
             cudaFree(h->centers);
             cudaFree(h->norms_int);
@@ -1196,6 +1209,8 @@ esom_status esom_destroy(esom_handle h) {
     cudaFree(h->img);
     cudaFree(h->qtab);
     cudaFree(h->ptab);
+    cudaFree(h->ptab_pos);
+    cudaFree(h->ipos);
     for (int i = 0; i < esom_ctx::kTimed; ++i)
         for (int j = 0; j < 2; ++j)
             if (h->tev[i][j]) cudaEventDestroy(h->tev[i][j]);

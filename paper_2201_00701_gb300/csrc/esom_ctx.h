@@ -75,6 +75,10 @@ struct esom_ctx {
     // frame server); order_valid: lperm holds an order of this handle
     int keep_order = 0, order_valid = 0;
     int *lperm = nullptr;
+    // the pair table in the landmark order lperm and the inverse order
+    // (with ptab and the orders), rebuilt with the tensor-core operands
+    float2 *ptab_pos = nullptr;
+    int *ipos = nullptr;
     float *centers = nullptr;
     float *norms_int = nullptr;
     unsigned short *corder = nullptr;

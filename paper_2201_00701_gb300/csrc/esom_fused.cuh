@@ -745,10 +745,16 @@ __device__ __forceinline__ void pair_sums_regs(const float (&hd)[KK], const floa
     }
 }
 
+// Stash words of the position-ordered pair table (POS): the landmark index
+// in the low 16 bits, its position in the landmark order in the high 16.
+__device__ __forceinline__ int stash_landmark(int w, bool pos) { return pos ? (w & 0xFFFF) : w; }
+__device__ __forceinline__ int stash_column(int w, bool pos) { return pos ? (w >> 16) : w; }
+
 // NG consecutive pairs (u, v0) .. (u, v0 + NG - 1) of the projection
 // kernels' pair loop (all of them exist): the landmark indices from the
 // stash column, then every table load of the group, then the pair terms.
-template <int NG, bool ADJ1, int MODE, int NT>
+// trow is u's table row; with POS its columns are landmark positions.
+template <int NG, bool ADJ1, int MODE, int NT, bool POS>
 __device__ __forceinline__ void pair_group(const float2 *sst, const int *sti, int v0,
                                            const float2 *trow, const float *qrow,
                                            const float2 *lo2, float2 pu, float ux, float uy,
@@ -762,14 +768,14 @@ __device__ __forceinline__ void pair_group(const float2 *sst, const int *sti, in
 #pragma unroll
     for (int j = 0; j < NG; ++j) {
         if (MODE == kPairTab2)
-            ev[j] = __ldg(trow + iv[j]);
+            ev[j] = __ldg(trow + stash_column(iv[j], POS));
         else
             ev[j].x = __ldg(qrow + iv[j]);
     }
 #pragma unroll
     for (int j = 0; j < NG; ++j) {
         const float2 vh = sst[(v0 + j) * NT];
-        const float2 pv = lo2[iv[j]];
+        const float2 pv = lo2[stash_landmark(iv[j], POS)];
         const float hx = pv.x - pu.x, hy = pv.y - pu.y;
         const float2 e = MODE == kPairTab2 ? ev[j] : pair_entry(ev[j].x, hx, hy);
         pair_add<ADJ1>(ux, uy, uh.x, uh.y, hx, hy, vh.x, vh.y, e, adjust, S);
@@ -782,16 +788,20 @@ __device__ __forceinline__ void pair_group(const float2 *sst, const int *sti, in
 // positions in lo2; the pair constants of u's row come from the table in
 // groups (pair_group) whose loads are issued before their pairs are summed
 // (MODE kPairTab2 / kPairTab1), or are computed from the rows (kPairRows).
-// Only the pairs u < v < m are visited, in ascending v.
-template <int D, bool ADJ1, int MODE, int NT>
+// Only the pairs u < v < m are visited, in ascending v.  With POS (table
+// mode only) the stash words also carry the landmarks' positions and the
+// constants come from the position-ordered table a.ptab_pos.
+template <int D, bool ADJ1, int MODE, int NT, bool POS = false>
 __device__ __forceinline__ void pair_sums_stash(const float2 *sst, const int *sti, int m,
                                                 const float2 *lo2, float2 l0, const FusedArgs &a,
                                                 NormalSys &S) {
+    static_assert(!POS || MODE == kPairTab2, "positions index the pair table only");
     constexpr int G = 8;
 #pragma unroll 1
     for (int u = 0; u < m - 1; ++u) {
         const float2 uh = sst[u * NT];  // (s_u, hd_u)
-        const int iu = sti[u * NT];
+        const int wu = sti[u * NT];
+        const int iu = stash_landmark(wu, POS);
         const float2 pu = lo2[iu];
         const float ux = pu.x - l0.x, uy = pu.y - l0.y;
         if constexpr (MODE == kPairRows) {
@@ -812,27 +822,30 @@ __device__ __forceinline__ void pair_sums_stash(const float2 *sst, const int *st
                                a.adjust, S);
             }
         } else {
-            const float2 *trow = MODE == kPairTab2 ? a.ptab + (size_t)iu * a.L : nullptr;
+            const float2 *trow =
+                MODE != kPairTab2 ? nullptr
+                : POS             ? a.ptab_pos + (size_t)stash_column(wu, true) * a.L
+                                  : a.ptab + (size_t)iu * a.L;
             const float *qrow = MODE == kPairTab1 ? a.qtab + (size_t)iu * a.L : nullptr;
             // whole groups of G, then one group each of 4, 2 and 1 as the
             // row's remainder asks: no slot runs past the row's last pair
             int v0 = u + 1;
 #pragma unroll 1
             for (; v0 + G <= m; v0 += G)
-                pair_group<G, ADJ1, MODE, NT>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
+                pair_group<G, ADJ1, MODE, NT, POS>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
                                               a.adjust, S);
             if (v0 + 4 <= m) {
-                pair_group<4, ADJ1, MODE, NT>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
+                pair_group<4, ADJ1, MODE, NT, POS>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
                                               a.adjust, S);
                 v0 += 4;
             }
             if (v0 + 2 <= m) {
-                pair_group<2, ADJ1, MODE, NT>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
+                pair_group<2, ADJ1, MODE, NT, POS>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
                                               a.adjust, S);
                 v0 += 2;
             }
             if (v0 < m)
-                pair_group<1, ADJ1, MODE, NT>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
+                pair_group<1, ADJ1, MODE, NT, POS>(sst, sti, v0, trow, qrow, lo2, pu, ux, uy, uh,
                                               a.adjust, S);
         }
     }
@@ -958,7 +971,9 @@ __device__ __forceinline__ float2 project_point(const float (&sd)[KK], const uin
 // exact squared distances in registers (si, sd); each neighbour's score and
 // half distance and its index go to this thread's stash columns sst / sti
 // (stride NT) for the pair loop.
-template <int D, int KK, int MODE, int NT, class SINK>
+// With POS the index words also carry each landmark's position in the
+// landmark order (a.ipos) for the position-ordered pair table.
+template <int D, int KK, int MODE, int NT, bool POS = false, class SINK>
 __device__ __forceinline__ float2 project_point_stash(const float (&sd)[KK], const int (&si)[KK],
                                                       float2 *sst, int *sti, const float2 *lo2,
                                                       const FusedArgs &a, long long row,
@@ -971,13 +986,13 @@ __device__ __forceinline__ float2 project_point_stash(const float (&sd)[KK], con
     for (int t = 0; t < KK; ++t)
         if (t < m) {
             sst[t * NT] = make_float2(ss[t], 0.5f * sd[t]);
-            sti[t * NT] = si[t];
+            sti[t * NT] = POS ? si[t] | (__ldg(a.ipos + si[t]) << 16) : si[t];
         }
     NormalSys S = {0.f, 0.f, 0.f, 0.f, 0.f};
     if (a.adjust == 1.f)
-        pair_sums_stash<D, true, MODE, NT>(sst, sti, m, lo2, l0, a, S);
+        pair_sums_stash<D, true, MODE, NT, POS>(sst, sti, m, lo2, l0, a, S);
     else
-        pair_sums_stash<D, false, MODE, NT>(sst, sti, m, lo2, l0, a, S);
+        pair_sums_stash<D, false, MODE, NT, POS>(sst, sti, m, lo2, l0, a, S);
     return point_solve(S, l0, row, active, sink);
 }
 
@@ -1665,9 +1680,11 @@ cudaError_t launch_rerank(const FusedArgs &a, int grid, size_t smem, cudaStream_
 // certified list, steps 2-4 of the projection kernel with the neighbours
 // still in registers, so no neighbour exchange buffer is written or read.
 // The re-rank reads the landmark rows through the L1 cache.  A point whose
-// certificate
-// fails goes to a.fail_list; rescan_kernel and the projection kernel over
-// that list finish it.
+// certificate fails goes to a.fail_list; rescan_kernel and the projection
+// kernel over that list finish it.  With the pair table in the landmark
+// order (a.ptab_pos) a point's pair constants come from it: its neighbours
+// sit close together in that order, so their entries of a table row share
+// cache lines (same values as a.ptab, so the same bits).
 template <int D, int KC, int MODE>
 __global__ void __launch_bounds__(proj_threads(MODE), proj_min_blocks(KC))
     rerank_project_kernel(const FusedArgs a) {
@@ -1722,9 +1739,15 @@ __global__ void __launch_bounds__(proj_threads(MODE), proj_min_blocks(KC))
         const bool proj = active && cert;
 #pragma unroll
         for (int t = 0; t < KK; ++t) si[t] = min(max(si[t], 0), a.L - 1);
-        const float2 p = project_point_stash<D, KK, MODE, NT>(
-            sd, si, sst + tid, sti + tid, lo2, a, row, proj,
-            RefineSink{a.refine_list, a.refine_count});
+        float2 p;
+        if (MODE == kPairTab2 && a.ptab_pos)
+            p = project_point_stash<D, KK, MODE, NT, MODE == kPairTab2>(
+                sd, si, sst + tid, sti + tid, lo2, a, row, proj,
+                RefineSink{a.refine_list, a.refine_count});
+        else
+            p = project_point_stash<D, KK, MODE, NT>(sd, si, sst + tid, sti + tid, lo2, a, row,
+                                                     proj,
+                                                     RefineSink{a.refine_list, a.refine_count});
         if (proj) reinterpret_cast<float2 *>(a.out)[row] = p;
     }
 }

@@ -44,6 +44,13 @@ struct FusedArgs {
     // (pair_q values) for larger L; both null: computed from the rows
     const float2 *ptab;
     const float *qtab;
+    // the pair table with rows and columns in the spatial landmark order
+    // (ptab_pos[i * L + j] = ptab[lperm[i] * L + lperm[j]]) and each
+    // landmark's position in that order (ipos[lperm[i]] = i): the re-rank +
+    // projection kernel gathers a point's pair constants from it, so that
+    // neighbouring landmarks' entries share cache lines; null: ptab
+    const float2 *ptab_pos;
+    const int *ipos;
     // k-NN mode: when set, a point whose screening certificate fails is not
     // rescanned in line but appended (row index) to fail_list, counted in
     // *fail_count; rescan_kernel then finds its neighbours exactly
@@ -255,6 +262,11 @@ constexpr int kOrderMaxL = 8192;
 cudaError_t launch_landmark_order(const float *hi, const float *norms, int L, int D, int *lperm,
                                   float *centers, float *norms_int, unsigned short *corder,
                                   cudaStream_t stream, bool reorder = true);
+// The pair table in the landmark order lperm (ptab_pos[i * L + j] =
+// ptab[lperm[i] * L + lperm[j]], the same entries moved) and the inverse
+// order (ipos[lperm[i]] = i), for L <= kPtabMaxL.
+cudaError_t launch_pair_table_positions(const float2 *ptab, const int *lperm, int L,
+                                        float2 *ptab_pos, int *ipos, cudaStream_t stream);
 // The points of one pass grouped by home chunk (nearest centroid):
 // perm[pos] = point at visiting position pos, tile_home[t] = home chunk of
 // position kTcRows t; home (n) and counts (nblocks * nch) are scratch.

@@ -450,4 +450,34 @@ cudaError_t launch_point_order(const float *X, long long n, int D, const float *
     return cudaGetLastError();
 }
 
+// ipos[lperm[i]] = i, one thread per position.
+__global__ void landmark_rank_kernel(const int *__restrict__ lperm, int L, int *__restrict__ ipos) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < L) ipos[lperm[i]] = i;
+}
+
+// ptab_pos[i * L + j] = ptab[lperm[i] * L + lperm[j]]: one block row per
+// position i (grid.y), threads over j; the source row is read in the order
+// lperm gives, the destination row written contiguously.
+__global__ void pair_table_positions_kernel(const float2 *__restrict__ ptab,
+                                            const int *__restrict__ lperm, int L,
+                                            float2 *__restrict__ ptab_pos) {
+    const int i = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L || j >= L) return;
+    const size_t src = (size_t)__ldg(lperm + i) * L;
+    ptab_pos[(size_t)i * L + j] = __ldg(ptab + src + __ldg(lperm + j));
+}
+
+cudaError_t launch_pair_table_positions(const float2 *ptab, const int *lperm, int L,
+                                        float2 *ptab_pos, int *ipos, cudaStream_t stream) {
+    if (L < 1) return cudaSuccess;
+    landmark_rank_kernel<<<(L + 255) / 256, 256, 0, stream>>>(lperm, L, ipos);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((L + 255) / 256), (unsigned)L);
+    pair_table_positions_kernel<<<grid, 256, 0, stream>>>(ptab, lperm, L, ptab_pos);
+    return cudaGetLastError();
+}
+
 }  // namespace esom

@@ -377,7 +377,9 @@ esom_status esom_server_add_session(esom_server s, const esom_session_desc *desc
     const size_t img = s->screening != ESOM_SCREEN_FP32
                            ? (size_t)((d.L + esom::kTcN - 1) / esom::kTcN) *
                                      esom::tc_chunk_bytes(d.d, esom::kTcTf32) +
-                                 (size_t)esom::kTcPass * (d.k * 8 + (d.k + 8) * 4)
+                                 (size_t)esom::kTcPass * (d.k * 8 + (d.k + 8) * 4) +
+                                 // the pair table in the landmark order
+                                 (d.L <= esom::kPtabMaxL ? (size_t)d.L * d.L * 8 + d.L * 4 : 0)
                            : 0;
     const size_t bytes = (size_t)d.n * d.d * 4 + (size_t)d.n * 8 + (size_t)d.L * (d.d + 2) * 4 * 2 +
                          (size_t)((d.L + 63) & ~63) * 4 + qtab + img +
